@@ -25,7 +25,9 @@
  *   - the barrier Hessian freezes the closest-point coefficients c (Sec. 3.2 states d2t/dx2 = 0).
  *   - closest points: PT interior projection (2x2 normal equations), else the three clamped point-edge cases;
  *     EE interior solution (2x2), else the four clamped point-edge cases; ties keep the first case in that order.
- *   - preconditioner P_ii = 1 / diag_ii when diag_ii > 0, else 1 / m_v; kinematic vertices get P = 0, g = 0.
+ *   - preconditioner P_ii = 1 / max(diag_ii, m_v): the Jacobi preconditioner of Sec. 4.2 wherever the diagonal is at
+ *     least the vertex mass; below that (the barrier term (b'/d) c_i^2 of Eq. 10 is negative) the inertia diagonal
+ *     alone, which keeps P continuous and bounded by 1/m_v; kinematic vertices get P = 0, g = 0.
  *   - PR+ beta = max(0, g1^T P1 (g1 - g0) / (g0^T P0 g0)); restart (beta = 0) when g^T p >= 0 after forming p.
  *   - ||p||_inf in the step cap is the largest per-vertex Euclidean length (the cap bounds vertex displacement
  *     by dhat/2, Sec. 4.3); the largest absolute component is an option.
@@ -992,7 +994,7 @@ int or_iteration(const or_model *m, double *x, const double *xtilde, double *g, 
         for (int a = 0; a < 3; ++a) {
             size_t q = 3 * (size_t)i + a;
             if (m->fixed[i]) { g1[q] = 0.0; P1[q] = 0.0; continue; }
-            P1[q] = d1[q] > 0.0 ? 1.0 / d1[q] : 1.0 / m->mass[i];
+            P1[q] = 1.0 / (d1[q] > m->mass[i] ? d1[q] : m->mass[i]);
         }
     int32_t nplane = 0;
     if (m->p.has_plane)

@@ -191,3 +191,21 @@ def test_drop_and_blocks_runs_are_penetration_free(oracle_mod):
                 assert x[:, 2].min() > 0
             idx, d, _ = o.active_pairs(x)
             assert len(d) == 0 or d.min() > 0
+
+
+def test_preconditioner_is_jacobi_clamped_at_the_mass(oracle_mod):
+    """Sec. 4.2 gives P = diag(H)^-1.  The barrier term (b'/d) c_i^2 of Eq. 10 is negative, so contact vertices can
+    have diag(H) below the mass (even negative); there P falls back to the inertia diagonal 1/m."""
+    sc = S.two_blocks(1)
+    o = oracle_mod.Oracle.from_scene(sc)
+    x = sc.x0.copy()
+    xt = o.predict(x, sc.v0)
+    _, diag, na = o.grad_diag(x, xt)
+    m = np.repeat(o.mass()[:, None], 3, axis=1)
+    low = diag < m
+    assert na > 0 and low.any() and (~low).any()
+    g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
+    o.iteration(x, xt, g, P, p, 0)
+    np.testing.assert_array_equal(P[low], 1.0 / m[low])
+    np.testing.assert_allclose(P[~low], 1.0 / diag[~low], rtol=1e-15)
+    assert np.all(P <= 1.0 / m)
