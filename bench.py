@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark of the PNCG solver on the 98,304-tet twisted bar (16x16x64 Kuhn-split cells, 0.1 x 0.1 x 0.4 m,
+Neo-Hookean E = 1e5 Pa, nu = 0.45, both end caps turned in opposite directions at 2 rad/s, dt = 1/30 s,
+dhat = 5e-4 m, kappa = 1e4, 50 NCG iterations per time step).
+
+One benchmark step is one time step: prediction, candidate passes, 50 PNCG iterations (gradient + Jacobi
+diagonal, beta reductions, direction, p^T H p, step, update), velocity update.  The headline value is NCG
+iterations per second of the FP32-mixed form (whole job: summed over all ranks), with the plain FP64 form timed
+beside it.  Inputs (the kinematic targets of every step) are resident on the device before the timed region; L2
+is flushed (a 256 MiB write) between timed steps and the flush is not timed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun, one process per GPU) every rank runs its own independent replica of the problem.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NCG iters/s and ms per time step at 98k tets; % HBM peak; vs FP64 plain"
+UNIT = "iter/s"
+WORKLOAD = ("twisted bar: 16x16x64 Kuhn grid (98,304 tets, 18,785 verts), 0.1x0.1x0.4 m, Neo-Hookean E=1e5 "
+            "nu=0.45 rho=1000, caps +-2 rad/s, dt=1/30 s, dhat=5e-4 m, kappa=1e4, 50 NCG iterations per step")
+
+
+def rank_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while GPU work runs (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def algorithmic_bytes(kernel: str, prec: int, sizes: dict, n_cand: int, n_active: int) -> float:
+    """Bytes each launch must move at least once (every array read or written counted once).
+
+    Vertex state: x (double4, 32 B) and, in the FP32 form, its float-float copy (2 x float4) and the float-float
+    rest positions; accumulators g, diag and the direction p are 4-vectors of the element type (16 B float, 32 B
+    double).  Per tet: 4 indices (16 B), D_m^-1 (9 values), h^2 V (1 value).  Candidates: int4 (16 B); active pairs
+    (64 B float form, 112 B double form) written by the gradient pass and read by p^T H p."""
+    T, V = sizes["n_tets"], sizes["n_verts"]
+    r = 4 if prec == 1 else 8
+    v4 = 4 * r
+    tet = 16 + 10 * r
+    act = 64 if prec == 1 else 112
+    xpos = 64 if prec == 1 else 32          # gathered positions per vertex (ff current + ff rest, or double4)
+    if kernel == "k_grad":
+        return T * tet + V * (xpos + 2 * 2 * v4) + n_cand * 16 + n_active * act
+    if kernel == "k_pHp":
+        return T * tet + V * ((32 if prec == 1 else 32) + v4) + n_active * act
+    if kernel in ("k_dots", "k_dir"):
+        return V * 4 * v4
+    if kernel == "k_update":
+        return V * (32 + 32 + v4 + 32 + 32 + 2 * v4 + (32 if prec == 1 else 0))
+    return None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2405_08001_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, prec_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_twisted_bar_{prec_name}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("- ") and ":" in ln:
+                k, v = ln[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def time_steps(B, torch, sim, targets, first, K, flush):
+    """Times K time steps one by one with CUDA events on the solver's stream; returns per-step milliseconds."""
+    stream = torch.cuda.current_stream()
+    times = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for s in range(K):
+        flush.zero_()
+        ev[s][0].record(stream)
+        B.sim_step_async(sim.h, 1, targets[first + s])
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = rank_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2405_08001_gb300 import binding as B, build, scenes as S
+    build.build()
+    B.load()
+    sc = S.twisted_bar()
+    iters = sc.iters
+    W, K = args.warmup, args.steps
+    n_total = W + K + 4
+    # a dedicated stream: the solver, the events and the L2 flush all run on it (the legacy default stream could
+    # not be captured into the solver's CUDA graph)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)
+    targets = torch.tensor(sc.all_targets(n_total), dtype=torch.float64, device="cuda").contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+
+    def one_form(prec, K_):
+        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream)
+        for s in range(W):
+            B.sim_step_async(sim.h, 1, targets[s])
+        torch.cuda.synchronize()
+        B.sim_get_state(sim.h, want_x=False, want_v=False)     # raises on a kernel error
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times = time_steps(B, torch, sim, targets, W, K_, flush)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        _, _, st = B.sim_get_state(sim.h, want_x=False, want_v=False)
+        return sim, times, st
+
+    sim32, t32, st32 = one_form(B.SIM_FP32_MIXED, K)
+    total_ms = sum(t32)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * K * iters / (total_ms / 1e3)
+
+    # kernel-by-kernel GPU times of three more steps (after the timed region) for the roofline
+    prof = {}
+    for s in range(3):
+        for k, (ms, n) in B.sim_profile_step(sim32.h, targets[W + K + s]).items():
+            a, b = prof.get(k, (0.0, 0))
+            prof[k] = (a + ms, b + n)
+    _, _, stp = B.sim_get_state(sim32.h, want_x=False, want_v=False)
+    sizes = sim32.sizes()
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    step_ms = sum(v[0] for v in prof.values()) / 3
+    per_launch_ms = prof[dom][0] / prof[dom][1]
+    iter_kernels = ("k_grad", "k_pHp", "k_dots", "k_dir", "k_update")
+    dom_all = dom
+    dom = max((k for k in iter_kernels if prof.get(k, (0, 0))[1] > 0), key=lambda k: prof[k][0])
+    per_launch_ms = prof[dom][0] / prof[dom][1]
+    abytes = algorithmic_bytes(dom, 1, sizes, stp["n_candidates"], stp["n_active"])
+    peak, peak_kind = measured_peaks()
+    achieved = abytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(dom, "fp32")
+    kernels = {k: {"ms_per_step": round(v[0] / 3, 4), "launches_per_step": v[1] // 3,
+                   "us_per_launch": round(1e3 * v[0] / v[1], 3) if v[1] else None,
+                   "share": round(v[0] / 3 / step_ms, 4) if step_ms > 0 else None}
+               for k, v in prof.items() if v[1] > 0}
+    sim32.close()
+
+    # plain FP64 form on the same steps
+    K64 = min(K, 40)
+    sim64, t64, st64 = one_form(B.SIM_FP64, K64)
+    sim64.close()
+    ms64 = sum(t64) / K64
+    v64 = K64 * iters / (sum(t64) / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned targets in, positions out, every step
+    e2e = None
+    if True:
+        sim = B.Sim(sc, precision=B.SIM_FP32_MIXED)
+        tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
+        x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
+        for s in range(W):
+            B.sim_step(sim.h, 1, tg_host[s])
+            B.sim_get_state(sim.h, x_out=x_host, want_v=False)
+        t0 = time.perf_counter()
+        for s in range(K):
+            B.sim_step(sim.h, 1, tg_host[W + s])
+            B.sim_get_state(sim.h, x_out=x_host, want_v=False)
+        te = time.perf_counter() - t0
+        sim.close()
+        e2e = {"value": round(K * iters / te, 2), "unit": UNIT, "ms_per_step": round(1e3 * te / K, 4),
+               "h2d_bytes_per_step": int(tg_host[0].numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 8)}
+    clocks = sampler.stop()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        launches_per_step = 2 + iters * 10
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tets": sizes["n_tets"], "verts": sizes["n_verts"],
+                       "iters_per_step": iters, "precision": "fp32-mixed: f32 element/barrier arithmetic on "
+                       "float-float vertex differences, f64 reductions and vertex state",
+                       "l2": "flushed between timed steps (256 MiB write, not timed)", "parallelism": "replicas",
+                       "graph": "one CUDA graph replay per time step"},
+            "time_steps_per_s": round(K / (total_ms / 1e3), 2),
+            "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
+                           "speedup_fp32_over_fp64": round(value / ws / v64, 3)},
+            "roofline": {"bound": "hbm", "kernel": dom, "largest_kernel_overall": dom_all, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes_per_launch": int(abytes),
+                         "us_per_launch": round(per_launch_ms * 1e3, 3)},
+            "kernels": kernels,
+            "stats_last_step": {k: st32[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")},
+            "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, budget_s=15.0):
+    """The FP64 oracle as it stands, single-threaded on the host, on a bounded sample of the same workload: NCG
+    iterations of time step 0 of the twisted bar (its contact search included)."""
+    import numpy as np
+    import oracle
+    o = oracle.Oracle.from_scene(sc)
+    x, v = sc.x0.copy(), sc.v0.copy()
+    tg = sc.targets(0)
+    xt = o.predict(x, v, tg)
+    x[sc.fixed.astype(bool)] = tg
+    g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
+    t0 = time.perf_counter()
+    n = 0
+    while n < sc.iters and (n == 0 or time.perf_counter() - t0 < budget_s):
+        o.iteration(x, xt, g, P, p, n)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} NCG iterations of time step 0 of the 98,304-tet twisted bar (FP64 C oracle, 1 thread, "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle on the same workload and metric; each benchmark step is one NCG
+    iteration (a bounded sample), iterations continuing through the time steps of the twist."""
+    import numpy as np
+    ws, rank, local = rank_info()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2405_08001_gb300 import scenes as S
+    sc = S.twisted_bar()
+    o = oracle.Oracle.from_scene(sc)
+    x, v = sc.x0.copy(), sc.v0.copy()
+    fx = sc.fixed.astype(bool)
+    state = {"step": -1, "k": sc.iters}
+
+    def one_iteration():
+        if state["k"] >= sc.iters:
+            if state["step"] >= 0:
+                v[:] = (x - state["xt0"]) / sc.dt
+            state["step"] += 1
+            tg = sc.targets(state["step"])
+            state["xt0"] = x.copy()
+            state["xtil"] = o.predict(x, v, tg)
+            x[fx] = tg
+            state["g"] = np.zeros_like(x); state["P"] = np.zeros_like(x); state["p"] = np.zeros_like(x)
+            state["k"] = 0
+        o.iteration(x, state["xtil"], state["g"], state["P"], state["p"], state["k"])
+        state["k"] += 1
+
+    for _ in range(args.warmup):
+        one_iteration()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one_iteration()
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "step": "one NCG iteration of the FP64 CPU oracle (bounded sample)"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 4), "unit": UNIT,
+                             "sample": f"{args.steps} consecutive NCG iterations of the twisted bar, 1 thread"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

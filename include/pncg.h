@@ -1,0 +1,243 @@
+/*
+ * pncg.h -- C ABI of the GB300 (sm_103a) PNCG solver library, libpncg.so.
+ *
+ * The library runs the per-iteration hot path of the Jacobi-preconditioned nonlinear conjugate gradient method
+ * for interior-point (IPC log-barrier) Neo-Hookean elastodynamics of Shen, Cai, Bi, Lv, "Preconditioned
+ * Nonlinear Conjugate Gradient Method for Real-time Interior-point Hyperelasticity" (SIGGRAPH 2024): the
+ * incremental-potential gradient, the Jacobi diagonal, p^T H p, the beta reductions, the single-pass step rule and
+ * a spatial-hash contact-candidate pass, all in hand-written CUDA kernels.
+ *
+ * Conventions (every entry point):
+ *   - Positions, velocities and vectors are double precision, array-of-structs [n_verts][3], SI units.
+ *   - Inputs are copied; nothing the caller passes is kept after the call returns.  Outputs go to caller-owned
+ *     buffers.  A pointer documented as "host or device" may be either: the library asks the CUDA driver which
+ *     one it is and copies accordingly.
+ *   - Every call returns a sim_status; nothing throws across the ABI.  Kernel errors (an inverted tet, a zero
+ *     contact distance, a non-finite value, a full candidate buffer) are recorded on the device and reported by
+ *     the next call that synchronises (sim_step, sim_get_state, sim_end_step, sim_eval_*).  sim_last_error()
+ *     gives a one-line description of the last failure of a handle.
+ *   - A handle is used by one host thread at a time.  All device work of a handle runs on its stream (the one in
+ *     sim_options.cuda_stream, or a stream the library creates), in order.
+ *   - There is no CPU fallback: without a CUDA device every call that needs one returns SIM_ERR_CUDA.
+ */
+#ifndef PNCG_H
+#define PNCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pncg_sim *sim_handle; /* opaque, owned by the library; released by sim_destroy */
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_ERR_INVALID_ARG = 1,  /* a null or out-of-range argument, a bad mesh (index out of range, tet of
+                                 non-positive rest volume) */
+    SIM_ERR_CUDA = 2,         /* a CUDA runtime call failed (no device, launch failure) */
+    SIM_ERR_OOM = 3,          /* device or host allocation failed */
+    SIM_ERR_INVERTED = 4,     /* det F <= 0 in some tet (log I3 undefined; Sec. 3.1 gives no remedy) */
+    SIM_ERR_PENETRATION = 5,  /* a contact distance (pair or plane) reached zero */
+    SIM_ERR_NONFINITE = 6,    /* a non-finite gradient, p^T H p or step */
+    SIM_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
+    SIM_ERR_CAPACITY = 8      /* the contact-candidate buffer overflowed; the step was not applied and the
+                                 buffer has been enlarged for the next call */
+} sim_status;
+
+enum { SIM_FP64 = 0, SIM_FP32_MIXED = 1 };                 /* sim_options.precision */
+enum { SIM_BETA_PR_PLUS = 0, SIM_BETA_DK = 1 };            /* sim_options.beta */
+enum { SIM_PNORM_VERTEX2 = 0, SIM_PNORM_COMPONENT_INF = 1 }; /* sim_options.pnorm */
+enum { SIM_SCATTER_ATOMIC = 0, SIM_SCATTER_SEGMENTED = 1 }; /* sim_options.scatter */
+
+/* Tetrahedral mesh and initial state (Sec. 3: x holds all vertex positions of the tet meshes). */
+typedef struct {
+    int32_t n_verts, n_tets;
+    const double *rest_x;   /* [n_verts][3] host, rest positions (define D_m and the rest-pose exclusion) */
+    const int32_t *tets;    /* [n_tets][4] host, vertex indices; rest volume must be positive */
+    const double *x0;       /* [n_verts][3] host, initial positions; NULL = rest_x */
+    const double *v0;       /* [n_verts][3] host, initial velocities; NULL = 0 */
+    const uint8_t *fixed;   /* [n_verts] host, 1 = kinematic (Dirichlet) vertex whose position is prescribed
+                               per step and whose g and p entries are held at zero; NULL = none */
+} sim_mesh;
+
+/* Neo-Hookean material (Sec. 3.1): mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)). */
+typedef struct {
+    double density;                /* rho, kg/m^3; lumped mass m_v = sum_e rho V_e / 4 */
+    double youngs, poisson;        /* E (Pa), nu */
+    const double *youngs_per_tet;  /* [n_tets] host, per-tet E overriding youngs; NULL = uniform */
+} sim_material;
+
+typedef struct {
+    int32_t precision;    /* SIM_FP64: all arithmetic in double.  SIM_FP32_MIXED: element and barrier arithmetic
+                             in float (from double vertex differences), reductions (dot products, p^T H p,
+                             energy) in double, distance re-evaluated in double when d < 1e-3 dhat */
+    int32_t beta;         /* SIM_BETA_PR_PLUS (default) or SIM_BETA_DK (Sec. 4.1-4.2) */
+    int32_t iters;        /* NCG iterations per time step (IterMax of Algorithm 1); default 50 */
+    double eps;           /* stop when Delta E < eps Delta E_0 (Sec. 4.4); 0 = always run iters (default) */
+    double gravity[3];    /* external acceleration, M^-1 f_ext (Sec. 3); default 0 */
+    int32_t has_plane;    /* 1 = vertex / half-space barrier n . x >= o with the same b, kappa, dhat */
+    double plane_n[3];    /* plane normal (normalised by the library) */
+    double plane_o;       /* plane offset */
+    double pad_r;         /* contact-candidate padding r: candidates are rebuilt when some vertex has moved r/2
+                             since the last build; <= 0 = default 4 dhat */
+    int32_t pnorm;        /* norm of p in alpha_upper = dhat / (2 ||p||): SIM_PNORM_VERTEX2 (largest per-vertex
+                             Euclidean length, default) or SIM_PNORM_COMPONENT_INF (largest component) */
+    int32_t scatter;      /* gradient / diagonal scatter: SIM_SCATTER_ATOMIC (default) or SIM_SCATTER_SEGMENTED
+                             (per-vertex gather over a vertex-to-(tet, corner) CSR list, deterministic) */
+    double excl_factor;   /* rest-pose exclusion radius in units of dhat (Sec. 5.1: 1.5; default 1.5; 0 = off) */
+    void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = a stream owned by the library */
+    int32_t use_graph;    /* 1 (default) = each time step is replayed from a captured CUDA graph */
+    int32_t candidate_capacity; /* initial candidate-buffer capacity in pairs; <= 0 = automatic */
+} sim_options;
+
+/* Statistics of the last completed time step. */
+typedef struct {
+    int64_t step;          /* number of completed time steps */
+    int32_t iters_done;    /* iterations of the last step (< iters when the eps rule fired) */
+    int32_t n_candidates;  /* contact candidates of the last build */
+    int32_t n_active;      /* active pairs (d < dhat) in the last iteration */
+    int32_t n_rebuilds;    /* candidate builds during the last step */
+    int32_t n_capped;      /* iterations of the last step that took alpha = alpha_upper */
+    int32_t n_surface_tris, n_surface_edges, n_surface_verts;
+    double dE0, dE_last;   /* Delta E of the first and the last iteration */
+} sim_stats;
+
+/* Scalars of the most recent iteration (Algorithm 1). */
+typedef struct {
+    int32_t k;             /* index of the next iteration within the step */
+    int32_t restarted;     /* 1 when the direction was restarted (beta = 0 because g^T p >= 0) */
+    int32_t capped;        /* 1 when alpha = alpha_upper */
+    int32_t n_active;      /* active contact pairs */
+    double beta, gp, pHp, pmax, alpha_bar, alpha_up, alpha, dE, dE0;
+} sim_iter_scalars;
+
+/* Fills *opt with the defaults listed above.  Returns SIM_ERR_INVALID_ARG when opt is NULL. */
+sim_status sim_default_options(sim_options *opt);
+
+/*
+ * Creates a solver for the problem of Sec. 3 (Eqs. 1, E): minimise, per time step of length dt,
+ *   E(x) = 1/2 (x - xt)^T M (x - xt) + dt^2 Psi(x) + kappa sum_{k in C} b(d_k(x)),
+ * with Neo-Hookean Psi, the IPC barrier b (Eq. barrier) of threshold dhat and stiffness kappa over surface
+ * point-triangle and edge-edge pairs (Sec. 3.2).  Host work: D_m^-1, volumes, lumped masses, the surface
+ * (faces used by one tet, their edges and vertices), objects (connected components) and the rest-pose exclusion
+ * of same-object pairs closer than excl_factor * dhat (Sec. 5.1).  Device buffers are allocated here.
+ *   mesh, mat: host descriptions, copied.  opt: NULL = defaults.  out: receives the handle.
+ * Errors: SIM_ERR_INVALID_ARG (null pointer, dt/dhat <= 0, kappa < 0, bad index or volume), SIM_ERR_CUDA,
+ * SIM_ERR_OOM.  On error *out is NULL.
+ */
+sim_status sim_create(const sim_mesh *mesh, const sim_material *mat, double dt, double dhat, double kappa,
+                      const sim_options *opt, sim_handle *out);
+
+/*
+ * Advances n_steps time steps, each one Algorithm 1: prediction xt = x + dt v + dt^2 gravity, kinematic vertices
+ * moved to their targets, `iters` PNCG iterations (constraint set, gradient + Jacobi preconditioner, beta,
+ * direction, p^T H p, step alpha = min(dhat / (2 ||p||), -g^T p / p^T H p), update), then v = (x - x^t) / dt.
+ *   targets: host or device, [n_steps][n_fixed][3] positions of the kinematic vertices (in increasing vertex
+ *            order) at the end of each step; NULL = kinematic vertices stay where they are.
+ * Synchronises the handle's stream before returning.  On a kernel error the failing step is not applied (the
+ * state is the one before it), later steps are skipped, and the error status is returned.
+ */
+sim_status sim_step(sim_handle h, int32_t n_steps, const double *targets);
+
+/* Launches n_steps steps like sim_step but returns without synchronising (errors surface at the next
+   synchronising call).  targets must stay valid until the stream reaches the copy. */
+sim_status sim_step_async(sim_handle h, int32_t n_steps, const double *targets);
+
+/*
+ * Copies the state out.  x_out, v_out: host or device, [n_verts][3], NULL = skip.  stats: host, NULL = skip.
+ * Synchronises.  Reports a pending kernel error.
+ */
+sim_status sim_get_state(sim_handle h, double *x_out, double *v_out, sim_stats *stats);
+
+/* Replaces positions and velocities (checkpoint / resume).  x, v: host or device [n_verts][3], NULL = keep. */
+sim_status sim_set_state(sim_handle h, const double *x, const double *v);
+
+/*
+ * The three phases of sim_step, run eagerly (no graph), for step-by-step inspection:
+ * sim_begin_step: prediction, kinematic targets (targets: host or device [n_fixed][3] or NULL) and the first
+ * candidate build; sim_iterate: n PNCG iterations; sim_end_step: velocity update (synchronises, reports errors).
+ */
+sim_status sim_begin_step(sim_handle h, const double *targets);
+sim_status sim_iterate(sim_handle h, int32_t n);
+sim_status sim_end_step(sim_handle h);
+
+/*
+ * Solver vectors after the most recent iteration, all host or device [n_verts][3], NULL = skip:
+ *   x: current iterate x_k; g: gradient g_k (evaluated at x_{k-1}, kinematic entries zero); P: Jacobi
+ *   preconditioner diag(H)^-1 (1/m_v where diag <= 0, zero on kinematic vertices); p: direction p_k;
+ *   xtilde: the prediction xt.  s: host, NULL = skip.  Synchronises.
+ */
+sim_status sim_get_iterate(sim_handle h, double *x, double *g, double *P, double *p, double *xtilde,
+                           sim_iter_scalars *s);
+
+/*
+ * Overwrites the solver vectors before the next sim_iterate (lock-step comparison): any of x, g, P, p may be
+ * NULL to keep it; k is the iteration index the next iteration takes (0 = first of the step); gPg is
+ * g^T P g of the given g and P (the PR+ denominator; ignored when k = 0).
+ */
+sim_status sim_set_iterate(sim_handle h, const double *x, const double *g, const double *P, const double *p,
+                           int32_t k, double gPg);
+
+/*
+ * Evaluates, with the library's kernels, at arbitrary positions (candidates rebuilt at x, active set d < dhat):
+ *   sim_eval_gradient: g = dE/dx and diag(H) (Eqs. E, Hessian; unmasked), host or device [n_verts][3].
+ *   sim_eval_pHp: *out = p^T H p at x (Eqs. Hessian, 12, 13; frozen closest-point coefficients).
+ *   sim_eval_energy: *out = E(x) with the given prediction xtilde; parts (host double[4], NULL = skip) =
+ *     {inertia, dt^2 Psi, kappa sum_pairs b, kappa sum_plane b}.
+ * These calls use the handle's iteration buffers: run them between steps, not inside a begin/end pair whose
+ * iterate you still need.  Synchronise; report kernel errors.
+ */
+sim_status sim_eval_gradient(sim_handle h, const double *x, const double *xtilde, double *g, double *diag);
+sim_status sim_eval_pHp(sim_handle h, const double *x, const double *p, double *out);
+sim_status sim_eval_energy(sim_handle h, const double *x, const double *xtilde, double *out, double *parts);
+
+/*
+ * Active contact pairs of the most recent gradient evaluation: rows (type, v0, v1, v2, v3) with type 0 =
+ * point-triangle (v0 the point) and 1 = edge-edge (v0-v1, v2-v3), and their distances.  idx: host [max][5],
+ * d: host [max] (NULL = skip).  *count receives the number of pairs (may exceed max).  Synchronises.
+ */
+sim_status sim_get_contacts(sim_handle h, int32_t *idx, double *d, int32_t max, int32_t *count);
+
+/*
+ * Contact candidates of the most recent build, rows (type, v0, v1, v2, v3) as in sim_get_contacts.
+ * idx: host [max][5].  *count receives the number of candidates.  Synchronises.
+ */
+sim_status sim_get_candidates(sim_handle h, int32_t *idx, int32_t max, int32_t *count);
+
+/*
+ * Per-iteration trace of the last step: rows {beta, g^T p, p^T H p, pmax, alpha, Delta E, n_active, capped},
+ * host [max_iters][8].  *n receives the number of rows written.  Synchronises.
+ */
+sim_status sim_get_trace(sim_handle h, double *buf, int32_t max_iters, int32_t *n);
+
+/*
+ * Advances one time step like sim_step (targets as there, for this one step) and times it kernel by kernel: the
+ * step is replayed from a CUDA graph with an event-record node before and after every kernel, so the times are
+ * measured on the GPU.  ms: host [n_kernels], milliseconds spent in each kernel over the step (all its launches);
+ * launches: host [n_kernels] or NULL, launch counts; kernel i is named by sim_kernel_name(i).  Synchronises.
+ */
+sim_status sim_profile_step(sim_handle h, const double *targets, float *ms, int32_t *launches, int32_t n_kernels);
+int32_t sim_kernel_count(void);
+const char *sim_kernel_name(int32_t i);
+
+/* Sizes: out[0..5] = n_verts, n_tets, n_surface_tris, n_surface_edges, n_surface_verts, n_excluded_pairs. */
+sim_status sim_get_sizes(sim_handle h, int32_t *out);
+
+/* Releases the handle and its device buffers (synchronises its stream first).  NULL is ignored. */
+void sim_destroy(sim_handle h);
+
+/* One-line description of the last failure of h (or of the last failed sim_create when h is NULL). */
+const char *sim_last_error(sim_handle h);
+
+/* Name of a status code. */
+const char *sim_status_string(sim_status s);
+
+/* ABI version of the library (incremented on incompatible changes). */
+int32_t sim_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNCG_H */

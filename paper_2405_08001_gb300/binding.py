@@ -1,0 +1,373 @@
+"""ctypes binding of libpncg.so with the names of the C ABI in include/pncg.h (argument marshalling only).
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA device); both must be C-contiguous and of the
+documented dtype.  Every solver step runs in the library's CUDA kernels: there is no Python or CPU compute path,
+and loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpncg.so")
+
+SIM_OK, SIM_ERR_INVALID_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_INVERTED, SIM_ERR_PENETRATION, \
+    SIM_ERR_NONFINITE, SIM_ERR_TIMEOUT, SIM_ERR_CAPACITY = range(9)
+SIM_FP64, SIM_FP32_MIXED = 0, 1
+SIM_BETA_PR_PLUS, SIM_BETA_DK = 0, 1
+SIM_PNORM_VERTEX2, SIM_PNORM_COMPONENT_INF = 0, 1
+SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED = 0, 1
+TRACE_COLUMNS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "n_active", "capped")
+
+
+class sim_mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_x", C.c_void_p), ("tets", C.c_void_p),
+                ("x0", C.c_void_p), ("v0", C.c_void_p), ("fixed", C.c_void_p)]
+
+
+class sim_material(C.Structure):
+    _fields_ = [("density", C.c_double), ("youngs", C.c_double), ("poisson", C.c_double),
+                ("youngs_per_tet", C.c_void_p)]
+
+
+class sim_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("beta", C.c_int32), ("iters", C.c_int32), ("eps", C.c_double),
+                ("gravity", C.c_double * 3), ("has_plane", C.c_int32), ("plane_n", C.c_double * 3),
+                ("plane_o", C.c_double), ("pad_r", C.c_double), ("pnorm", C.c_int32), ("scatter", C.c_int32),
+                ("excl_factor", C.c_double), ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
+                ("candidate_capacity", C.c_int32)]
+
+
+class sim_stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("iters_done", C.c_int32), ("n_candidates", C.c_int32),
+                ("n_active", C.c_int32), ("n_rebuilds", C.c_int32), ("n_capped", C.c_int32),
+                ("n_surface_tris", C.c_int32), ("n_surface_edges", C.c_int32), ("n_surface_verts", C.c_int32),
+                ("dE0", C.c_double), ("dE_last", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sim_iter_scalars(C.Structure):
+    _fields_ = [("k", C.c_int32), ("restarted", C.c_int32), ("capped", C.c_int32), ("n_active", C.c_int32),
+                ("beta", C.c_double), ("gp", C.c_double), ("pHp", C.c_double), ("pmax", C.c_double),
+                ("alpha_bar", C.c_double), ("alpha_up", C.c_double), ("alpha", C.c_double), ("dE", C.c_double),
+                ("dE0", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{_status_name(status)}: {msg}")
+
+
+_lib = None
+
+
+def load():
+    """Loads libpncg.so (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2405_08001_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, D = C.c_void_p, C.c_int32, C.c_double
+    sigs = {
+        "sim_abi_version": (I32, []),
+        "sim_status_string": (C.c_char_p, [C.c_int]),
+        "sim_default_options": (C.c_int, [P]),
+        "sim_create": (C.c_int, [P, P, D, D, D, P, P]),
+        "sim_step": (C.c_int, [P, I32, P]),
+        "sim_step_async": (C.c_int, [P, I32, P]),
+        "sim_get_state": (C.c_int, [P, P, P, P]),
+        "sim_set_state": (C.c_int, [P, P, P]),
+        "sim_begin_step": (C.c_int, [P, P]),
+        "sim_iterate": (C.c_int, [P, I32]),
+        "sim_end_step": (C.c_int, [P]),
+        "sim_get_iterate": (C.c_int, [P, P, P, P, P, P, P]),
+        "sim_set_iterate": (C.c_int, [P, P, P, P, P, I32, D]),
+        "sim_eval_gradient": (C.c_int, [P, P, P, P, P]),
+        "sim_eval_pHp": (C.c_int, [P, P, P, P]),
+        "sim_eval_energy": (C.c_int, [P, P, P, P, P]),
+        "sim_get_contacts": (C.c_int, [P, P, P, I32, P]),
+        "sim_get_candidates": (C.c_int, [P, P, I32, P]),
+        "sim_get_trace": (C.c_int, [P, P, I32, P]),
+        "sim_profile_step": (C.c_int, [P, P, P, P, I32]),
+        "sim_kernel_count": (I32, []),
+        "sim_kernel_name": (C.c_char_p, [I32]),
+        "sim_get_sizes": (C.c_int, [P, P]),
+        "sim_destroy": (None, [P]),
+        "sim_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_name(st):
+    try:
+        return load().sim_status_string(st).decode()
+    except Exception:
+        return f"status {st}"
+
+
+def _check(st, h=None):
+    if st != SIM_OK:
+        raise SimError(st, load().sim_last_error(h).decode())
+
+
+def _ptr(a, dtype=np.float64, n=None):
+    """Address of a C-contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):   # torch tensor
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        if n is not None and a.numel() < n:
+            raise ValueError(f"tensor has {a.numel()} elements, {n} needed")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if n is not None and arr.size < n:
+        raise ValueError(f"array has {arr.size} elements, {n} needed")
+    return arr.ctypes.data, arr
+
+
+def sim_default_options() -> sim_options:
+    o = sim_options()
+    _check(load().sim_default_options(C.byref(o)))
+    return o
+
+
+def sim_create(rest_x, tets, *, density, youngs, poisson, dt, dhat, kappa, x0=None, v0=None, fixed=None,
+               youngs_per_tet=None, options: sim_options | None = None):
+    """sim_create with host arrays; returns the opaque handle (a c_void_p value)."""
+    lib = load()
+    rx = np.ascontiguousarray(rest_x, dtype=np.float64).reshape(-1, 3)
+    nv = rx.shape[0]
+    tt = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    keep = [rx, tt]
+    m = sim_mesh()
+    m.n_verts, m.n_tets = nv, tt.shape[0]
+    m.rest_x, m.tets = rx.ctypes.data, tt.ctypes.data
+    for name, arr, dt_ in (("x0", x0, np.float64), ("v0", v0, np.float64), ("fixed", fixed, np.uint8)):
+        if arr is not None:
+            a = np.ascontiguousarray(arr, dtype=dt_)
+            keep.append(a)
+            setattr(m, name, a.ctypes.data)
+    mat = sim_material()
+    mat.density, mat.youngs, mat.poisson = density, youngs, poisson
+    if youngs_per_tet is not None:
+        e = np.ascontiguousarray(youngs_per_tet, dtype=np.float64)
+        keep.append(e)
+        mat.youngs_per_tet = e.ctypes.data
+    h = C.c_void_p()
+    st = lib.sim_create(C.byref(m), C.byref(mat), float(dt), float(dhat), float(kappa),
+                        None if options is None else C.byref(options), C.byref(h))
+    _check(st)
+    return h.value
+
+
+def sim_step(h, n_steps: int = 1, targets=None):
+    p, keep = _ptr(targets)
+    _check(load().sim_step(h, int(n_steps), p), h)
+
+
+def sim_step_async(h, n_steps: int = 1, targets=None):
+    p, keep = _ptr(targets)
+    _check(load().sim_step_async(h, int(n_steps), p), h)
+    return keep
+
+
+def sim_get_sizes(h):
+    out = np.zeros(6, np.int32)
+    _check(load().sim_get_sizes(h, out.ctypes.data), h)
+    return dict(zip(["n_verts", "n_tets", "n_surface_tris", "n_surface_edges", "n_surface_verts", "n_excluded"],
+                    out.tolist()))
+
+
+def _out(a, nv):
+    if a is None:
+        a = np.zeros((nv, 3))
+    p, arr = _ptr(a, n=3 * nv)
+    return p, arr
+
+
+def sim_get_state(h, x_out=None, v_out=None, want_x=True, want_v=True):
+    nv = sim_get_sizes(h)["n_verts"]
+    px, x = _out(x_out, nv) if want_x else (None, None)
+    pv, v = _out(v_out, nv) if want_v else (None, None)
+    st = sim_stats()
+    _check(load().sim_get_state(h, px, pv, C.byref(st)), h)
+    return x, v, st.as_dict()
+
+
+def sim_set_state(h, x=None, v=None):
+    px, kx = _ptr(x)
+    pv, kv = _ptr(v)
+    _check(load().sim_set_state(h, px, pv), h)
+
+
+def sim_begin_step(h, targets=None):
+    p, keep = _ptr(targets)
+    _check(load().sim_begin_step(h, p), h)
+
+
+def sim_iterate(h, n: int = 1):
+    _check(load().sim_iterate(h, int(n)), h)
+
+
+def sim_end_step(h):
+    _check(load().sim_end_step(h), h)
+
+
+def sim_get_iterate(h):
+    """(x, g, P, p, xtilde, scalars) after the most recent iteration, as numpy arrays."""
+    nv = sim_get_sizes(h)["n_verts"]
+    arrs = [np.zeros((nv, 3)) for _ in range(5)]
+    s = sim_iter_scalars()
+    _check(load().sim_get_iterate(h, *[a.ctypes.data for a in arrs], C.byref(s)), h)
+    return (*arrs, s.as_dict())
+
+
+def sim_set_iterate(h, x=None, g=None, P=None, p=None, k: int = 0, gPg: float = 0.0):
+    ptrs = [_ptr(a) for a in (x, g, P, p)]
+    _check(load().sim_set_iterate(h, *[q[0] for q in ptrs], int(k), float(gPg)), h)
+
+
+def sim_eval_gradient(h, x, xtilde):
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x, n=3 * nv)
+    pt, kt = _ptr(xtilde, n=3 * nv)
+    g = np.zeros((nv, 3))
+    d = np.zeros((nv, 3))
+    _check(load().sim_eval_gradient(h, px, pt, g.ctypes.data, d.ctypes.data), h)
+    return g, d
+
+
+def sim_eval_pHp(h, x, p):
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x, n=3 * nv)
+    pp, kp = _ptr(p, n=3 * nv)
+    out = C.c_double()
+    _check(load().sim_eval_pHp(h, px, pp, C.byref(out)), h)
+    return out.value
+
+
+def sim_eval_energy(h, x, xtilde):
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x, n=3 * nv)
+    pt, kt = _ptr(xtilde, n=3 * nv)
+    out = C.c_double()
+    parts = np.zeros(4)
+    _check(load().sim_eval_energy(h, px, pt, C.byref(out), parts.ctypes.data), h)
+    return out.value, parts
+
+
+def sim_get_contacts(h):
+    cnt = C.c_int32()
+    _check(load().sim_get_contacts(h, None, None, 0, C.byref(cnt)), h)
+    n = cnt.value
+    idx = np.zeros((max(n, 1), 5), np.int32)
+    d = np.zeros(max(n, 1))
+    _check(load().sim_get_contacts(h, idx.ctypes.data, d.ctypes.data, n, C.byref(cnt)), h)
+    return idx[:n], d[:n]
+
+
+def sim_get_candidates(h):
+    cnt = C.c_int32()
+    _check(load().sim_get_candidates(h, None, 0, C.byref(cnt)), h)
+    n = cnt.value
+    idx = np.zeros((max(n, 1), 5), np.int32)
+    _check(load().sim_get_candidates(h, idx.ctypes.data, n, C.byref(cnt)), h)
+    return idx[:n]
+
+
+def sim_get_trace(h, max_iters: int = 4096):
+    buf = np.zeros((max_iters, len(TRACE_COLUMNS)))
+    n = C.c_int32()
+    _check(load().sim_get_trace(h, buf.ctypes.data, max_iters, C.byref(n)), h)
+    return buf[:n.value]
+
+
+def sim_kernel_names():
+    lib = load()
+    return [lib.sim_kernel_name(i).decode() for i in range(lib.sim_kernel_count())]
+
+
+def sim_profile_step(h, targets=None):
+    """One time step timed kernel by kernel on the GPU: {kernel: (milliseconds over the step, launches)}."""
+    names = sim_kernel_names()
+    ms = np.zeros(len(names), np.float32)
+    n = np.zeros(len(names), np.int32)
+    p, keep = _ptr(targets)
+    _check(load().sim_profile_step(h, p, ms.ctypes.data, n.ctypes.data, len(names)), h)
+    return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+
+
+def sim_destroy(h):
+    if h:
+        load().sim_destroy(h)
+
+
+def options_for(scene, precision=SIM_FP64, **kw) -> sim_options:
+    """Default options filled from a scenes.Scene (gravity, plane, iterations), overridden by keyword arguments."""
+    o = sim_default_options()
+    o.precision = precision
+    o.iters = scene.iters
+    o.gravity[:] = list(scene.gravity)
+    if scene.plane is not None:
+        o.has_plane = 1
+        o.plane_n[:] = list(scene.plane[0])
+        o.plane_o = float(scene.plane[1])
+    for k, v in kw.items():
+        if k == "gravity":
+            o.gravity[:] = list(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Sim:
+    """Owning wrapper of a handle: Sim(scene, precision=..., **options)."""
+
+    def __init__(self, scene, precision=SIM_FP64, options: sim_options | None = None, **kw):
+        self.scene = scene
+        self.options = options if options is not None else options_for(scene, precision, **kw)
+        self.h = sim_create(scene.rest_x, scene.tets, density=scene.density, youngs=scene.youngs,
+                            poisson=scene.poisson, dt=scene.dt, dhat=scene.dhat, kappa=scene.kappa, x0=scene.x0,
+                            v0=scene.v0, fixed=scene.fixed, youngs_per_tet=scene.youngs_per_tet,
+                            options=self.options)
+        self.nv = scene.n_verts
+
+    def close(self):
+        if getattr(self, "h", None):
+            sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1, targets=None):
+        sim_step(self.h, n, targets)
+
+    def state(self):
+        return sim_get_state(self.h)
+
+    def sizes(self):
+        return sim_get_sizes(self.h)

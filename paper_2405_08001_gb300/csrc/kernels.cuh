@@ -1,0 +1,910 @@
+// PNCG iteration kernels (Algorithm 1), templated on the element / barrier arithmetic type R:
+//   R = double: the plain FP64 form;  R = float: FP32 element and barrier arithmetic on double vertex differences,
+//   every reduction accumulated in double, the contact distance re-evaluated in double when d < 1e-3 dhat.
+// Vertex state (x, xt, x~, v) is always double4_32a (w: unused / mass).  g, diag and p are R4 vectors.  The FP32 form
+// also keeps float-float copies of the current and rest positions, so that its element kernels form vertex
+// differences to ~2^-46 relative accuracy without FP64 arithmetic (FP64 throughput is low on this GPU).
+#pragma once
+
+#include "common.cuh"
+#include "ffloat.cuh"
+#include "geometry.cuh"
+
+namespace pncg {
+
+constexpr int VB = 128;   // threads per block, vertex kernels (148 blocks for the 18.8K-vertex bar: every SM busy)
+constexpr int EB = 256;   // threads per block, element / pair kernels
+
+template <typename R> struct Dev {
+    typedef typename V4<R>::T R4;
+    int nv, nt, nfix;
+    double4_32a *x, *xt, *xtil, *v, *xb;   // xtil.w = mass (free vertex) or -1 (kinematic)
+    float4 *xh, *xl;                   // FP32 form: float-float copy of x (hi, lo); null in the FP64 form
+    float4 *xbh;                       // FP32 form: xh at the last candidate build (displacement check)
+    const float4 *Xh, *Xl;             // FP32 form: float-float rest positions
+    R4 *g[2], *dg[2];                  // ping-pong by iteration parity; g.w = plane curvature kappa b'', dg.w = xtil.w
+    R4 *p;
+    const double *mass;
+    const int *fix_slot;               // [nv] target slot or -1
+    const double *tgt;                 // staging [nfix][3] targets of the current step
+    int has_tgt;
+    // tets
+    const int4 *tet;
+    const R *Dm;                       // [9][nt] row-major D_m^-1 entries
+    const R *hv;                       // [nt] h^2 V_e
+    const R *escale;                   // [nt] E_e / E or nullptr
+    R mu, lam;
+    // contacts
+    const int4 *cand;                  // candidates: PT (v, t0, t1, t2), EE (-1 - a0, a1, b0, b1)
+    int cand_cap;
+    Active<R> *act;
+    // constants
+    double h, dhat, kappa, eps, pad_r;
+    double grav[3];
+    int has_plane;
+    double pn[3], po;
+    int beta_rule, pnorm, iters;
+    // segmented scatter: per (tet, corner) contributions [6][4 nt] and the vertex CSR
+    R *contrib;
+    const int *v2c_off, *v2c;          // v2c: 4*tet + corner
+    int segmented;
+    Ctrl *ctrl;
+    double *part;                      // reduction partials
+    double *trace;                     // [iters][TRACE_COLS]
+};
+
+template <typename R> __device__ inline void atomic_add4(typename V4<R>::T *p, R a, R b, R c);
+template <> __device__ inline void atomic_add4<float>(float4 *p, float a, float b, float c)
+{
+    atomicAdd(p, make_float4(a, b, c, 0.0f));
+}
+template <> __device__ inline void atomic_add4<double>(double4_32a *p, double a, double b, double c)
+{
+    atomicAdd(&p->x, a);
+    atomicAdd(&p->y, b);
+    atomicAdd(&p->z, c);
+}
+
+__device__ inline void flag_error(Ctrl *c, uint32_t bits) { atomicOr(&c->err, bits); }
+
+// Writes vertex i's position (and, in the FP32 form, its float-float copy).
+template <typename R> __device__ inline void put_x(const Dev<R> &D, int i, const double4_32a &X)
+{
+    D.x[i] = X;
+    if constexpr (sizeof(R) == 4) {
+        const ffl a = ff_split(X.x), b = ff_split(X.y), c = ff_split(X.z);
+        D.xh[i] = make_float4(a.h, b.h, c.h, 0.0f);
+        D.xl[i] = make_float4(a.l, b.l, c.l, 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------------------------------ vertex initialisation
+
+// g = M (x - x~) and diag = m (Eq. E inertia term) plus the vertex / half-space barrier, written (not added) to
+// the accumulators of parity `par`.  Kinematic vertices (xtil.w < 0) get zero inertia.
+template <typename R>
+__device__ inline void init_vertex(const Dev<R> &D, int i, const double4_32a &X, const double4_32a &XT, int par)
+{
+    const double m = XT.w;
+    const double mm = m > 0.0 ? m : 0.0;
+    double gx, gy, gz;
+    if constexpr (sizeof(R) == 4) {   // the difference in double, the product in float (the value is rounded anyway)
+        gx = float(mm) * float(X.x - XT.x); gy = float(mm) * float(X.y - XT.y); gz = float(mm) * float(X.z - XT.z);
+    } else {
+        gx = mm * (X.x - XT.x); gy = mm * (X.y - XT.y); gz = mm * (X.z - XT.z);
+    }
+    double dx = mm, dy = mm, dz = mm, curv = 0.0;
+    if (D.has_plane) {
+        double d = D.pn[0] * X.x + D.pn[1] * X.y + D.pn[2] * X.z - D.po;
+        if (d < D.dhat) {
+            if (!(d > 0.0)) {
+                flag_error(D.ctrl, ERR_PENETRATION);
+            } else {
+                double b1, b2;
+                barrier_d12<double>(d, D.dhat, b1, b2);
+                double k1 = D.kappa * b1, k2 = D.kappa * b2;
+                gx += k1 * D.pn[0]; gy += k1 * D.pn[1]; gz += k1 * D.pn[2];
+                dx += k2 * D.pn[0] * D.pn[0]; dy += k2 * D.pn[1] * D.pn[1]; dz += k2 * D.pn[2] * D.pn[2];
+                curv = k2;
+            }
+        }
+    }
+    D.g[par][i] = mk4<R>(R(gx), R(gy), R(gz), R(curv));
+    D.dg[par][i] = mk4<R>(R(dx), R(dy), R(dz), R(m));
+}
+
+__device__ inline double dist2(const double4_32a &a, const double4_32a &b)
+{
+    double x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
+    return x * x + y * y + z * z;
+}
+
+// Squared displacement of vertex i since the last candidate build (float copies in the FP32 form).
+template <typename R> __device__ inline double disp2(const Dev<R> &D, int i, const double4_32a &X)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float4 a = D.xh[i], b = D.xbh[i];
+        const float x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
+        return (double)(x * x + y * y + z * z);
+    } else {
+        return dist2(X, D.xb[i]);
+    }
+}
+
+// Displacement bookkeeping shared by k_predict and k_update: when some vertex has moved pad_r / 2 since the last
+// candidate build, request a rebuild (contacts can then not be missed: d changes by at most twice the largest
+// vertex displacement).
+template <typename R> __device__ inline void request_rebuild_if(const Dev<R> &D, double maxd2)
+{
+    double lim = 0.5 * D.pad_r * (1.0 - 1e-4);   // margin for the float displacement of the FP32 form
+    if (maxd2 >= lim * lim && !D.ctrl->rebuild) {
+        D.ctrl->cell_bits = 0u;
+        D.ctrl->rebuild = 1;
+    }
+}
+
+// a0: x^t = x; x~ = x + h v + h^2 gravity; kinematic vertices jump to their targets; init of iteration 0.
+template <typename R>
+__global__ void __launch_bounds__(VB) k_predict(Dev<R> D)
+{
+    __shared__ double sh[32 * 1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool skip = D.ctrl->err != 0u;
+    double md2 = 0.0;
+    if (i < D.nv && !skip) {
+        double4_32a X = D.x[i], V = D.v[i];
+        D.xt[i] = X;
+        const int slot = D.fix_slot[i];
+        double4_32a XT;
+        if (slot >= 0) {
+            if (D.has_tgt) {
+                X.x = D.tgt[3 * slot]; X.y = D.tgt[3 * slot + 1]; X.z = D.tgt[3 * slot + 2];
+            }
+            XT = make_double4_32a(X.x, X.y, X.z, -1.0);
+            put_x<R>(D, i, X);
+        } else {
+            const double h = D.h, h2 = D.h * D.h;
+            XT = make_double4_32a(X.x + h * V.x + h2 * D.grav[0], X.y + h * V.y + h2 * D.grav[1],
+                              X.z + h * V.z + h2 * D.grav[2], D.mass[i]);
+        }
+        D.xtil[i] = XT;
+        init_vertex<R>(D, i, X, XT, 0);
+        md2 = disp2<R>(D, i, X);
+    }
+    double mx = block_max(md2, sh);
+    double v1[1] = {mx};
+    if (publish_partials<1>(v1, D.part, &D.ctrl->ticket[TK_PREDICT])) {
+        double m = finish_max(D.part, 0, sh);
+        if (threadIdx.x == 0) {
+            Ctrl *c = D.ctrl;
+            c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->iters_done = 0; c->converged = 0;
+            c->n_active = 0; c->dE0 = 0.0; c->gPg_prev = 0.0;
+            if (!skip) request_rebuild_if(D, m);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------ a2-a3: gradient + diag
+
+// Per-tet Neo-Hookean quantities (Sec. 3.1): F = Ds Dm^-1, cofactor columns (gradient g3 of I3), I3 = det F.
+template <typename R> struct TetF {
+    R F[3][3];
+    R cf[3][3];   // cf[a][b] = d det / d F_ab (columns f1 x f2, f2 x f0, f0 x f1)
+    R J;
+    R w[3][3];    // rows of Dm^-1 (vertex weights of x1, x2, x3; x0 gets minus their sum)
+};
+
+__device__ inline float comp(const float4 &v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
+
+// Edge vectors Ds[a][c] = x_{c+1,a} - x_{0,a}: from the double positions in the FP64 form, from the float-float
+// positions (rounded once to float) in the FP32 form.
+template <typename R> __device__ inline void tet_ds(const Dev<R> &D, const int4 &tv, R ds[3][3])
+{
+    if constexpr (sizeof(R) == 8) {
+        const double4_32a X0 = D.x[tv.x], X1 = D.x[tv.y], X2 = D.x[tv.z], X3 = D.x[tv.w];
+        ds[0][0] = X1.x - X0.x; ds[1][0] = X1.y - X0.y; ds[2][0] = X1.z - X0.z;
+        ds[0][1] = X2.x - X0.x; ds[1][1] = X2.y - X0.y; ds[2][1] = X2.z - X0.z;
+        ds[0][2] = X3.x - X0.x; ds[1][2] = X3.y - X0.y; ds[2][2] = X3.z - X0.z;
+    } else {
+        const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+        const float4 h0 = D.xh[vid[0]], l0 = D.xl[vid[0]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 h = D.xh[vid[c + 1]], l = D.xl[vid[c + 1]];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ds[a][c] = ff_val(ff_sub(comp(h, a), comp(l, a), comp(h0, a), comp(l0, a)));
+        }
+    }
+}
+
+template <typename R> __device__ inline void load_w(const Dev<R> &D, int e, R w[3][3])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[r][c] = D.Dm[(3 * r + c) * D.nt + e];
+}
+
+template <typename R> __device__ inline void tet_F_from(const R ds[3][3], TetF<R> &T)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) T.F[a][b] = ds[a][0] * T.w[0][b] + ds[a][1] * T.w[1][b] + ds[a][2] * T.w[2][b];
+    T.cf[0][0] = T.F[1][1] * T.F[2][2] - T.F[2][1] * T.F[1][2];
+    T.cf[1][0] = T.F[2][1] * T.F[0][2] - T.F[0][1] * T.F[2][2];
+    T.cf[2][0] = T.F[0][1] * T.F[1][2] - T.F[1][1] * T.F[0][2];
+    T.cf[0][1] = T.F[1][2] * T.F[2][0] - T.F[2][2] * T.F[1][0];
+    T.cf[1][1] = T.F[2][2] * T.F[0][0] - T.F[0][2] * T.F[2][0];
+    T.cf[2][1] = T.F[0][2] * T.F[1][0] - T.F[1][2] * T.F[0][0];
+    T.cf[0][2] = T.F[1][0] * T.F[2][1] - T.F[2][0] * T.F[1][1];
+    T.cf[1][2] = T.F[2][0] * T.F[0][1] - T.F[0][0] * T.F[2][1];
+    T.cf[2][2] = T.F[0][0] * T.F[1][1] - T.F[1][0] * T.F[0][1];
+    T.J = T.F[0][0] * T.cf[0][0] + T.F[1][0] * T.cf[1][0] + T.F[2][0] * T.cf[2][0];
+}
+
+template <typename R> __device__ inline void tet_F(const Dev<R> &D, int e, const int4 &tv, TetF<R> &T)
+{
+    R ds[3][3];
+    tet_ds<R>(D, tv, ds);
+    load_w<R>(D, e, T.w);
+    tet_F_from<R>(ds, T);
+}
+
+template <typename R> __device__ inline void tet_material(const Dev<R> &D, int e, R &mu, R &lam)
+{
+    mu = D.mu;
+    lam = D.lam;
+    if (D.escale) { R s = D.escale[e]; mu *= s; lam *= s; }
+}
+
+// First Piola-Kirchhoff stress of the FP32 form, evaluated from the metric change so that it stays accurate for
+// small strains under any rotation.  With C = F^T F and the Neo-Hookean density of Sec. 3.1 written in C,
+//   P = F C^-1 (mu (C - I) + lambda log J I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
+// which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly.  The metric change G = Ds^T Ds - Dm^T Dm is
+// accumulated in float-float from the float-float current and rest positions, so that rounding never acts on the
+// O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the entries of C - I.
+// Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
+__device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 &tv, TetF<float> &T, float P[3][3],
+                                         float &Psi33)
+{
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    float4 xh[4], xl[4], Xh[4], Xl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { xh[k] = D.xh[vid[k]]; xl[k] = D.xl[vid[k]]; Xh[k] = D.Xh[vid[k]]; Xl[k] = D.Xl[vid[k]]; }
+    ffl ds[3][3], dm[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ds[a][c] = ff_sub(comp(xh[c + 1], a), comp(xl[c + 1], a), comp(xh[0], a), comp(xl[0], a));
+            dm[a][c] = ff_sub(comp(Xh[c + 1], a), comp(Xl[c + 1], a), comp(Xh[0], a), comp(Xl[0], a));
+        }
+    float G[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            ffacc acc;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc.add_prod(ds[a][i], ds[a][j], 1.0f);
+                acc.add_prod(dm[a][i], dm[a][j], -1.0f);
+            }
+            G[i][j] = G[j][i] = acc.value();
+        }
+    float dsf[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dsf[a][c] = ff_val(ds[a][c]);
+    load_w<float>(D, e, T.w);
+    tet_F_from<float>(dsf, T);
+    if (!(T.J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
+    // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc)
+    float GW[3][3], A[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) GW[i][b] = G[i][0] * T.w[0][b] + G[i][1] * T.w[1][b] + G[i][2] * T.w[2][b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) A[a][b] = A[b][a] = T.w[0][a] * GW[0][b] + T.w[1][a] * GW[1][b] + T.w[2][a] * GW[2][b];
+    const float m01 = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+    const float m02 = A[0][0] * A[2][2] - A[0][2] * A[0][2];
+    const float m12 = A[1][1] * A[2][2] - A[1][2] * A[1][2];
+    const float detA = A[0][0] * m12 - A[0][1] * (A[0][1] * A[2][2] - A[1][2] * A[0][2]) +
+                       A[0][2] * (A[0][1] * A[1][2] - A[1][1] * A[0][2]);
+    const float dC = (A[0][0] + A[1][1] + A[2][2]) + (m01 + m02 + m12) + detA;   // det C - 1
+    const float detC = 1.0f + dC;
+    const float L = 0.5f * log1pf(dC);                                             // log J
+    float mu, lam;
+    tet_material<float>(D, e, mu, lam);
+    // C^-1 = cof(C) / det C (C symmetric)
+    const float c00 = 1.0f + A[0][0], c11 = 1.0f + A[1][1], c22 = 1.0f + A[2][2];
+    const float ic = 1.0f / detC;
+    float Ci[3][3];
+    Ci[0][0] = (c11 * c22 - A[1][2] * A[1][2]) * ic;
+    Ci[1][1] = (c00 * c22 - A[0][2] * A[0][2]) * ic;
+    Ci[2][2] = (c00 * c11 - A[0][1] * A[0][1]) * ic;
+    Ci[0][1] = Ci[1][0] = (A[0][2] * A[1][2] - A[0][1] * c22) * ic;
+    Ci[0][2] = Ci[2][0] = (A[0][1] * A[1][2] - A[0][2] * c11) * ic;
+    Ci[1][2] = Ci[2][1] = (A[0][1] * A[0][2] - A[1][2] * c00) * ic;
+    float M[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) M[a][b] = mu * A[a][b] + (a == b ? lam * L : 0.0f);
+    float S[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) S[a][b] = Ci[a][0] * M[0][b] + Ci[a][1] * M[1][b] + Ci[a][2] * M[2][b];
+    const float sc = D.hv[e];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P[a][b] = sc * (T.F[a][0] * S[0][b] + T.F[a][1] * S[1][b] + T.F[a][2] * S[2][b]);
+    Psi33 = (mu + lam * (1.0f - L)) / detC;
+    return true;
+}
+
+// Element gradient and Jacobi diagonal (Sec. 3.1 split; NH has Psi_22 = 0 and the H3 term has a zero
+// diagonal, so diag_i[a] = h^2 V (mu |w_i|^2 + Psi_33 (cof(F) w_i)_a^2)).
+template <typename R>
+__device__ inline void tet_grad(const Dev<R> &D, int e, int par)
+{
+    const int4 tv = D.tet[e];
+    TetF<R> T;
+    R P[3][3], Psi33, mu, lam;
+    const R sc = D.hv[e];
+    if constexpr (sizeof(R) == 4) {
+        if (!tet_stress_metric(D, e, tv, T, P, Psi33)) return;
+        tet_material<R>(D, e, mu, lam);
+    } else {
+        tet_F<R>(D, e, tv, T);
+        if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return; }
+        tet_material<R>(D, e, mu, lam);
+        const R L = log(T.J);
+        const R Psi3 = (lam * L - mu) / T.J;
+        Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) P[a][b] = sc * (mu * T.F[a][b] + Psi3 * T.cf[a][b]);
+    }
+    R gv[4][3], dv[4][3];
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+        const R *w = T.w[i - 1];
+        const R ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gv[i][a] = P[a][0] * w[0] + P[a][1] * w[1] + P[a][2] * w[2];
+            const R cw = T.cf[a][0] * w[0] + T.cf[a][1] * w[1] + T.cf[a][2] * w[2];
+            dv[i][a] = sc * (mu * ww + Psi33 * cw * cw);
+        }
+    }
+    {
+        R w0[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) w0[b] = -(T.w[0][b] + T.w[1][b] + T.w[2][b]);
+        const R ww = w0[0] * w0[0] + w0[1] * w0[1] + w0[2] * w0[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gv[0][a] = -(gv[1][a] + gv[2][a] + gv[3][a]);
+            const R cw = T.cf[a][0] * w0[0] + T.cf[a][1] * w0[1] + T.cf[a][2] * w0[2];
+            dv[0][a] = sc * (mu * ww + Psi33 * cw * cw);
+        }
+    }
+    if (D.segmented) {
+        const int q0 = 4 * e;
+        const int n4 = 4 * D.nt;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                D.contrib[a * n4 + q0 + i] = gv[i][a];
+                D.contrib[(3 + a) * n4 + q0 + i] = dv[i][a];
+            }
+        return;
+    }
+    const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        atomic_add4<R>(&D.g[par][vid[i]], gv[i][0], gv[i][1], gv[i][2]);
+        atomic_add4<R>(&D.dg[par][vid[i]], dv[i][0], dv[i][1], dv[i][2]);
+    }
+}
+
+// Closest-point coefficients and t of a candidate.  Relative coordinates come from the double positions (FP64
+// form, and the FP32 form's double re-evaluation) or from the float-float positions (FP32 form).
+template <typename R>
+__device__ inline R pair_geom(bool ee, const double4_32a &X0, const double4_32a &X1, const double4_32a &X2, const double4_32a &X3,
+                              R c[4], v3<R> &t)
+{
+    if (!ee) {
+        return pt_coeffs<R>(rel<R>(X0.x, X0.y, X0.z, X1.x, X1.y, X1.z), rel<R>(X2.x, X2.y, X2.z, X1.x, X1.y, X1.z),
+                            rel<R>(X3.x, X3.y, X3.z, X1.x, X1.y, X1.z), c, t);
+    }
+    return ee_coeffs<R>(rel<R>(X0.x, X0.y, X0.z, X2.x, X2.y, X2.z), rel<R>(X1.x, X1.y, X1.z, X2.x, X2.y, X2.z),
+                        rel<R>(X3.x, X3.y, X3.z, X2.x, X2.y, X2.z), c, t);
+}
+
+__device__ inline v3<float> rel_ff(const Dev<float> &D, int a, int b)
+{
+    const float4 ha = D.xh[a], la = D.xl[a], hb = D.xh[b], lb = D.xl[b];
+    return mkv(ff_val(ff_sub(ha.x, la.x, hb.x, lb.x)), ff_val(ff_sub(ha.y, la.y, hb.y, lb.y)),
+               ff_val(ff_sub(ha.z, la.z, hb.z, lb.z)));
+}
+
+__device__ inline float pair_geom_ff(const Dev<float> &D, bool ee, const int4 &v, float c[4], v3<float> &t)
+{
+    if (!ee) return pt_coeffs<float>(rel_ff(D, v.x, v.y), rel_ff(D, v.z, v.y), rel_ff(D, v.w, v.y), c, t);
+    return ee_coeffs<float>(rel_ff(D, v.x, v.z), rel_ff(D, v.y, v.z), rel_ff(D, v.w, v.z), c, t);
+}
+
+// Barrier gradient and diagonal of one candidate (Eqs. 8-11) when d < dhat; records the pair for p^T H p.
+template <typename R>
+__device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
+{
+    const int4 q = D.cand[ci];
+    const bool ee = q.x < 0;
+    int4 v = make_int4(ee ? -1 - q.x : q.x, q.y, q.z, q.w);
+    R c[4];
+    v3<R> t;
+    R d;
+    if constexpr (sizeof(R) == 4) {
+        d = pair_geom_ff(D, ee, v, c, t);
+    } else {
+        d = pair_geom<R>(ee, D.x[v.x], D.x[v.y], D.x[v.z], D.x[v.w], c, t);
+    }
+    if (!(d < R(D.dhat))) return;
+    R A, B;
+    if (sizeof(R) == 4 && d < R(1e-3) * R(D.dhat)) {
+        // near-zero distance: evaluate in double and round the results
+        double cd[4];
+        v3<double> td;
+        double dd = pair_geom<double>(ee, D.x[v.x], D.x[v.y], D.x[v.z], D.x[v.w], cd, td);
+        if (!(dd > 0.0)) { flag_error(D.ctrl, ERR_PENETRATION); return; }
+        double b1, b2;
+        barrier_d12<double>(dd, D.dhat, b1, b2);
+        A = R(D.kappa * (b2 / (dd * dd) - b1 / (dd * dd * dd)));
+        B = R(D.kappa * b1 / dd);
+        for (int k = 0; k < 4; ++k) c[k] = R(cd[k]);
+        t = mkv(R(td.x), R(td.y), R(td.z));
+        d = R(dd);
+    } else {
+        if (!(d > R(0))) { flag_error(D.ctrl, ERR_PENETRATION); return; }
+        R b1, b2;
+        barrier_d12<R>(d, R(D.dhat), b1, b2);
+        A = R(D.kappa) * (b2 / (d * d) - b1 / (d * d * d));
+        B = R(D.kappa) * b1 / d;
+    }
+    const int slot = atomicAdd(&D.ctrl->n_active, 1);
+    if (slot >= D.cand_cap) { flag_error(D.ctrl, ERR_CAPACITY); return; }
+    Active<R> ap;
+    ap.v = v;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ap.c[k] = c[k];
+    ap.t[0] = t.x; ap.t[1] = t.y; ap.t[2] = t.z;
+    ap.A = A; ap.B = B; ap.d = d;
+    ap.ty = ee ? 1 : 0;
+    D.act[slot] = ap;
+    const int vid[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R ck = c[k];
+        const R ctx = ck * t.x, cty = ck * t.y, ctz = ck * t.z;
+        atomic_add4<R>(&D.g[par][vid[k]], B * ctx, B * cty, B * ctz);
+        const R bc = B * ck * ck;
+        atomic_add4<R>(&D.dg[par][vid[k]], A * ctx * ctx + bc, A * cty * cty + bc, A * ctz * ctz + bc);
+    }
+}
+
+// Gradient pass: blocks [0, ntb) own tets, the rest loop over the candidates.
+template <typename R>
+__global__ void __launch_bounds__(EB) k_grad(Dev<R> D, int par, int ntb)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = D.ctrl;
+        c->rebuild = 0;
+        if (c->n_cand > D.cand_cap) flag_error(c, ERR_CAPACITY);
+    }
+    if ((int)blockIdx.x < ntb) {
+        const int e = blockIdx.x * blockDim.x + threadIdx.x;
+        if (e < D.nt) tet_grad<R>(D, e, par);
+    } else {
+        const int nc = min(D.ctrl->n_cand, D.cand_cap);
+        const int stride = (gridDim.x - ntb) * blockDim.x;
+        for (int ci = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; ci < nc; ci += stride) pair_grad<R>(D, ci, par);
+    }
+}
+
+// Segmented form: per-vertex gather of the (tet, corner) contributions in CSR order (deterministic).
+template <typename R>
+__global__ void __launch_bounds__(VB) k_gather(Dev<R> D, int par)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nv) return;
+    const int n4 = 4 * D.nt;
+    R s[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = D.v2c_off[i]; q < D.v2c_off[i + 1]; ++q) {
+        const int c = D.v2c[q];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s[k] += D.contrib[k * n4 + c];
+    }
+    typename V4<R>::T G = D.g[par][i], Dg = D.dg[par][i];
+    G.x += s[0]; G.y += s[1]; G.z += s[2];
+    Dg.x += s[3]; Dg.y += s[4]; Dg.z += s[5];
+    D.g[par][i] = G;
+    D.dg[par][i] = Dg;
+}
+
+// ------------------------------------------------------------------------------------------ a4: beta reductions
+
+// Preconditioner entry of a free vertex (Sec. 4.2): 1 / max(diag, m).  The Jacobi entry 1/diag wherever the
+// diagonal is at least the vertex mass; the inertia diagonal where the negative barrier term (b'/d) c_i^2 of
+// Eq. 10 pulls it lower, which keeps P continuous and bounded by 1/m.
+template <typename R> __device__ inline R precond(R d, R m) { return R(1) / (d > m ? d : m); }
+
+template <typename R>
+__global__ void __launch_bounds__(VB) k_dots(Dev<R> D, int par)
+{
+    __shared__ double sh[32 * 5];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // PR+: {g P (g - g0), g P g, g . p0, 0, 0};  DK: {g P y, y P y, y . p0, p0 . g, g P g}
+    R s[5] = {0, 0, 0, 0, 0};
+    if (i < D.nv) {
+        const typename V4<R>::T G = D.g[par][i], Dg = D.dg[par][i], G0 = D.g[par ^ 1][i], P0 = D.p[i];
+        if (Dg.w > R(0)) {
+            const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const R P = precond<R>(dv[a], Dg.w);
+                const R g = gv[a], y = g - g0[a];
+                if (D.beta_rule == 0) {
+                    s[0] += g * P * y;
+                    s[1] += g * P * g;
+                    s[2] += g * p0[a];
+                } else {
+                    s[0] += g * P * y;
+                    s[1] += y * P * y;
+                    s[2] += y * p0[a];
+                    s[3] += p0[a] * g;
+                    s[4] += g * P * g;
+                }
+            }
+        }
+    }
+    double sd[5];
+    block_sum_acc<5>(s, sd, sh);
+    if (publish_partials<5>(sd, D.part, &D.ctrl->ticket[TK_DOTS])) {
+        double t[5];
+        finish_sums<5>(t, D.part, sh);
+        if (threadIdx.x == 0) {
+            Ctrl *c = D.ctrl;
+            double beta = 0.0, gPg, gp_new;
+            int rs = 0;
+            if (D.beta_rule == 0) {
+                gPg = t[1];
+                if (c->k > 0) {
+                    beta = c->gPg_prev > 0.0 ? t[0] / c->gPg_prev : 0.0;
+                    if (beta < 0.0) beta = 0.0;
+                }
+                gp_new = -gPg + beta * t[2];
+            } else {
+                gPg = t[4];
+                if (c->k > 0) beta = fabs(t[2]) < 1e-30 ? 0.0 : t[0] / t[2] - (t[1] / t[2]) * (t[3] / t[2]);
+                gp_new = -gPg + beta * t[3];
+            }
+            if (gp_new >= 0.0 && beta != 0.0) { beta = 0.0; rs = 1; }
+            c->beta = beta;
+            c->restarted = rs;
+            c->gPg_prev = gPg;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------ a5: direction
+
+template <typename R>
+__global__ void __launch_bounds__(VB) k_dir(Dev<R> D, int par)
+{
+    __shared__ double sh[32 * 2];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double beta = D.ctrl->beta;
+    R s[2] = {0, 0};   // g . p, p^T M p + plane part
+    R pm = 0;
+    if (i < D.nv) {
+        const typename V4<R>::T G = D.g[par][i], Dg = D.dg[par][i];
+        typename V4<R>::T Pn = mk4<R>(R(0), R(0), R(0), R(0));
+        if (Dg.w > R(0)) {
+            const typename V4<R>::T P0 = D.p[i];
+            const R b = R(beta);
+            if (beta != 0.0) {
+                Pn.x = -precond<R>(Dg.x, Dg.w) * G.x + b * P0.x;
+                Pn.y = -precond<R>(Dg.y, Dg.w) * G.y + b * P0.y;
+                Pn.z = -precond<R>(Dg.z, Dg.w) * G.z + b * P0.z;
+            } else {
+                Pn.x = -precond<R>(Dg.x, Dg.w) * G.x;
+                Pn.y = -precond<R>(Dg.y, Dg.w) * G.y;
+                Pn.z = -precond<R>(Dg.z, Dg.w) * G.z;
+            }
+            const R px = Pn.x, py = Pn.y, pz = Pn.z;
+            s[0] = G.x * px + G.y * py + G.z * pz;
+            s[1] = Dg.w * (px * px + py * py + pz * pz);
+            if (D.has_plane && G.w != R(0)) {
+                const R np = R(D.pn[0]) * px + R(D.pn[1]) * py + R(D.pn[2]) * pz;
+                s[1] += G.w * np * np;
+            }
+            if (D.pnorm == 0) pm = sqrt(px * px + py * py + pz * pz);
+            else pm = fmax(fabs(px), fmax(fabs(py), fabs(pz)));
+        }
+        D.p[i] = Pn;
+    }
+    double sd[2];
+    block_sum_acc<2>(s, sd, sh);
+    double mx;
+    if constexpr (sizeof(R) == 4) mx = (double)block_max_f(pm, (float *)sh);
+    else mx = block_max(pm, sh);
+    double v[3] = {sd[0], sd[1], mx};
+    if (publish_partials<3>(v, D.part, &D.ctrl->ticket[TK_DIR])) {
+        double t[2];
+        {
+            const int nblk = gridDim.x;
+            for (int q = 0; q < 2; ++q) {
+                double a = 0.0;
+                for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += __ldcg(D.part + q * nblk + b);
+                t[q] = a;
+            }
+            block_sum<2>(t, sh);
+        }
+        double m = finish_max(D.part, 2, sh);
+        if (threadIdx.x == 0) {
+            D.ctrl->gp = t[0];
+            D.ctrl->pHp_vert = t[1];
+            D.ctrl->pmax = m;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------ a6-a7: p^T H p, step
+
+// h^2 V [mu |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF]] (Sec. 3.1 with H2 = 2I, H3 the det Hessian)
+template <typename R>
+__device__ inline R tet_pHp(const Dev<R> &D, int e)
+{
+    const int4 tv = D.tet[e];
+    TetF<R> T;
+    tet_F<R>(D, e, tv, T);
+    if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return R(0); }
+    const typename V4<R>::T P0 = D.p[tv.x], P1 = D.p[tv.y], P2 = D.p[tv.z], P3 = D.p[tv.w];
+    R dp[3][3];
+    dp[0][0] = P1.x - P0.x; dp[1][0] = P1.y - P0.y; dp[2][0] = P1.z - P0.z;
+    dp[0][1] = P2.x - P0.x; dp[1][1] = P2.y - P0.y; dp[2][1] = P2.z - P0.z;
+    dp[0][2] = P3.x - P0.x; dp[1][2] = P3.y - P0.y; dp[2][2] = P3.z - P0.z;
+    R dF[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) dF[a][b] = dp[a][0] * T.w[0][b] + dp[a][1] * T.w[1][b] + dp[a][2] * T.w[2][b];
+    R mu, lam;
+    tet_material<R>(D, e, mu, lam);
+    const R L = log(T.J);
+    const R Psi3 = (lam * L - mu) / T.J;
+    const R Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
+    R n2 = 0, g3 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) { n2 += dF[a][b] * dF[a][b]; g3 += T.cf[a][b] * dF[a][b]; }
+    // columns: f_b = F[.][b], df_b = dF[.][b]
+    v3<R> f0 = mkv(T.F[0][0], T.F[1][0], T.F[2][0]), f1 = mkv(T.F[0][1], T.F[1][1], T.F[2][1]),
+          f2 = mkv(T.F[0][2], T.F[1][2], T.F[2][2]);
+    v3<R> d0 = mkv(dF[0][0], dF[1][0], dF[2][0]), d1 = mkv(dF[0][1], dF[1][1], dF[2][1]),
+          d2 = mkv(dF[0][2], dF[1][2], dF[2][2]);
+    const R h3 = R(2) * (dot(d0, cross(d1, f2)) + dot(d0, cross(f1, d2)) + dot(f0, cross(d1, d2)));
+    return D.hv[e] * (mu * n2 + Psi33 * g3 * g3 + Psi3 * h3);
+}
+
+// Eqs. 12-13 with the recorded A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d.
+template <typename R>
+__device__ inline R pair_pHp(const Dev<R> &D, int k)
+{
+    const Active<R> ap = D.act[k];
+    const typename V4<R>::T P0 = D.p[ap.v.x], P1 = D.p[ap.v.y], P2 = D.p[ap.v.z], P3 = D.p[ap.v.w];
+    const R cx = ap.c[0] * P0.x + ap.c[1] * P1.x + ap.c[2] * P2.x + ap.c[3] * P3.x;
+    const R cy = ap.c[0] * P0.y + ap.c[1] * P1.y + ap.c[2] * P2.y + ap.c[3] * P3.y;
+    const R cz = ap.c[0] * P0.z + ap.c[1] * P1.z + ap.c[2] * P2.z + ap.c[3] * P3.z;
+    const R ct = cx * ap.t[0] + cy * ap.t[1] + cz * ap.t[2];
+    return ap.A * ct * ct + ap.B * (cx * cx + cy * cy + cz * cz);
+}
+
+// The step rule of Sec. 4.3 and the predicted decrease of Sec. 4.4, in the last block of k_pHp.
+template <typename R>
+__device__ inline void finish_step(const Dev<R> &D, double pHp)
+{
+    Ctrl *c = D.ctrl;
+    const double gp = c->gp, pmax = c->pmax;
+    const double au = pmax > 0.0 ? D.dhat / (2.0 * pmax) : 0.0;
+    const double ab = -gp / pHp;
+    double a;
+    int capped;
+    if (!(pHp > 0.0) || !isfinite(ab)) { a = au; capped = 1; }
+    else if (ab < au) { a = ab; capped = 0; }
+    else { a = au; capped = 1; }
+    const double dE = -a * gp - 0.5 * a * a * pHp;
+    const int k = c->k;
+    if (!isfinite(a) || !isfinite(gp)) flag_error(c, ERR_NONFINITE);
+    if (c->err != 0u || c->converged) a = 0.0;
+    c->pHp = pHp; c->alpha_bar = ab; c->alpha_up = au; c->alpha = a; c->dE = dE; c->capped = capped;
+    c->n_active_last = c->n_active;
+    if (!c->converged && c->err == 0u) {
+        if (k == 0) c->dE0 = dE;
+        c->n_capped += capped;
+        c->iters_done = k + 1;
+        if (D.trace && k < D.iters) {
+            double *tr = D.trace + (size_t)k * TRACE_COLS;
+            tr[0] = c->beta; tr[1] = gp; tr[2] = pHp; tr[3] = pmax; tr[4] = a; tr[5] = dE;
+            tr[6] = c->n_active; tr[7] = capped;
+        }
+        if (D.eps > 0.0 && dE < D.eps * c->dE0) c->converged = 1;
+    }
+    c->k = k + 1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(EB) k_pHp(Dev<R> D, int ntb)
+{
+    __shared__ double sh[32];
+    R s[1] = {R(0)};
+    if ((int)blockIdx.x < ntb) {
+        const int e = blockIdx.x * blockDim.x + threadIdx.x;
+        if (e < D.nt) s[0] = tet_pHp<R>(D, e);
+    } else {
+        const int na = D.ctrl->n_active;
+        const int stride = (gridDim.x - ntb) * blockDim.x;
+        for (int k = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; k < na; k += stride) s[0] += pair_pHp<R>(D, k);
+    }
+    double sd[1];
+    block_sum_acc<1>(s, sd, sh);
+    if (publish_partials<1>(sd, D.part, &D.ctrl->ticket[TK_PHP])) {
+        double t[1];
+        finish_sums<1>(t, D.part, sh);
+        if (threadIdx.x == 0) finish_step<R>(D, t[0] + D.ctrl->pHp_vert);
+    }
+}
+
+// ------------------------------------------------------------------------------------------ a8: update
+
+// x += alpha p, then the inertia / plane initialisation of the next iteration's accumulators (parity par ^ 1) and
+// the displacement check for the candidate padding.
+template <typename R>
+__global__ void __launch_bounds__(VB) k_update(Dev<R> D, int par)
+{
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double a = D.ctrl->alpha;
+    double md2 = 0.0;
+    if (i < D.nv) {
+        double4_32a X = D.x[i];
+        const typename V4<R>::T P = D.p[i];
+        X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
+        put_x<R>(D, i, X);
+        init_vertex<R>(D, i, X, D.xtil[i], par ^ 1);
+        md2 = disp2<R>(D, i, X);
+    }
+    double mx = block_max(md2, sh);
+    double v1[1] = {mx};
+    if (publish_partials<1>(v1, D.part, &D.ctrl->ticket[TK_UPDATE])) {
+        double m = finish_max(D.part, 0, sh);
+        if (threadIdx.x == 0) {
+            D.ctrl->n_active = 0;
+            request_rebuild_if(D, m);
+        }
+    }
+}
+
+// v = (x - x^t) / h; on a kernel error the step is undone (x = x^t) and the velocity kept.
+template <typename R>
+__global__ void __launch_bounds__(VB) k_finish(Dev<R> D)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool bad = D.ctrl->err != 0u;
+    if (i < D.nv) {
+        const double4_32a X = D.x[i], XT = D.xt[i];
+        if (bad) {
+            put_x<R>(D, i, XT);
+        } else {
+            const double ih = 1.0 / D.h;
+            double4_32a V = D.v[i];
+            V.x = (X.x - XT.x) * ih; V.y = (X.y - XT.y) * ih; V.z = (X.z - XT.z) * ih;
+            D.v[i] = V;
+        }
+    }
+    if (i == 0) {
+        if (bad) { if (D.ctrl->err_step < 0) D.ctrl->err_step = (int)D.ctrl->step; }
+        else D.ctrl->step += 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------ energy (reporting)
+
+template <typename R>
+__global__ void __launch_bounds__(EB) k_energy(Dev<R> D, int ntb, int nvb)
+{
+    __shared__ double sh[32 * 4];
+    double s[4] = {0, 0, 0, 0};
+    const int b = blockIdx.x;
+    if (b < ntb) {
+        const int e = b * blockDim.x + threadIdx.x;
+        if (e < D.nt) {
+            const int4 tv = D.tet[e];
+            TetF<double> T;
+            // energy is evaluated in double in both forms
+            double ds[3][3];
+            const double4_32a X0 = D.x[tv.x], X1 = D.x[tv.y], X2 = D.x[tv.z], X3 = D.x[tv.w];
+            ds[0][0] = X1.x - X0.x; ds[1][0] = X1.y - X0.y; ds[2][0] = X1.z - X0.z;
+            ds[0][1] = X2.x - X0.x; ds[1][1] = X2.y - X0.y; ds[2][1] = X2.z - X0.z;
+            ds[0][2] = X3.x - X0.x; ds[1][2] = X3.y - X0.y; ds[2][2] = X3.z - X0.z;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) T.w[r][c] = double(D.Dm[(3 * r + c) * D.nt + e]);
+            double I2 = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    T.F[a][c] = ds[a][0] * T.w[0][c] + ds[a][1] * T.w[1][c] + ds[a][2] * T.w[2][c];
+                    I2 += T.F[a][c] * T.F[a][c];
+                }
+            const double J = T.F[0][0] * (T.F[1][1] * T.F[2][2] - T.F[2][1] * T.F[1][2]) -
+                             T.F[0][1] * (T.F[1][0] * T.F[2][2] - T.F[2][0] * T.F[1][2]) +
+                             T.F[0][2] * (T.F[1][0] * T.F[2][1] - T.F[2][0] * T.F[1][1]);
+            if (!(J > 0.0)) flag_error(D.ctrl, ERR_INVERTED);
+            else {
+                double mu = D.mu, lam = D.lam;
+                if (D.escale) { mu *= D.escale[e]; lam *= D.escale[e]; }
+                const double L = log(J);
+                s[1] = double(D.hv[e]) * (0.5 * mu * (I2 - 3.0) - mu * L + 0.5 * lam * L * L);
+            }
+        }
+    } else if (b < ntb + nvb) {
+        const int i = (b - ntb) * blockDim.x + threadIdx.x;
+        if (i < D.nv) {
+            const double4_32a X = D.x[i], XT = D.xtil[i];
+            const double m = XT.w > 0.0 ? XT.w : 0.0;
+            s[0] = 0.5 * m * dist2(X, XT);
+            if (D.has_plane) {
+                double d = D.pn[0] * X.x + D.pn[1] * X.y + D.pn[2] * X.z - D.po;
+                if (d < D.dhat) {
+                    if (!(d > 0.0)) flag_error(D.ctrl, ERR_PENETRATION);
+                    else s[3] = D.kappa * barrier_b<double>(d, D.dhat);
+                }
+            }
+        }
+    } else {
+        const int nc = min(D.ctrl->n_cand, D.cand_cap);
+        const int stride = (gridDim.x - ntb - nvb) * blockDim.x;
+        for (int ci = (b - ntb - nvb) * blockDim.x + threadIdx.x; ci < nc; ci += stride) {
+            const int4 q = D.cand[ci];
+            const bool ee = q.x < 0;
+            const double4_32a X0 = D.x[ee ? -1 - q.x : q.x], X1 = D.x[q.y], X2 = D.x[q.z], X3 = D.x[q.w];
+            double c[4];
+            v3<double> t;
+            const double d = pair_geom<double>(ee, X0, X1, X2, X3, c, t);
+            if (d < D.dhat) {
+                if (!(d > 0.0)) flag_error(D.ctrl, ERR_PENETRATION);
+                else s[2] += D.kappa * barrier_b<double>(d, D.dhat);
+            }
+        }
+    }
+    block_sum<4>(s, sh);
+    if (publish_partials<4>(s, D.part, &D.ctrl->ticket[TK_ENERGY])) {
+        double t[4];
+        finish_sums<4>(t, D.part, sh);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 4; ++q) D.ctrl->energy[q] = t[q];
+    }
+}
+
+} // namespace pncg
