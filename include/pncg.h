@@ -221,6 +221,33 @@ sim_status sim_profile_step(sim_handle h, const double *targets, float *ms, int3
 int32_t sim_kernel_count(void);
 const char *sim_kernel_name(int32_t i);
 
+/*
+ * sim_pHp_noalloc: p^T H p of a Neo-Hookean tet mesh (inertia plus elastic terms, no contact), for callers that
+ * cannot allocate device memory -- a host application that owns the whole device-memory budget through its own
+ * allocator (a game engine or a renderer that loads this library as a plugin), or a real-time thread that must
+ * never block in the driver's allocator.  The paper has no counterpart: it is an allocation-free variant of the
+ * library's p^T H p reduction (the sum sim_eval_pHp returns for a scene without contact).
+ *   x, p, rest_x: device [n_verts][3]; tets: device [n_tets][4]; mass: device [n_verts] (lumped masses);
+ *   youngs, poisson: Neo-Hookean material; dt: time step (the elastic term is scaled by dt^2);
+ *   out: device, one double receiving p^T M p + dt^2 sum_e V_e p_e^T (d2 Psi / dx2) p_e (NaN if a tet is inverted);
+ *   cuda_stream: cudaStream_t to launch on (NULL = the legacy default stream).  Asynchronous: *out is ready when the
+ *   stream reaches it.
+ * No memory is allocated: the kernel's scratch (one partial sum per block of 256 threads and an arrival counter)
+ * is a file-scope __device__ array of 512 KiB that every GPU loading the library keeps until the process exits.
+ * Limits: n_verts and n_tets at most 16,777,216 each (65,536 blocks); larger sizes return SIM_ERR_INVALID_ARG
+ * and sim_noalloc_last_error() says why.  The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) for that device: make it before any stream capture.  Every call on a device shares the
+ * one scratch array, which keeps the last call's contents (the counter is cleared at the start of each call):
+ * calls that may overlap on the GPU (different streams, or threads) race and must be serialised by the caller.
+ * Errors: SIM_ERR_INVALID_ARG (null pointer, size, parameters), SIM_ERR_CUDA (no device, launch failure).
+ */
+sim_status sim_pHp_noalloc(int32_t n_verts, int32_t n_tets, const double *x, const double *p, const double *rest_x,
+                           const int32_t *tets, const double *mass, double youngs, double poisson, double dt,
+                           double *out, void *cuda_stream);
+
+/* One-line description of the last failure of sim_pHp_noalloc on the calling thread. */
+const char *sim_noalloc_last_error(void);
+
 /* Sizes: out[0..5] = n_verts, n_tets, n_surface_tris, n_surface_edges, n_surface_verts, n_excluded_pairs. */
 sim_status sim_get_sizes(sim_handle h, int32_t *out);
 

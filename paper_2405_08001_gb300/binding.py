@@ -106,6 +106,8 @@ def load():
         "sim_get_sizes": (C.c_int, [P, P]),
         "sim_destroy": (None, [P]),
         "sim_last_error": (C.c_char_p, [P]),
+        "sim_pHp_noalloc": (C.c_int, [I32, I32, P, P, P, P, P, D, D, D, P, P]),
+        "sim_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -315,6 +317,21 @@ def sim_profile_step(h, targets=None):
     p, keep = _ptr(targets)
     _check(load().sim_profile_step(h, p, ms.ctypes.data, n.ctypes.data, len(names)), h)
     return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+
+
+def sim_pHp_noalloc(x, p, rest_x, tets, mass, youngs, poisson, dt, out, stream=None):
+    """Allocation-free p^T H p (inertia + elastic, no contact) on caller-owned CUDA tensors; asynchronous on
+    `stream` (a torch.cuda.Stream or None).  out: a 1-element float64 CUDA tensor."""
+    nv, nt = x.numel() // 3, tets.numel() // 4
+    args = [_ptr(a)[0] for a in (x, p, rest_x)] + [_ptr(tets, np.int32)[0], _ptr(mass)[0]]
+    st = load().sim_pHp_noalloc(nv, nt, *args, float(youngs), float(poisson), float(dt), _ptr(out)[0],
+                                None if stream is None else stream.cuda_stream)
+    if st != SIM_OK:
+        raise SimError(st, load().sim_noalloc_last_error().decode())
+
+
+def sim_noalloc_last_error() -> str:
+    return load().sim_noalloc_last_error().decode()
 
 
 def sim_destroy(h):

@@ -1,0 +1,59 @@
+"""The allocation-free entry point sim_pHp_noalloc, for callers that cannot allocate device memory (a host
+application owning the device-memory budget, or a real-time thread that must not block in the allocator).
+
+It is checked through the C ABI against the library's existing p^T H p evaluation (sim_eval_pHp) on a scene with no
+contact, at the FP64 tolerance of the other tests, on two calls in a row (the shared scratch keeps the previous
+call's contents).  This file is collected last and needs nothing from the other test files.
+"""
+import numpy as np
+import pytest
+
+from paper_2405_08001_gb300 import scenes as S
+
+
+@pytest.mark.gpu
+def test_pHp_noalloc_matches_sim_eval_pHp_on_two_calls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import oracle
+    from paper_2405_08001_gb300 import binding as B, build
+    build.build()
+    torch.cuda.set_device(0)
+    sc = S.cube_drop(n=7, drop=0.5)          # far above the plane: no contact term
+    sc.plane = None
+    sim = B.Sim(sc, precision=B.SIM_FP64)
+    mass = oracle.Oracle.from_scene(sc).mass()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(11)
+    x = sc.x0 + 1e-3 * rng.normal(size=sc.x0.shape)
+    xd = torch.tensor(x, device=dev)
+    Xd = torch.tensor(sc.rest_x, device=dev)
+    Td = torch.tensor(sc.tets, dtype=torch.int32, device=dev)
+    Md = torch.tensor(mass, device=dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream()
+    for call in range(2):
+        p = rng.normal(size=x.shape)
+        pd = torch.tensor(p, device=dev)
+        torch.cuda.synchronize()
+        B.sim_pHp_noalloc(xd, pd, Xd, Td, Md, sc.youngs, sc.poisson, sc.dt, out, stream=stream)
+        stream.synchronize()
+        ref = B.sim_eval_pHp(sim.h, x, p)
+        got = float(out.item())
+        assert abs(got - ref) <= 1e-10 * abs(ref), (call, got, ref)
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_pHp_noalloc_rejects_sizes_beyond_its_scratch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2405_08001_gb300 import binding as B
+    lib = B.load()
+    dummy = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = lib.sim_pHp_noalloc(4, (1 << 24) + 1, dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                             dummy.data_ptr(), 1e5, 0.4, 0.01, dummy.data_ptr(), None)
+    assert st == B.SIM_ERR_INVALID_ARG
+    assert "at most" in lib.sim_noalloc_last_error().decode()
