@@ -89,6 +89,10 @@ typedef struct {
     void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = a stream owned by the library */
     int32_t use_graph;    /* 1 (default) = each time step is replayed from a captured CUDA graph */
     int32_t candidate_capacity; /* initial candidate-buffer capacity in pairs; <= 0 = automatic */
+    int32_t persistent;   /* 1 (default) = each time step (and each sim_iterate call) is one cooperative launch
+                             whose blocks stay resident and meet at grid barriers between the phases of
+                             Algorithm 1; 0 = one kernel per phase.  Falls back to 0 when the device cannot
+                             launch cooperative kernels. */
 } sim_options;
 
 /* Statistics of the last completed time step. */

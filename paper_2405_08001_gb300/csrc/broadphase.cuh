@@ -72,7 +72,7 @@ __device__ inline void box_of(const double4_32a *x, const int *v, int n, double 
 {
     double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
     for (int k = 0; k < n; ++k) {
-        const double4_32a X = x[v[k]];
+        const double4_32a X = ldcg4(x + v[k]);
         l[0] = fmin(l[0], X.x); l[1] = fmin(l[1], X.y); l[2] = fmin(l[2], X.z);
         h[0] = fmax(h[0], X.x); h[1] = fmax(h[1], X.y); h[2] = fmax(h[2], X.z);
     }
@@ -203,7 +203,7 @@ __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
 // 1e-3 relative margin, far above the float error of d)
 __device__ inline float pair_dist_build(const BPDev &B, bool ee, int a, int b, int c, int d)
 {
-    const double4_32a X0 = B.x[a], X1 = B.x[b], X2 = B.x[c], X3 = B.x[d];
+    const double4_32a X0 = ldcg4(B.x + a), X1 = ldcg4(B.x + b), X2 = ldcg4(B.x + c), X3 = ldcg4(B.x + d);
     float cc[4];
     v3<float> t;
     if (!ee) {
@@ -220,17 +220,14 @@ __device__ inline void emit(const BPDev &B, int4 c)
     if (slot < B.cap) B.cand[slot] = c;
 }
 
-// One warp per query primitive; the lanes split the entries of each bucket.
-static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
+// Query j (a surface vertex for j < ns, else edge j - ns) by one warp; the lanes split the entries of each bucket.
+__device__ inline void bp_query_one(const BPDev &B, int j, float s)
 {
-    if (!B.ctrl->rebuild) return;
-    const float s = cell_size(B);
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j < B.ns) {
         // point-triangle: the point's own cell
         const int v = B.svert[j];
-        const double4_32a X = B.x[v];
+        const double4_32a X = ldcg4(B.x + v);
         const float qx = (float)X.x, qy = (float)X.y, qz = (float)X.z;
         int ix, iy, iz;
         if (!cell_of(qx, s, ix) || !cell_of(qy, s, iy) || !cell_of(qz, s, iz)) {
@@ -239,14 +236,14 @@ static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
         }
         const unsigned long long key = cell_key(ix, iy, iz);
         const unsigned int b = cell_hash(ix, iy, iz, B.H);
-        const unsigned int st = B.boff[b / BP_SCAN_N] + B.off[b], en = st + B.cnt[b];
+        const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
         const int ov = B.obj[v];
         for (unsigned int q = st + lane; q < en; q += 32) {
-            const int f = B.eprim[q];
-            if (f < 0 || B.ekey[q] != key) continue;
+            const int f = __ldcg(B.eprim + q);
+            if (f < 0 || __ldcg(B.ekey + q) != key) continue;
             const int4 t = B.tri[f];
             if (t.x == v || t.y == v || t.z == v) continue;
-            const float4 lo = B.blo[f], hi = B.bhi[f];
+            const float4 lo = __ldcg(B.blo + f), hi = __ldcg(B.bhi + f);
             if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             if (B.nexcl && t.w == ov && is_excluded(B, ((unsigned long long)j << 31) | (unsigned long long)f)) continue;
             if (!(pair_dist_build(B, false, v, t.x, t.y, t.z) < B.thr)) continue;
@@ -271,15 +268,15 @@ static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
                 for (int iz = l[2]; iz <= h[2]; ++iz) {
                     const unsigned long long key = cell_key(ix, iy, iz);
                     const unsigned int b = cell_hash(ix, iy, iz, B.H);
-                    const unsigned int st = B.boff[b / BP_SCAN_N] + B.off[b], en = st + B.cnt[b];
+                    const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
                     for (unsigned int q = st + lane; q < en; q += 32) {
-                        const int pr = B.eprim[q];
-                        if (pr >= 0 || B.ekey[q] != key) continue;
+                        const int pr = __ldcg(B.eprim + q);
+                        if (pr >= 0 || __ldcg(B.ekey + q) != key) continue;
                         const int bi = -1 - pr;
                         if (bi <= a) continue;
                         const int4 f = B.edge[bi];
                         if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) continue;
-                        const float4 ilo = B.blo[B.nf + bi], ihi = B.bhi[B.nf + bi];
+                        const float4 ilo = __ldcg(B.blo + B.nf + bi), ihi = __ldcg(B.bhi + B.nf + bi);
                         if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
                         int cx, cy, cz;
                         cell_of(fmaxf(lo.x, ilo.x), s, cx);
@@ -294,6 +291,13 @@ static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
                     }
                 }
     }
+}
+
+// One warp per query primitive.
+static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
+{
+    if (!B.ctrl->rebuild) return;
+    bp_query_one(B, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, cell_size(B));
 }
 
 } // namespace pncg

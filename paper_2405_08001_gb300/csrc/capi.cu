@@ -61,6 +61,7 @@ sim_status sim_default_options(sim_options *o)
     o->cuda_stream = nullptr;
     o->use_graph = 1;
     o->candidate_capacity = 0;
+    o->persistent = 1;
     return SIM_OK;
 }
 

@@ -47,6 +47,20 @@ struct Ctrl {
     double energy[4];      // inertia, elastic, pair barrier, plane barrier (sim_eval_energy)
 };
 
+// Loads of data that other blocks write during a launch (positions, directions, accumulators, candidate and hash
+// arrays) go through L2 (ld.global.cg): in the persistent form one launch spans many phases, and an SM's L1 may
+// still hold a line from an earlier phase.
+__device__ inline double4_32a ldcg4(const double4_32a *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    double4_32a r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+__device__ inline float4 ldcg4(const float4 *p) { return __ldcg(p); }
+__device__ inline int4 ldcg4(const int4 *p) { return __ldcg(p); }
+
 template <typename R> struct V4;
 template <> struct V4<float> { typedef float4 T; };
 template <> struct V4<double> { typedef double4_32a T; };

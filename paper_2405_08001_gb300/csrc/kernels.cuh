@@ -201,16 +201,16 @@ __device__ inline float comp(const float4 &v, int a) { return a == 0 ? v.x : (a 
 template <typename R> __device__ inline void tet_ds(const Dev<R> &D, const int4 &tv, R ds[3][3])
 {
     if constexpr (sizeof(R) == 8) {
-        const double4_32a X0 = D.x[tv.x], X1 = D.x[tv.y], X2 = D.x[tv.z], X3 = D.x[tv.w];
+        const double4_32a X0 = ldcg4(D.x + tv.x), X1 = ldcg4(D.x + tv.y), X2 = ldcg4(D.x + tv.z), X3 = ldcg4(D.x + tv.w);
         ds[0][0] = X1.x - X0.x; ds[1][0] = X1.y - X0.y; ds[2][0] = X1.z - X0.z;
         ds[0][1] = X2.x - X0.x; ds[1][1] = X2.y - X0.y; ds[2][1] = X2.z - X0.z;
         ds[0][2] = X3.x - X0.x; ds[1][2] = X3.y - X0.y; ds[2][2] = X3.z - X0.z;
     } else {
         const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
-        const float4 h0 = D.xh[vid[0]], l0 = D.xl[vid[0]];
+        const float4 h0 = ldcg4(D.xh + vid[0]), l0 = ldcg4(D.xl + vid[0]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float4 h = D.xh[vid[c + 1]], l = D.xl[vid[c + 1]];
+            const float4 h = ldcg4(D.xh + vid[c + 1]), l = ldcg4(D.xl + vid[c + 1]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) ds[a][c] = ff_val(ff_sub(comp(h, a), comp(l, a), comp(h0, a), comp(l0, a)));
         }
@@ -271,7 +271,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
     float4 xh[4], xl[4], Xh[4], Xl[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { xh[k] = D.xh[vid[k]]; xl[k] = D.xl[vid[k]]; Xh[k] = D.Xh[vid[k]]; Xl[k] = D.Xl[vid[k]]; }
+    for (int k = 0; k < 4; ++k) { xh[k] = ldcg4(D.xh + vid[k]); xl[k] = ldcg4(D.xl + vid[k]); Xh[k] = D.Xh[vid[k]]; Xl[k] = D.Xl[vid[k]]; }
     ffl ds[3][3], dm[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -434,7 +434,7 @@ __device__ inline R pair_geom(bool ee, const double4_32a &X0, const double4_32a 
 
 __device__ inline v3<float> rel_ff(const Dev<float> &D, int a, int b)
 {
-    const float4 ha = D.xh[a], la = D.xl[a], hb = D.xh[b], lb = D.xl[b];
+    const float4 ha = ldcg4(D.xh + a), la = ldcg4(D.xl + a), hb = ldcg4(D.xh + b), lb = ldcg4(D.xl + b);
     return mkv(ff_val(ff_sub(ha.x, la.x, hb.x, lb.x)), ff_val(ff_sub(ha.y, la.y, hb.y, lb.y)),
                ff_val(ff_sub(ha.z, la.z, hb.z, lb.z)));
 }
@@ -449,7 +449,7 @@ __device__ inline float pair_geom_ff(const Dev<float> &D, bool ee, const int4 &v
 template <typename R>
 __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
 {
-    const int4 q = D.cand[ci];
+    const int4 q = ldcg4(D.cand + ci);
     const bool ee = q.x < 0;
     int4 v = make_int4(ee ? -1 - q.x : q.x, q.y, q.z, q.w);
     R c[4];
@@ -458,7 +458,7 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
     if constexpr (sizeof(R) == 4) {
         d = pair_geom_ff(D, ee, v, c, t);
     } else {
-        d = pair_geom<R>(ee, D.x[v.x], D.x[v.y], D.x[v.z], D.x[v.w], c, t);
+        d = pair_geom<R>(ee, ldcg4(D.x + v.x), ldcg4(D.x + v.y), ldcg4(D.x + v.z), ldcg4(D.x + v.w), c, t);
     }
     if (!(d < R(D.dhat))) return;
     R A, B;
@@ -466,7 +466,7 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
         // near-zero distance: evaluate in double and round the results
         double cd[4];
         v3<double> td;
-        double dd = pair_geom<double>(ee, D.x[v.x], D.x[v.y], D.x[v.z], D.x[v.w], cd, td);
+        double dd = pair_geom<double>(ee, ldcg4(D.x + v.x), ldcg4(D.x + v.y), ldcg4(D.x + v.z), ldcg4(D.x + v.w), cd, td);
         if (!(dd > 0.0)) { flag_error(D.ctrl, ERR_PENETRATION); return; }
         double b1, b2;
         barrier_d12<double>(dd, D.dhat, b1, b2);
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(VB) k_dots(Dev<R> D, int par)
     // PR+: {g P (g - g0), g P g, g . p0, 0, 0};  DK: {g P y, y P y, y . p0, p0 . g, g P g}
     R s[5] = {0, 0, 0, 0, 0};
     if (i < D.nv) {
-        const typename V4<R>::T G = D.g[par][i], Dg = D.dg[par][i], G0 = D.g[par ^ 1][i], P0 = D.p[i];
+        const typename V4<R>::T G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i), P0 = ldcg4(D.p + i);
         if (Dg.w > R(0)) {
             const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
 #pragma unroll
@@ -618,10 +618,10 @@ __global__ void __launch_bounds__(VB) k_dir(Dev<R> D, int par)
     R s[2] = {0, 0};   // g . p, p^T M p + plane part
     R pm = 0;
     if (i < D.nv) {
-        const typename V4<R>::T G = D.g[par][i], Dg = D.dg[par][i];
+        const typename V4<R>::T G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i);
         typename V4<R>::T Pn = mk4<R>(R(0), R(0), R(0), R(0));
         if (Dg.w > R(0)) {
-            const typename V4<R>::T P0 = D.p[i];
+            const typename V4<R>::T P0 = ldcg4(D.p + i);
             const R b = R(beta);
             if (beta != 0.0) {
                 Pn.x = -precond<R>(Dg.x, Dg.w) * G.x + b * P0.x;
@@ -680,7 +680,7 @@ __device__ inline R tet_pHp(const Dev<R> &D, int e)
     TetF<R> T;
     tet_F<R>(D, e, tv, T);
     if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return R(0); }
-    const typename V4<R>::T P0 = D.p[tv.x], P1 = D.p[tv.y], P2 = D.p[tv.z], P3 = D.p[tv.w];
+    const typename V4<R>::T P0 = ldcg4(D.p + tv.x), P1 = ldcg4(D.p + tv.y), P2 = ldcg4(D.p + tv.z), P3 = ldcg4(D.p + tv.w);
     R dp[3][3];
     dp[0][0] = P1.x - P0.x; dp[1][0] = P1.y - P0.y; dp[2][0] = P1.z - P0.z;
     dp[0][1] = P2.x - P0.x; dp[1][1] = P2.y - P0.y; dp[2][1] = P2.z - P0.z;
@@ -710,16 +710,24 @@ __device__ inline R tet_pHp(const Dev<R> &D, int e)
 }
 
 // Eqs. 12-13 with the recorded A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d.
+// in double: B = kappa b'/d is negative, so the two terms cancel in part (pairs are few)
 template <typename R>
-__device__ inline R pair_pHp(const Dev<R> &D, int k)
+__device__ inline double pair_pHp(const Dev<R> &D, int k)
 {
-    const Active<R> ap = D.act[k];
-    const typename V4<R>::T P0 = D.p[ap.v.x], P1 = D.p[ap.v.y], P2 = D.p[ap.v.z], P3 = D.p[ap.v.w];
+    Active<R> ap;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(D.act + k);
+        int4 *dst = reinterpret_cast<int4 *>(&ap);
+#pragma unroll
+        for (int w = 0; w < (int)(sizeof(Active<R>) / sizeof(int4)); ++w) dst[w] = __ldcg(src + w);
+    }
+    const typename V4<R>::T P0 = ldcg4(D.p + ap.v.x), P1 = ldcg4(D.p + ap.v.y), P2 = ldcg4(D.p + ap.v.z), P3 = ldcg4(D.p + ap.v.w);
     const R cx = ap.c[0] * P0.x + ap.c[1] * P1.x + ap.c[2] * P2.x + ap.c[3] * P3.x;
     const R cy = ap.c[0] * P0.y + ap.c[1] * P1.y + ap.c[2] * P2.y + ap.c[3] * P3.y;
     const R cz = ap.c[0] * P0.z + ap.c[1] * P1.z + ap.c[2] * P2.z + ap.c[3] * P3.z;
     const R ct = cx * ap.t[0] + cy * ap.t[1] + cz * ap.t[2];
-    return ap.A * ct * ct + ap.B * (cx * cx + cy * cy + cz * cz);
+    const double dct = ct;
+    return double(ap.A) * dct * dct + double(ap.B) * (double(cx) * cx + double(cy) * cy + double(cz) * cz);
 }
 
 // The step rule of Sec. 4.3 and the predicted decrease of Sec. 4.4, in the last block of k_pHp.
@@ -759,17 +767,18 @@ template <typename R>
 __global__ void __launch_bounds__(EB) k_pHp(Dev<R> D, int ntb)
 {
     __shared__ double sh[32];
-    R s[1] = {R(0)};
+    double sd[1] = {0.0};
     if ((int)blockIdx.x < ntb) {
+        R s[1] = {R(0)};
         const int e = blockIdx.x * blockDim.x + threadIdx.x;
         if (e < D.nt) s[0] = tet_pHp<R>(D, e);
+        block_sum_acc<1>(s, sd, sh);
     } else {
         const int na = D.ctrl->n_active;
         const int stride = (gridDim.x - ntb) * blockDim.x;
-        for (int k = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; k < na; k += stride) s[0] += pair_pHp<R>(D, k);
+        for (int k = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; k < na; k += stride) sd[0] += pair_pHp<R>(D, k);
+        block_sum<1>(sd, sh);
     }
-    double sd[1];
-    block_sum_acc<1>(s, sd, sh);
     if (publish_partials<1>(sd, D.part, &D.ctrl->ticket[TK_PHP])) {
         double t[1];
         finish_sums<1>(t, D.part, sh);
@@ -789,11 +798,11 @@ __global__ void __launch_bounds__(VB) k_update(Dev<R> D, int par)
     const double a = D.ctrl->alpha;
     double md2 = 0.0;
     if (i < D.nv) {
-        double4_32a X = D.x[i];
-        const typename V4<R>::T P = D.p[i];
+        double4_32a X = ldcg4(D.x + i);
+        const typename V4<R>::T P = ldcg4(D.p + i);
         X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
         put_x<R>(D, i, X);
-        init_vertex<R>(D, i, X, D.xtil[i], par ^ 1);
+        init_vertex<R>(D, i, X, ldcg4(D.xtil + i), par ^ 1);
         md2 = disp2<R>(D, i, X);
     }
     double mx = block_max(md2, sh);

@@ -8,6 +8,7 @@
 
 #include "broadphase.cuh"
 #include "kernels.cuh"
+#include "persistent.cuh"
 #include "sim.h"
 
 namespace pncg {
@@ -99,17 +100,18 @@ template <typename R> __global__ void __launch_bounds__(VB) k_eval_vert_pHp(Dev<
 template <typename R> __global__ void __launch_bounds__(EB) k_eval_pHp(Dev<R> D, int ntb)
 {
     __shared__ double sh[32];
-    R s[1] = {R(0)};
+    double sdd[1] = {0.0};
     if ((int)blockIdx.x < ntb) {
+        R s[1] = {R(0)};
         const int e = blockIdx.x * blockDim.x + threadIdx.x;
         if (e < D.nt) s[0] = tet_pHp<R>(D, e);
+        block_sum_acc<1>(s, sdd, sh);
     } else {
         const int na = D.ctrl->n_active;
         const int stride = (gridDim.x - ntb) * blockDim.x;
-        for (int k = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; k < na; k += stride) s[0] += pair_pHp<R>(D, k);
+        for (int k = (blockIdx.x - ntb) * blockDim.x + threadIdx.x; k < na; k += stride) sdd[0] += pair_pHp<R>(D, k);
+        block_sum<1>(sdd, sh);
     }
-    double sdd[1];
-    block_sum_acc<1>(s, sdd, sh);
     if (publish_partials<1>(sdd, D.part, &D.ctrl->ticket[TK_PHP])) {
         double t[1];
         finish_sums<1>(t, D.part, sh);
@@ -118,6 +120,7 @@ template <typename R> __global__ void __launch_bounds__(EB) k_eval_pHp(Dev<R> D,
 }
 static __global__ void k_copy_count(Ctrl *c) { c->n_active_last = c->n_active; }
 
+#define AL3(p, n) do { sim_status st_ = dalloc(p, n); if (st_ != SIM_OK) return st_; } while (0)
 #define CK(call)                                                                      \
     do {                                                                              \
         cudaError_t e_ = (call);                                                      \
@@ -170,7 +173,8 @@ public:
         CK(cudaSetDevice(dev));
         sim_status st = stage_targets(targets);
         if (st != SIM_OK) return st;
-        launch_predict();
+        if (persist) CK(launch_persistent(1, 0, 0, 0));
+        else launch_predict();
         k_host = 0;
         CK(cudaGetLastError());
         return SIM_OK;
@@ -179,7 +183,12 @@ public:
     sim_status iterate(int n) override
     {
         CK(cudaSetDevice(dev));
-        for (int i = 0; i < n; ++i) { launch_iteration(k_host & 1); ++k_host; }
+        if (persist && n > 0) {
+            CK(launch_persistent(0, k_host, n, 0));
+            k_host += n;
+        } else {
+            for (int i = 0; i < n; ++i) { launch_iteration(k_host & 1); ++k_host; }
+        }
         CK(cudaGetLastError());
         return SIM_OK;
     }
@@ -404,6 +413,7 @@ public:
         if (!ms || n_kernels <= 0) return fail(SIM_ERR_INVALID_ARG, "bad profile arguments");
         sim_status st = stage_targets(targets);
         if (st != SIM_OK) return st;
+        if (persist) return profile_step_persistent(ms, launches, n_kernels);
         const int n_launch = 2 + M.opt.iters * (D.segmented ? 11 : 10);
         if ((int)prof_ev.size() < n_launch + 1) {
             for (size_t i = prof_ev.size(); i < (size_t)n_launch + 1; ++i) {
@@ -463,6 +473,36 @@ public:
         return sync_and_check();
     }
 
+    // the persistent step with phase stamps: time from the end of one phase to the end of the next (as block 0
+    // sees it) is attributed to the later phase's kernel slot; launches count the phases
+    sim_status profile_step_persistent(float *ms, int32_t *launches, int n_kernels)
+    {
+        const int maxst = 64 + M.opt.iters * 16;
+        if (!stamp_buf) {
+            AL3(stamp_buf, (size_t)maxst);
+            AL3(stamp_kind, (size_t)maxst);
+        }
+        CK(cudaMemsetAsync(stamp_kind, 0x7F, sizeof(int) * maxst, s));   // out-of-range kind marks the end
+        CK(launch_persistent(1, 0, M.opt.iters, 1, stamp_buf, stamp_kind, maxst));
+        CK(cudaStreamSynchronize(s));
+        std::vector<unsigned long long> t(maxst);
+        std::vector<int> kd(maxst);
+        CK(cudaMemcpy(t.data(), stamp_buf, sizeof(unsigned long long) * maxst, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(kd.data(), stamp_kind, sizeof(int) * maxst, cudaMemcpyDeviceToHost));
+        k_host = M.opt.iters;
+        const int nk = std::min(n_kernels, (int)N_PROFILED);
+        for (int k = 0; k < nk; ++k) { ms[k] = 0.0f; if (launches) launches[k] = 0; }
+        for (int i = 1; i < maxst; ++i) {
+            const int k = kd[i];
+            if (k < 0 || k >= (int)N_PROFILED) break;
+            if (k < nk) {
+                ms[k] += (float)((t[i] - t[i - 1]) * 1e-6);
+                if (launches) launches[k] += 1;
+            }
+        }
+        return sync_and_check();
+    }
+
     void sizes(int32_t *out) override
     {
         out[0] = M.nv; out[1] = M.nt; out[2] = M.nf; out[3] = M.ne; out[4] = M.ns; out[5] = (int32_t)M.excl.size();
@@ -485,6 +525,13 @@ private:
     int cap = 0, k_host = 0;
     int nvb = 1, ntb = 1, ncb = 1, npb = 1, bpb_boxes = 1, bpb_prims = 1, bpb_query = 1;
     std::vector<cudaEvent_t> prof_ev;
+    // persistent form
+    bool persist = false;
+    int pgrid = 0;
+    GridSync gsync{nullptr, nullptr};
+    void *ppart = nullptr;
+    unsigned long long *stamp_buf = nullptr;
+    int *stamp_kind = nullptr;
 
     sim_status fail(sim_status st, const std::string &m) { err = m; return st; }
     sim_status cuda_fail(cudaError_t e, const char *what, int line)
@@ -523,6 +570,31 @@ private:
     }
 
 #define AL(p, n) do { sim_status st_ = dalloc(p, n); if (st_ != SIM_OK) return st_; } while (0)
+#define AL2(p, n) do { sim_status st_ = dalloc(p, n); if (st_ != SIM_OK) return st_; } while (0)
+
+    sim_status setup_persistent()
+    {
+        persist = false;
+        if (!M.opt.persistent) return SIM_OK;
+        int coop = 0;
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (!coop) return SIM_OK;
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R>, PB, 0));
+        if (per_sm <= 0) return SIM_OK;
+        per_sm = std::min(per_sm, 4);
+        pgrid = per_sm * nsm;
+        unsigned int *sync;
+        AL2(sync, 2);
+        gsync.count = sync;
+        gsync.gen = sync + 1;
+        const size_t bytes = 16 * (size_t)pgrid * sizeof(typename PartT<R>::T) + 2 * (size_t)pgrid * sizeof(R);
+        char *pp;
+        AL2(pp, bytes);
+        ppart = pp;
+        persist = true;
+        return SIM_OK;
+    }
 
     sim_status alloc_candidates()
     {
@@ -620,9 +692,14 @@ private:
         bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), H) + BP_B - 1) / BP_B));
         bpb_prims = std::max(1, (M.nf + M.ne + BP_B - 1) / BP_B);
         bpb_query = std::max(1, (32 * (M.ns + M.ne) + BP_B - 1) / BP_B);   // one warp per query primitive
+        {
+            sim_status st = setup_persistent();
+            if (st != SIM_OK) return st;
+        }
         return alloc_candidates();
     }
 #undef AL
+#undef AL2
 
     template <typename T> sim_status up(const T *dst, const void *src, size_t bytes)
     {
@@ -795,8 +872,26 @@ private:
         k_update<R><<<nvb, VB, 0, s>>>(D, par);
     }
     void launch_finish() { k_finish<R><<<nvb, VB, 0, s>>>(D); }
+    cudaError_t launch_persistent(int do_predict, int k0, int n_iters, int do_finish, unsigned long long *stamps = nullptr,
+                                  int *kinds = nullptr, int max_stamps = 0)
+    {
+        cudaError_t e = cudaMemsetAsync(gsync.count, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+        PersistArgs A;
+        A.do_predict = do_predict; A.k0 = k0; A.n_iters = n_iters; A.do_finish = do_finish;
+        A.gs = gsync;
+        A.part = ppart;
+        A.stamps = stamps; A.stamp_kind = kinds; A.max_stamps = max_stamps;
+        void *args[] = {(void *)&D, (void *)&B, (void *)&A};
+        return cudaLaunchCooperativeKernel((const void *)k_persistent<R>, dim3(pgrid), dim3(PB), args, 0, s);
+    }
     sim_status launch_step()
     {
+        if (persist) {
+            CK(launch_persistent(1, 0, M.opt.iters, 1));
+            k_host = M.opt.iters;
+            return SIM_OK;
+        }
         launch_predict();
         for (int k = 0; k < M.opt.iters; ++k) launch_iteration(k & 1);
         launch_finish();
@@ -815,11 +910,30 @@ private:
             M.opt.use_graph = 0;
             return SIM_OK;
         }
-        launch_predict();
-        for (int k = 0; k < M.opt.iters; ++k) launch_iteration(k & 1);
-        launch_finish();
-        CK(cudaStreamEndCapture(s, &graph));
-        CK(cudaGraphInstantiate(&gexec, graph, 0));
+        if (persist) {
+            cudaError_t le = launch_persistent(1, 0, M.opt.iters, 1);
+            cudaError_t ee = cudaStreamEndCapture(s, &graph);
+            if (le != cudaSuccess || ee != cudaSuccess) {
+                // cooperative launches that cannot be captured: launch them directly, one per step
+                cudaGetLastError();
+                if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+                M.opt.use_graph = 0;
+                return SIM_OK;
+            }
+        } else {
+            launch_predict();
+            for (int k = 0; k < M.opt.iters; ++k) launch_iteration(k & 1);
+            launch_finish();
+            CK(cudaStreamEndCapture(s, &graph));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+            gexec = nullptr;
+            M.opt.use_graph = 0;
+        }
         return SIM_OK;
     }
 };
@@ -840,5 +954,6 @@ template <typename R> void SimImpl<R>::launch_targets_from_x()
 }
 
 #undef CK
+#undef AL3
 
 } // namespace pncg

@@ -91,11 +91,12 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
       g, P  : gradient and preconditioner at the GPU's x_k (oracle's full iteration from the GPU's state)
       p     : direction from the GPU's g_{k+1}, P_{k+1} and its g_k, P_k, p_k (beta, restart and update)
       pHp   : p^T H p at x_k for the GPU's direction
+      pmax  : the largest per-vertex length of the GPU's direction
       alpha : step rule from the GPU's g^T p, p^T H p and max |p_v|
       dx    : the update alpha p
     plus `chain_p`: the oracle's direction from its own g_{k+1} (rounding of g amplified through beta)."""
     B.sim_begin_step(sim.h, targets)
-    keys = ("g", "P", "p", "pHp", "alpha", "dx", "chain_p")
+    keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "chain_p")
     worst = dict.fromkeys(keys, 0.0)
     fixed = sc.fixed.astype(bool) if sc.fixed is not None else np.zeros(sc.n_verts, bool)
     for k in range(iters):
@@ -108,7 +109,9 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
         pd, beta, gp, rs = O.ncg_direction(g1, P1, g, P, p, k, o_rule(sc))
         pHp_ref = o.pHp(x, p1)
         a_ref = O.ncg_alpha(s1["gp"], s1["pHp"], s1["pmax"], sc.dhat)[0]
+        pm_ref = O.pmax(p1)
         e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
+                 pmax=abs(s1["pmax"] - pm_ref) / pm_ref,
                  alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1), chain_p=rel(p1, po))
         for kk in worst:
             worst[kk] = max(worst[kk], e[kk])
@@ -120,7 +123,7 @@ def o_rule(sc):
     return 0
 
 
-CHECKED = ("g", "P", "p", "pHp", "alpha", "dx")
+CHECKED = ("g", "P", "p", "pHp", "pmax", "alpha", "dx")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -301,3 +304,19 @@ def test_capacity_overflow_grows_and_retries(B, O):
     o.step(xo, vo, iters=sc.iters)
     assert rel(x - sc.x0, xo - sc.x0) < 1e-7
     sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_persistent_launch_equals_per_phase_kernels(B, prec):
+    """Free fall of the drop config (no contact): the persistent cooperative step and the one-kernel-per-phase step
+    agree to rounding (their reductions group the sums differently)."""
+    sc = S.cube_drop()
+    out = []
+    for persistent in (1, 0):
+        sim = B.Sim(sc, precision=prec, persistent=persistent)
+        sim.step(3)
+        x, v, st = sim.state()
+        out.append(x)
+        assert st["step"] == 3 and st["iters_done"] == sc.iters
+        sim.close()
+    assert rel(out[0] - sc.x0, out[1] - sc.x0) < (1e-9 if prec == 0 else 1e-3)
