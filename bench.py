@@ -198,7 +198,7 @@ def run_ours(args):
     sampler.start()
 
     def one_form(prec, K_):
-        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream)
+        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else 1)
         for s in range(W):
             B.sim_step_async(sim.h, 1, targets[s])
         torch.cuda.synchronize()
@@ -256,7 +256,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: pinned targets in, positions out, every step
     e2e = None
     if True:
-        sim = B.Sim(sc, precision=B.SIM_FP32_MIXED)
+        sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
         tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
         x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
         for s in range(W):
@@ -286,7 +286,8 @@ def run_ours(args):
                        "iters_per_step": iters, "precision": "fp32-mixed: f32 element/barrier arithmetic on "
                        "float-float vertex differences, f64 reductions and vertex state",
                        "l2": "flushed between timed steps (256 MiB write, not timed)", "parallelism": "replicas",
-                       "graph": "one CUDA graph replay per time step"},
+                       "graph": "one CUDA graph replay per time step",
+                       "launch": "one kernel per phase" if args.phases else "one persistent cooperative kernel per step"},
             "time_steps_per_s": round(K / (total_ms / 1e3), 2),
             "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
                            "speedup_fp32_over_fp64": round(value / ws / v64, 3)},
@@ -381,6 +382,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", action="store_true", help="one kernel per phase instead of the persistent step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -6,9 +6,10 @@
 //
 // The five kernels run only when Ctrl::rebuild is set (they return at once otherwise):
 //   bp_boxes  : inflated float boxes (rounded outwards), largest extent -> cell size, zero bucket counts, x_b = x
-//   bp_count  : entries per hash bucket (each primitive covers at most 2 cells per axis)
+//   bp_count  : entries per hash bucket (each primitive covers at most 2 cells per axis); triangles and edges
+//               have separate tables (buckets [0, H) and [H, 2H)) so each query scans one kind only
 //   bp_scan   : exclusive scan of the counts (block-local scans + the last block scans the block sums)
-//   bp_fill   : entries (cell key, primitive) in bucket order
+//   bp_fill   : entries (cell key, primitive, a copy of the primitive's box) in bucket order
 //   bp_query  : per surface vertex (PT) and per edge (EE) lookup, exact cell-key match, box test, then the exact
 //               distance at the build positions: only pairs with d < (dhat + r)(1 + 1e-3) become candidates
 #pragma once
@@ -37,6 +38,7 @@ struct BPDev {
     unsigned int *cnt, *off, *boff;
     unsigned long long *ekey;
     int *eprim;             // triangle f or -1 - edge
+    float4 *eblo, *ebhi;    // the entry's primitive box (streamed with the key instead of gathered)
     int ecap;               // entry capacity (8 per primitive)
     int4 *cand;
     int cap;
@@ -50,6 +52,11 @@ struct BPDev {
 __device__ inline unsigned int cell_hash(int ix, int iy, int iz, int H)
 {
     return ((unsigned int)ix * 73856093u ^ (unsigned int)iy * 19349663u ^ (unsigned int)iz * 83492791u) & (unsigned int)(H - 1);
+}
+// bucket of primitive j's cell: triangles in [0, H), edges in [H, 2H)
+__device__ inline unsigned int prim_bucket(const BPDev &B, int j, int ix, int iy, int iz)
+{
+    return cell_hash(ix, iy, iz, B.H) + (j < B.nf ? 0u : (unsigned int)B.H);
 }
 __device__ inline unsigned long long cell_key(int ix, int iy, int iz)
 {
@@ -83,11 +90,11 @@ __device__ inline void box_of(const double4_32a *x, const int *v, int n, double 
 static __global__ void __launch_bounds__(BP_B) bp_boxes(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
-    const int n = max(max(B.nf + B.ne, B.nv), B.H);
+    const int n = max(max(B.nf + B.ne, B.nv), 2 * B.H);
     const int stride = gridDim.x * blockDim.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) { B.ctrl->n_cand = 0; B.ctrl->n_rebuilds += 1; }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        if (j < B.H) B.cnt[j] = 0u;
+        if (j < 2 * B.H) B.cnt[j] = 0u;
         if (j < B.nv) {
             B.xb[j] = B.x[j];
             if (B.xbh) B.xbh[j] = B.xh[j];
@@ -128,7 +135,7 @@ static __global__ void __launch_bounds__(BP_B) bp_count(BPDev B)
     const float s = cell_size(B);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= B.nf + B.ne) return;
-    for_cells(B, B.blo[j], B.bhi[j], s, [&](int i, int jj, int k) { atomicAdd(&B.cnt[cell_hash(i, jj, k, B.H)], 1u); });
+    for_cells(B, B.blo[j], B.bhi[j], s, [&](int i, int jj, int k) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, k)], 1u); });
 }
 
 static __global__ void __launch_bounds__(BP_SCAN_T) bp_scan(BPDev B)
@@ -180,12 +187,15 @@ static __global__ void __launch_bounds__(BP_B) bp_fill(BPDev B)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= B.nf + B.ne) return;
     const int prim = j < B.nf ? j : -1 - (j - B.nf);
-    for_cells(B, B.blo[j], B.bhi[j], s, [&](int i, int jj, int k) {
-        const unsigned int b = cell_hash(i, jj, k, B.H);
+    const float4 lo = B.blo[j], hi = B.bhi[j];
+    for_cells(B, lo, hi, s, [&](int i, int jj, int k) {
+        const unsigned int b = prim_bucket(B, j, i, jj, k);
         const unsigned int slot = B.boff[b / BP_SCAN_N] + B.off[b] + atomicAdd(&B.cnt[b], 1u);
         if (slot >= (unsigned int)B.ecap) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
         B.ekey[slot] = cell_key(i, jj, k);
         B.eprim[slot] = prim;
+        B.eblo[slot] = lo;
+        B.ebhi[slot] = hi;
     });
 }
 
@@ -235,16 +245,16 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             return;
         }
         const unsigned long long key = cell_key(ix, iy, iz);
-        const unsigned int b = cell_hash(ix, iy, iz, B.H);
+        const unsigned int b = cell_hash(ix, iy, iz, B.H);                 // the triangle table
         const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
         const int ov = B.obj[v];
         for (unsigned int q = st + lane; q < en; q += 32) {
+            if (__ldcg(B.ekey + q) != key) continue;
+            const float4 lo = __ldcg(B.eblo + q), hi = __ldcg(B.ebhi + q);
+            if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             const int f = __ldcg(B.eprim + q);
-            if (f < 0 || __ldcg(B.ekey + q) != key) continue;
             const int4 t = B.tri[f];
             if (t.x == v || t.y == v || t.z == v) continue;
-            const float4 lo = __ldcg(B.blo + f), hi = __ldcg(B.bhi + f);
-            if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             if (B.nexcl && t.w == ov && is_excluded(B, ((unsigned long long)j << 31) | (unsigned long long)f)) continue;
             if (!(pair_dist_build(B, false, v, t.x, t.y, t.z) < B.thr)) continue;
             emit(B, make_int4(v, t.x, t.y, t.z));
@@ -267,17 +277,16 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             for (int iy = l[1]; iy <= h[1]; ++iy)
                 for (int iz = l[2]; iz <= h[2]; ++iz) {
                     const unsigned long long key = cell_key(ix, iy, iz);
-                    const unsigned int b = cell_hash(ix, iy, iz, B.H);
+                    const unsigned int b = cell_hash(ix, iy, iz, B.H) + (unsigned int)B.H;   // the edge table
                     const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
                     for (unsigned int q = st + lane; q < en; q += 32) {
-                        const int pr = __ldcg(B.eprim + q);
-                        if (pr >= 0 || __ldcg(B.ekey + q) != key) continue;
-                        const int bi = -1 - pr;
+                        if (__ldcg(B.ekey + q) != key) continue;
+                        const float4 ilo = __ldcg(B.eblo + q), ihi = __ldcg(B.ebhi + q);
+                        if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
+                        const int bi = -1 - __ldcg(B.eprim + q);
                         if (bi <= a) continue;
                         const int4 f = B.edge[bi];
                         if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) continue;
-                        const float4 ilo = __ldcg(B.blo + B.nf + bi), ihi = __ldcg(B.bhi + B.nf + bi);
-                        if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
                         int cx, cy, cz;
                         cell_of(fmaxf(lo.x, ilo.x), s, cx);
                         cell_of(fmaxf(lo.y, ilo.y), s, cy);

@@ -25,12 +25,22 @@ struct GridSync {
     unsigned int *gen;
 };
 
+__device__ inline unsigned int ld_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Arrival: one atomic per block on `count` after a fence; release: the last block resets `count` and bumps `gen`;
+// the others poll `gen` with acquire loads and fence again before the block proceeds (count and gen live on
+// different 128-byte lines, so polling does not queue behind the arrivals).
 __device__ inline void grid_barrier(const GridSync &gs, Ctrl *c)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int nb = gridDim.x;
-        const unsigned int g = atomicAdd(gs.gen, 0u);
+        const unsigned int g = ld_acquire(gs.gen);
         __threadfence();
         if (atomicAdd(gs.count, 1u) == nb - 1) {
             atomicExch(gs.count, 0u);
@@ -38,7 +48,7 @@ __device__ inline void grid_barrier(const GridSync &gs, Ctrl *c)
             atomicAdd(gs.gen, 1u);
         } else {
             long long n = 0;
-            while (atomicAdd(gs.gen, 0u) == g) {
+            while (ld_acquire(gs.gen) == g) {
                 if ((volatile uint32_t &)c->err & ERR_TIMEOUT) break;
                 if (++n > BARRIER_SPIN_LIMIT) {
                     atomicOr(&c->err, ERR_TIMEOUT);
@@ -151,6 +161,69 @@ __device__ inline void grid_sum(Acc<R> (&a)[N], double (&out)[N], typename PartT
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < N; ++q) out[q] = sh.res[q];
+    __syncthreads();
+}
+
+// Grid-wide sum of N accumulators and max of one non-negative value with a single barrier; the max travels in the
+// (N)th partial slot (its head carries the value, its tail is zero).
+template <typename R, int N>
+__device__ inline void grid_sum_max(Acc<R> (&a)[N], R mx, double (&out)[N], R &mx_out, typename PartT<R>::T *part,
+                                    PShared<R> &sh, const GridSync &gs, Ctrl *c)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        for (int o = 16; o > 0; o >>= 1) a[q].add(a[q].shfl_down(o));
+        if (lane == 0) sh.w[warp][q] = a[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) sh.fmax_[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x < N) {
+        Acc<R> b;
+        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
+        put_part(part + threadIdx.x * gridDim.x + blockIdx.x, b);
+    } else if (threadIdx.x == N) {
+        R m = R(0);
+        for (int w = 0; w < nw; ++w) m = fmax(m, sh.fmax_[w]);
+        Acc<R> b;
+        b.add(m);
+        put_part(part + N * gridDim.x + blockIdx.x, b);
+    }
+    grid_barrier(gs, c);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        Acc<R> s;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            Acc<R> v;
+            get_part(part + q * gridDim.x + b, v);
+            s.add(v);
+        }
+        for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_down(o));
+        if (lane == 0) sh.w[warp][q] = s;
+    }
+    R m = R(0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        Acc<R> v;
+        get_part(part + N * gridDim.x + b, v);
+        m = fmax(m, (R)v.value());
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (lane == 0) sh.fmax_[warp] = m;
+    __syncthreads();
+    if (threadIdx.x < N) {
+        Acc<R> b;
+        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
+        sh.res[threadIdx.x] = b.value();
+    } else if (threadIdx.x == N) {
+        R r = R(0);
+        for (int w = 0; w < nw; ++w) r = fmax(r, sh.fmax_[w]);
+        sh.res[N] = (double)r;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = sh.res[q];
+    mx_out = (R)sh.res[N];
     __syncthreads();
 }
 
@@ -291,8 +364,8 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             st.mark(1);   // K_BP_BOXES (set-up)
             // boxes, bucket counts to zero, build positions
             const int nprim = B.nf + B.ne;
-            for (int j = tid; j < max(max(nprim, B.nv), B.H); j += nthr) {
-                if (j < B.H) B.cnt[j] = 0u;
+            for (int j = tid; j < max(max(nprim, B.nv), 2 * B.H); j += nthr) {
+                if (j < 2 * B.H) B.cnt[j] = 0u;
                 if (j < B.nv) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
                 if (j < nprim) {
                     int v[3];
@@ -311,12 +384,12 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             st.mark(1);   // K_BP_BOXES
             const float s = cell_size(B);
             for (int j = tid; j < nprim; j += nthr)
-                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[cell_hash(i, jj, kk, B.H)], 1u); });
+                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
             grid_barrier(A.gs, c);
             st.mark(2);   // K_BP_COUNT
             // block-local exclusive scans of 1024-bucket chunks (one warp per chunk)
             {
-                const int nchunk = B.H / BP_SCAN_N;
+                const int nchunk = 2 * B.H / BP_SCAN_N;
                 const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
                 for (int ch = gw; ch < nchunk; ch += nwarps) {
                     unsigned int run = 0;
@@ -339,7 +412,7 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             // chunk offsets: every block scans the chunk totals into shared memory
             __shared__ unsigned int choff[1024];
             {
-                const int nchunk = B.H / BP_SCAN_N;
+                const int nchunk = 2 * B.H / BP_SCAN_N;
                 if (threadIdx.x == 0) {
                     unsigned int run = 0;
                     for (int ch = 0; ch < nchunk && ch < 1024; ++ch) { choff[ch] = run; run += __ldcg(&B.boff[ch]); }
@@ -348,19 +421,22 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             }
             for (int j = tid; j < nprim; j += nthr) {
                 const int prim = j < B.nf ? j : -1 - (j - B.nf);
-                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) {
-                    const unsigned int b = cell_hash(i, jj, kk, B.H);
+                const float4 lo = __ldcg(B.blo + j), hi = __ldcg(B.bhi + j);
+                for_cells(B, lo, hi, s, [&](int i, int jj, int kk) {
+                    const unsigned int b = prim_bucket(B, j, i, jj, kk);
                     const unsigned int slot = choff[b / BP_SCAN_N] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u);
                     if (slot >= (unsigned int)B.ecap) { atomicOr(&c->err, ERR_RANGE); return; }
                     B.ekey[slot] = cell_key(i, jj, kk);
                     B.eprim[slot] = prim;
+                    B.eblo[slot] = lo;
+                    B.ebhi[slot] = hi;
                 });
             }
             grid_barrier(A.gs, c);
             st.mark(4);   // K_BP_FILL
             // queries: one warp per query primitive (offsets of the scan stored for bp_query's layout)
             if (blockIdx.x == 0) {
-                const int nchunk = B.H / BP_SCAN_N;
+                const int nchunk = 2 * B.H / BP_SCAN_N;
                 for (int ch = threadIdx.x; ch < nchunk && ch < 1024; ch += blockDim.x) B.boff[ch] = choff[ch];
             }
             grid_barrier(A.gs, c);
@@ -474,10 +550,11 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                 D.p[i] = Pn;
             }
             double t[2];
-            grid_sum<R, 2>(s2, t, rb.sum_region<PT>(), sh, A.gs, c);
+            R pmr;
+            grid_sum_max<R, 2>(s2, pm, t, pmr, rb.sum_region<PT>(), sh, A.gs, c);
             gp = t[0];
             pHp_vert = t[1];
-            pmax = (double)grid_max<R>(pm, rb.max_region<PT, R>(), sh, A.gs, c);
+            pmax = (double)pmr;
             st.mark(9);   // K_DIR
         }
         // ------------------------------------------------------------ a6-a7: p^T H p and the step

@@ -437,7 +437,7 @@ public:
             const int par = k & 1;
             mark(K_BP_BOXES); bp_boxes<<<bpb_boxes, BP_B, 0, s>>>(B);
             mark(K_BP_COUNT); bp_count<<<bpb_prims, BP_B, 0, s>>>(B);
-            mark(K_BP_SCAN); bp_scan<<<B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
+            mark(K_BP_SCAN); bp_scan<<<2 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
             mark(K_BP_FILL); bp_fill<<<bpb_prims, BP_B, 0, s>>>(B);
             mark(K_BP_QUERY); bp_query<<<bpb_query, BP_B, 0, s>>>(B);
             mark(K_GRAD); k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
@@ -576,6 +576,7 @@ private:
     {
         persist = false;
         if (!M.opt.persistent) return SIM_OK;
+        if (2 * B.H / BP_SCAN_N > 1024) return SIM_OK;   // the persistent scan keeps chunk offsets in shared memory
         int coop = 0;
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (!coop) return SIM_OK;
@@ -585,9 +586,9 @@ private:
         per_sm = std::min(per_sm, 4);
         pgrid = per_sm * nsm;
         unsigned int *sync;
-        AL2(sync, 2);
+        AL2(sync, 64);                    // count and gen on different 128-byte lines
         gsync.count = sync;
-        gsync.gen = sync + 1;
+        gsync.gen = sync + 32;
         const size_t bytes = 16 * (size_t)pgrid * sizeof(typename PartT<R>::T) + 2 * (size_t)pgrid * sizeof(R);
         char *pp;
         AL2(pp, bytes);
@@ -680,8 +681,9 @@ private:
         int4 *ed; AL(ed, M.ne); B.edge = ed;
         int *ob; AL(ob, nv); B.obj = ob;
         AL(B.blo, (size_t)(M.nf + M.ne)); AL(B.bhi, (size_t)(M.nf + M.ne));
-        AL(B.cnt, H); AL(B.off, H); AL(B.boff, H / BP_SCAN_N);
+        AL(B.cnt, 2 * (size_t)H); AL(B.off, 2 * (size_t)H); AL(B.boff, 2 * (size_t)H / BP_SCAN_N);
         AL(B.ekey, 8 * (size_t)(M.nf + M.ne)); AL(B.eprim, 8 * (size_t)(M.nf + M.ne));
+        AL(B.eblo, 8 * (size_t)(M.nf + M.ne)); AL(B.ebhi, 8 * (size_t)(M.nf + M.ne));
         B.ecap = 8 * (M.nf + M.ne);
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
@@ -689,7 +691,7 @@ private:
         B.infl = M.dhat + D.pad_r;
         B.thr = (float)(B.infl * 1.001);
         B.ctrl = c;
-        bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), H) + BP_B - 1) / BP_B));
+        bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), 2 * H) + BP_B - 1) / BP_B));
         bpb_prims = std::max(1, (M.nf + M.ne + BP_B - 1) / BP_B);
         bpb_query = std::max(1, (32 * (M.ns + M.ne) + BP_B - 1) / BP_B);   // one warp per query primitive
         {
@@ -853,7 +855,7 @@ private:
     {
         bp_boxes<<<bpb_boxes, BP_B, 0, s>>>(B);
         bp_count<<<bpb_prims, BP_B, 0, s>>>(B);
-        bp_scan<<<B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
+        bp_scan<<<2 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
         bp_fill<<<bpb_prims, BP_B, 0, s>>>(B);
         bp_query<<<bpb_query, BP_B, 0, s>>>(B);
     }
