@@ -216,12 +216,25 @@ sim_status sim_get_candidates(sim_handle h, int32_t *idx, int32_t max, int32_t *
 sim_status sim_get_trace(sim_handle h, double *buf, int32_t max_iters, int32_t *n);
 
 /*
- * Advances one time step like sim_step (targets as there, for this one step) and times it kernel by kernel: the
- * step is replayed from a CUDA graph with an event-record node before and after every kernel, so the times are
- * measured on the GPU.  ms: host [n_kernels], milliseconds spent in each kernel over the step (all its launches);
- * launches: host [n_kernels] or NULL, launch counts; kernel i is named by sim_kernel_name(i).  Synchronises.
+ * Advances one time step like sim_step (targets as there, for this one step) and times it kernel by kernel, on
+ * the GPU.  Per-phase form: the step is replayed from a CUDA graph with an event-record node before and after every
+ * kernel.  Persistent form (one cooperative kernel per step): block 0 stamps the GPU global timer after the grid
+ * barrier that closes each phase, and a phase's time runs from the previous stamp.  ms: host [n_kernels],
+ * milliseconds spent in each kernel (phase) over the step (all its launches); launches: host [n_kernels] or NULL,
+ * launch (phase) counts; kernel i is named by sim_kernel_name(i).  Synchronises.
  */
 sim_status sim_profile_step(sim_handle h, const double *targets, float *ms, int32_t *launches, int32_t n_kernels);
+
+/*
+ * Persistent form only: advances one time step like sim_step and records, for every grid barrier of the step and
+ * every block of the cooperative launch, the GPU global timer (ns) when the block arrived and when it left.
+ * arrive, depart: host [max_barriers][n_blocks] (n_blocks = the launch's grid, at most 4 x the SM count);
+ * kind: host [max_barriers], the sim_kernel_name index of the phase each barrier closes.  *n_barriers receives the
+ * number of barriers recorded (at most max_barriers), *n_blocks the grid size.  SIM_ERR_INVALID_ARG when the
+ * handle runs the per-phase form.  Synchronises.  A profiling aid: the paper has no counterpart.
+ */
+sim_status sim_profile_barriers(sim_handle h, const double *targets, uint64_t *arrive, uint64_t *depart,
+                                int32_t *kind, int32_t max_barriers, int32_t *n_barriers, int32_t *n_blocks);
 int32_t sim_kernel_count(void);
 const char *sim_kernel_name(int32_t i);
 

@@ -101,6 +101,7 @@ def load():
         "sim_get_candidates": (C.c_int, [P, P, I32, P]),
         "sim_get_trace": (C.c_int, [P, P, I32, P]),
         "sim_profile_step": (C.c_int, [P, P, P, P, I32]),
+        "sim_profile_barriers": (C.c_int, [P, P, P, P, P, I32, P, P]),
         "sim_kernel_count": (I32, []),
         "sim_kernel_name": (C.c_char_p, [I32]),
         "sim_get_sizes": (C.c_int, [P, P]),
@@ -317,6 +318,27 @@ def sim_profile_step(h, targets=None):
     p, keep = _ptr(targets)
     _check(load().sim_profile_step(h, p, ms.ctypes.data, n.ctypes.data, len(names)), h)
     return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+
+
+def sim_profile_barriers(h, targets=None, max_barriers=4096, max_blocks=4096):
+    """Persistent form: one time step with every block's arrival and departure time (ns) at every grid barrier.
+    Returns (arrive [n_barriers, n_blocks] uint64, depart [n_barriers, n_blocks] uint64, phase names [n_barriers])."""
+    names = sim_kernel_names()
+    arrive = np.zeros((max_barriers, max_blocks), np.uint64)
+    depart = np.zeros((max_barriers, max_blocks), np.uint64)
+    kind = np.zeros(max_barriers, np.int32)
+    nb = C.c_int32(0)
+    ng = C.c_int32(0)
+    p, keep = _ptr(targets)
+    _check(load().sim_profile_barriers(h, p, arrive.ctypes.data, depart.ctypes.data, kind.ctypes.data, max_barriers,
+                                       C.byref(nb), C.byref(ng)), h)
+    n, g = nb.value, ng.value
+    if g > max_blocks:
+        raise ValueError(f"the launch has {g} blocks, more than max_blocks = {max_blocks}")
+    # the library wrote rows of g blocks contiguously
+    flat_a = arrive.reshape(-1)[: n * g].reshape(n, g).copy()
+    flat_d = depart.reshape(-1)[: n * g].reshape(n, g).copy()
+    return flat_a, flat_d, [names[k] for k in kind[:n]]
 
 
 def sim_pHp_noalloc(x, p, rest_x, tets, mass, youngs, poisson, dt, out, stream=None):

@@ -230,7 +230,9 @@ __device__ inline void emit(const BPDev &B, int4 c)
     if (slot < B.cap) B.cand[slot] = c;
 }
 
-// Query j (a surface vertex for j < ns, else edge j - ns) by one warp; the lanes split the entries of each bucket.
+// Query j (a surface vertex for j < ns, else edge j - ns) by one warp.  The lanes take consecutive entries of the
+// query's buckets (an edge's buckets are concatenated, so no lane idles at the end of a short bucket), and each
+// lane loads an entry's key, primitive and box together.
 __device__ inline void bp_query_one(const BPDev &B, int j, float s)
 {
     const int lane = threadIdx.x & 31;
@@ -246,13 +248,15 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
         }
         const unsigned long long key = cell_key(ix, iy, iz);
         const unsigned int b = cell_hash(ix, iy, iz, B.H);                 // the triangle table
-        const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
+        const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b);
+        const unsigned int en = min(st + __ldcg(B.cnt + b), (unsigned int)B.ecap);   // a fill overflow is flagged
         const int ov = B.obj[v];
         for (unsigned int q = st + lane; q < en; q += 32) {
-            if (__ldcg(B.ekey + q) != key) continue;
+            const unsigned long long ek = __ldcg(B.ekey + q);
             const float4 lo = __ldcg(B.eblo + q), hi = __ldcg(B.ebhi + q);
-            if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             const int f = __ldcg(B.eprim + q);
+            if (ek != key) continue;
+            if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             const int4 t = B.tri[f];
             if (t.x == v || t.y == v || t.z == v) continue;
             if (B.nexcl && t.w == ov && is_excluded(B, ((unsigned long long)j << 31) | (unsigned long long)f)) continue;
@@ -260,8 +264,8 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             emit(B, make_int4(v, t.x, t.y, t.z));
         }
     } else if (j < B.ns + B.ne) {
-        // edge-edge: cells of the edge's own box; a pair is emitted from the cell holding the lower corner of the
-        // intersection of the two boxes only
+        // edge-edge: cells of the edge's own box (at most 2 per axis: the box is no wider than a cell); a pair is
+        // emitted from the cell holding the lower corner of the intersection of the two boxes only
         const int a = j - B.ns;
         const int4 e = B.edge[a];
         int vv[2] = {e.x, e.y};
@@ -273,32 +277,62 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             if (lane == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
             return;
         }
-        for (int ix = l[0]; ix <= h[0]; ++ix)
-            for (int iy = l[1]; iy <= h[1]; ++iy)
-                for (int iz = l[2]; iz <= h[2]; ++iz) {
-                    const unsigned long long key = cell_key(ix, iy, iz);
-                    const unsigned int b = cell_hash(ix, iy, iz, B.H) + (unsigned int)B.H;   // the edge table
-                    const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b), en = st + __ldcg(B.cnt + b);
-                    for (unsigned int q = st + lane; q < en; q += 32) {
-                        if (__ldcg(B.ekey + q) != key) continue;
-                        const float4 ilo = __ldcg(B.eblo + q), ihi = __ldcg(B.ebhi + q);
-                        if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
-                        const int bi = -1 - __ldcg(B.eprim + q);
-                        if (bi <= a) continue;
-                        const int4 f = B.edge[bi];
-                        if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) continue;
-                        int cx, cy, cz;
-                        cell_of(fmaxf(lo.x, ilo.x), s, cx);
-                        cell_of(fmaxf(lo.y, ilo.y), s, cy);
-                        cell_of(fmaxf(lo.z, ilo.z), s, cz);
-                        if (cx != ix || cy != iy || cz != iz) continue;
-                        if (B.nexcl && f.z == e.z &&
-                            is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)bi))
-                            continue;
-                        if (!(pair_dist_build(B, true, e.x, e.y, f.x, f.y) < B.thr)) continue;
-                        emit(B, make_int4(-1 - e.x, e.y, f.x, f.y));
-                    }
-                }
+        const int nx = h[0] - l[0] + 1, ny = h[1] - l[1] + 1, nz = h[2] - l[2] + 1;
+        const int ncell = nx * ny * nz;
+        if (ncell > 8) {
+            if (lane == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
+            return;
+        }
+        // lane c < ncell holds cell c's coordinates, first entry and entry count
+        int cx = 0, cy = 0, cz = 0;
+        unsigned int cst = 0, clen = 0;
+        if (lane < ncell) {
+            cx = l[0] + lane % nx;
+            cy = l[1] + (lane / nx) % ny;
+            cz = l[2] + lane / (nx * ny);
+            const unsigned int b = cell_hash(cx, cy, cz, B.H) + (unsigned int)B.H;   // the edge table
+            cst = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b);
+            clen = __ldcg(B.cnt + b);
+        }
+        unsigned int inc = clen;   // inclusive prefix of the counts over lanes 0..7
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        const unsigned int total = __shfl_sync(0xffffffffu, inc, 7);
+        for (unsigned int base = 0; base < total; base += 32) {
+            const unsigned int it = base + lane;
+            int c = 0;   // the cell of item it: the number of cells whose entries all come before it
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c += (__shfl_sync(0xffffffffu, inc, k) <= it) ? 1 : 0;
+            c = min(c, 7);
+            const unsigned int c_inc = __shfl_sync(0xffffffffu, inc, c), c_len = __shfl_sync(0xffffffffu, clen, c);
+            const unsigned int c_st = __shfl_sync(0xffffffffu, cst, c);
+            const int ix = __shfl_sync(0xffffffffu, cx, c), iy = __shfl_sync(0xffffffffu, cy, c),
+                      iz = __shfl_sync(0xffffffffu, cz, c);
+            if (it >= total) continue;
+            const unsigned int q = c_st + (it - (c_inc - c_len));
+            if (q >= (unsigned int)B.ecap) continue;   // a fill overflow is flagged
+            const unsigned long long ek = __ldcg(B.ekey + q);
+            const float4 ilo = __ldcg(B.eblo + q), ihi = __ldcg(B.ebhi + q);
+            const int bi = -1 - __ldcg(B.eprim + q);
+            if (ek != cell_key(ix, iy, iz)) continue;
+            if (bi <= a) continue;
+            if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
+            int kx, ky, kz;
+            cell_of(fmaxf(lo.x, ilo.x), s, kx);
+            cell_of(fmaxf(lo.y, ilo.y), s, ky);
+            cell_of(fmaxf(lo.z, ilo.z), s, kz);
+            if (kx != ix || ky != iy || kz != iz) continue;
+            const int4 f = B.edge[bi];
+            if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) continue;
+            if (B.nexcl && f.z == e.z &&
+                is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)bi))
+                continue;
+            if (!(pair_dist_build(B, true, e.x, e.y, f.x, f.y) < B.thr)) continue;
+            emit(B, make_int4(-1 - e.x, e.y, f.x, f.y));
+        }
     }
 }
 

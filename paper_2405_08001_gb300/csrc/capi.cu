@@ -200,6 +200,13 @@ sim_status sim_profile_step(sim_handle h, const double *targets, float *ms, int3
     return h->impl->profile_step(targets, ms, launches, n_kernels);
 }
 
+sim_status sim_profile_barriers(sim_handle h, const double *targets, uint64_t *arrive, uint64_t *depart, int32_t *kind,
+                                int32_t max_barriers, int32_t *n_barriers, int32_t *n_blocks)
+{
+    if (guard(h) || !n_barriers || !n_blocks) return SIM_ERR_INVALID_ARG;
+    return h->impl->profile_barriers(targets, arrive, depart, kind, max_barriers, n_barriers, n_blocks);
+}
+
 int32_t sim_kernel_count(void) { return pncg::N_PROFILED; }
 
 const char *sim_kernel_name(int32_t i)

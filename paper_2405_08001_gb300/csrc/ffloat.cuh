@@ -51,7 +51,74 @@ struct ffacc {
         s = t;
         c = __fadd_rn(c, __fadd_rn(err, e));
     }
+    // subtracts the float-float value h + l
+    __device__ inline void sub_ff(float h, float l)
+    {
+        const float p = -h;
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fsub_rn(err, l));
+    }
     __device__ inline float value() const { return __fadd_rn(s, c); }
 };
+
+// A float-float number with arithmetic, for re-evaluating the closest-point geometry of active contact pairs in the
+// FP32 form (Sec. 3.2 templates instantiated on it): about 2^-44 relative accuracy on the FP32 pipes.  Addition
+// is TwoSum of the heads plus the tails, multiplication the FMA TwoProd plus cross terms, division and square root
+// one correction step of the float quotient / root (Dekker's double-length arithmetic).
+struct ffn {
+    float h, l;
+    __host__ __device__ ffn() : h(0.0f), l(0.0f) {}
+    __host__ __device__ explicit ffn(float a) : h(a), l(0.0f) {}
+    __host__ __device__ explicit ffn(double a) : h((float)a), l((float)(a - (double)(float)a)) {}
+    __host__ __device__ explicit ffn(int a) : h((float)a), l(0.0f) {}
+    __device__ ffn(float a, float b) : h(a), l(b) {}
+};
+
+__device__ inline ffn ffn_renorm(float s, float e)
+{
+    const float h = __fadd_rn(s, e);
+    return ffn(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ inline ffn operator+(ffn a, ffn b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return ffn_renorm(s, e);
+}
+__device__ inline ffn operator-(ffn a) { return ffn(-a.h, -a.l); }
+__device__ inline ffn operator-(ffn a, ffn b) { return a + (-b); }
+__device__ inline ffn operator*(ffn a, ffn b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ffn_renorm(p, e);
+}
+__device__ inline ffn operator/(ffn a, ffn b)
+{
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const ffn r = a - b * ffn(q1);
+    const float q2 = __fdiv_rn(r.h, b.h);
+    return ffn_renorm(q1, q2);
+}
+__device__ inline ffn gsqrt(ffn a)
+{
+    if (!(a.h > 0.0f)) return ffn(0.0f);
+    const float s = __fsqrt_rn(a.h);
+    const float p = __fmul_rn(s, s);
+    const float pe = __fmaf_rn(s, s, -p);
+    const ffn r = a - ffn(p, pe);
+    return ffn_renorm(s, __fdiv_rn(r.h, __fmul_rn(2.0f, s)));
+}
+__device__ inline bool operator<(ffn a, ffn b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ inline bool operator>(ffn a, ffn b) { return b < a; }
+__device__ inline bool operator<=(ffn a, ffn b) { return !(b < a); }
+__device__ inline bool operator>=(ffn a, ffn b) { return !(a < b); }
 
 } // namespace pncg

@@ -1,5 +1,6 @@
 // Contact geometry of Sec. 3.2: the unified point-triangle / edge-edge distance d = |t|, t = sum c_i x_i, and the
-// IPC log barrier (Eq. barrier) with its first two derivatives.  Host + device templates (R = float or double).
+// IPC log barrier (Eq. barrier) with its first two derivatives.  Host + device templates (R = float, double, or
+// the float-float number type of the FP32 form).
 #pragma once
 
 #include <math.h>
@@ -7,6 +8,10 @@
 namespace pncg {
 
 template <typename R> struct v3 { R x, y, z; };
+
+// square root of the geometry's number type (float, double, or the float-float type of the FP32 form)
+__host__ __device__ inline float gsqrt(float a) { return sqrtf(a); }
+__host__ __device__ inline double gsqrt(double a) { return ::sqrt(a); }
 
 template <typename R> __host__ __device__ inline v3<R> mkv(R a, R b, R c) { v3<R> r; r.x = a; r.y = b; r.z = c; return r; }
 template <typename R> __host__ __device__ inline v3<R> operator-(v3<R> a, v3<R> b) { return mkv(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -45,7 +50,7 @@ template <typename R> __host__ __device__ inline R pt_coeffs(v3<R> r, v3<R> e1, 
         if (be >= R(0) && ga >= R(0) && be + ga <= R(1)) {
             c[0] = R(1); c[1] = -(R(1) - be - ga); c[2] = -be; c[3] = -ga;
             t = r - (be * e1 + ga * e2);
-            return sqrt(dot(t, t));
+            return gsqrt(dot(t, t));
         }
     }
     v3<R> zero = mkv(R(0), R(0), R(0));
@@ -60,7 +65,7 @@ template <typename R> __host__ __device__ inline R pt_coeffs(v3<R> r, v3<R> e1, 
     d2 = seg_closest(r, e2, zero, u);
     if (d2 < best) { best = d2; c[1] = -u; c[2] = R(0); c[3] = -(R(1) - u); }
     t = r + c[2] * e1 + c[3] * e2;
-    return sqrt(dot(t, t));
+    return gsqrt(dot(t, t));
 }
 
 // Edge-edge in coordinates relative to x2 (first vertex of the second edge):
@@ -94,7 +99,7 @@ template <typename R> __host__ __device__ inline R ee_coeffs(v3<R> r, v3<R> a1, 
         if (d2 < best) { best = d2; c[0] = R(1) - u; c[1] = u; c[2] = R(0); c[3] = R(-1); }
     }
     t = c[0] * r + c[1] * a1 + c[3] * e1;
-    return sqrt(dot(t, t));
+    return gsqrt(dot(t, t));
 }
 
 // Relative coordinates of a pair from double positions, rounded to R after the subtraction.

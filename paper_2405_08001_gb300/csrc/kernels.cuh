@@ -21,9 +21,11 @@ template <typename R> struct Dev {
     double4_32a *x, *xt, *xtil, *v, *xb;   // xtil.w = mass (free vertex) or -1 (kinematic)
     float4 *xh, *xl;                   // FP32 form: float-float copy of x (hi, lo); null in the FP64 form
     float4 *xbh;                       // FP32 form: xh at the last candidate build (displacement check)
-    const float4 *Xh, *Xl;             // FP32 form: float-float rest positions
+    const float *G0;                   // FP32 form: [12][nt] rest metric Dm^T Dm of each tet as float-float
+                                       // (hi of entries 00 01 02 11 12 22, then lo)
     R4 *g[2], *dg[2];                  // ping-pong by iteration parity; g.w = plane curvature kappa b'', dg.w = xtil.w
     R4 *p;
+    R4 *pg, *pnext;                    // persistent form: P g of the current iteration, the next direction
     const double *mass;
     const int *fix_slot;               // [nv] target slot or -1
     const double *tgt;                 // staging [nfix][3] targets of the current step
@@ -262,35 +264,34 @@ template <typename R> __device__ inline void tet_material(const Dev<R> &D, int e
 // small strains under any rotation.  With C = F^T F and the Neo-Hookean density of Sec. 3.1 written in C,
 //   P = F C^-1 (mu (C - I) + lambda log J I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
 // which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly.  The metric change G = Ds^T Ds - Dm^T Dm is
-// accumulated in float-float from the float-float current and rest positions, so that rounding never acts on the
-// O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the entries of C - I.
-// Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
+// accumulated in float-float from the float-float current positions and the tet's float-float rest metric, so that
+// rounding never acts on the O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the
+// entries of C - I.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
 __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 &tv, TetF<float> &T, float P[3][3],
                                          float &Psi33)
 {
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
-    float4 xh[4], xl[4], Xh[4], Xl[4];
+    float4 xh[4], xl[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { xh[k] = ldcg4(D.xh + vid[k]); xl[k] = ldcg4(D.xl + vid[k]); Xh[k] = D.Xh[vid[k]]; Xl[k] = D.Xl[vid[k]]; }
-    ffl ds[3][3], dm[3][3];
+    for (int k = 0; k < 4; ++k) { xh[k] = ldcg4(D.xh + vid[k]); xl[k] = ldcg4(D.xl + vid[k]); }
+    float g0h[6], g0l[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) { g0h[q] = D.G0[q * D.nt + e]; g0l[q] = D.G0[(6 + q) * D.nt + e]; }
+    ffl ds[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            ds[a][c] = ff_sub(comp(xh[c + 1], a), comp(xl[c + 1], a), comp(xh[0], a), comp(xl[0], a));
-            dm[a][c] = ff_sub(comp(Xh[c + 1], a), comp(Xl[c + 1], a), comp(Xh[0], a), comp(Xl[0], a));
-        }
+        for (int a = 0; a < 3; ++a) ds[a][c] = ff_sub(comp(xh[c + 1], a), comp(xl[c + 1], a), comp(xh[0], a), comp(xl[0], a));
     float G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
+            const int q = (i == 0 ? j : (i == 1 ? 2 + j : 5));   // 00 01 02 11 12 22
             ffacc acc;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                acc.add_prod(ds[a][i], ds[a][j], 1.0f);
-                acc.add_prod(dm[a][i], dm[a][j], -1.0f);
-            }
+            for (int a = 0; a < 3; ++a) acc.add_prod(ds[a][i], ds[a][j], 1.0f);
+            acc.sub_ff(g0h[q], g0l[q]);
             G[i][j] = G[j][i] = acc.value();
         }
     float dsf[3][3];
@@ -445,6 +446,21 @@ __device__ inline float pair_geom_ff(const Dev<float> &D, bool ee, const int4 &v
     return ee_coeffs<float>(rel_ff(D, v.x, v.z), rel_ff(D, v.y, v.z), rel_ff(D, v.w, v.z), c, t);
 }
 
+// The same geometry in float-float arithmetic, for the pairs the float pass found active: the float distance
+// loses about log2(|x_i - x_j| / d) bits, and the barrier terms (B = kappa b'/d < 0 against A > 0) often cancel in
+// p^T H p and in the diagonal.
+__device__ inline v3<ffn> rel_ffn(const Dev<float> &D, int a, int b)
+{
+    const float4 ha = ldcg4(D.xh + a), la = ldcg4(D.xl + a), hb = ldcg4(D.xh + b), lb = ldcg4(D.xl + b);
+    const ffl x = ff_sub(ha.x, la.x, hb.x, lb.x), y = ff_sub(ha.y, la.y, hb.y, lb.y), z = ff_sub(ha.z, la.z, hb.z, lb.z);
+    return mkv(ffn(x.h, x.l), ffn(y.h, y.l), ffn(z.h, z.l));
+}
+__device__ inline ffn pair_geom_ffn(const Dev<float> &D, bool ee, const int4 &v, ffn c[4], v3<ffn> &t)
+{
+    if (!ee) return pt_coeffs<ffn>(rel_ffn(D, v.x, v.y), rel_ffn(D, v.z, v.y), rel_ffn(D, v.w, v.y), c, t);
+    return ee_coeffs<ffn>(rel_ffn(D, v.x, v.z), rel_ffn(D, v.y, v.z), rel_ffn(D, v.w, v.z), c, t);
+}
+
 // Barrier gradient and diagonal of one candidate (Eqs. 8-11) when d < dhat; records the pair for p^T H p.
 template <typename R>
 __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
@@ -457,11 +473,24 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
     R d;
     if constexpr (sizeof(R) == 4) {
         d = pair_geom_ff(D, ee, v, c, t);
+        if (!(d < R(D.dhat) * R(1.0001))) return;   // float filter; the exact cut-off test follows
     } else {
         d = pair_geom<R>(ee, ldcg4(D.x + v.x), ldcg4(D.x + v.y), ldcg4(D.x + v.z), ldcg4(D.x + v.w), c, t);
+        if (!(d < R(D.dhat))) return;
     }
-    if (!(d < R(D.dhat))) return;
     R A, B;
+    if constexpr (sizeof(R) == 4) {
+        if (!(d < R(1e-3) * R(D.dhat))) {
+            ffn cf[4];
+            v3<ffn> tf;
+            const ffn df = pair_geom_ffn(D, ee, v, cf, tf);
+            if (!(df < ffn(D.dhat))) return;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = __fadd_rn(cf[k].h, cf[k].l);
+            t = mkv(__fadd_rn(tf.x.h, tf.x.l), __fadd_rn(tf.y.h, tf.y.l), __fadd_rn(tf.z.h, tf.z.l));
+            d = __fadd_rn(df.h, df.l);
+        }
+    }
     if (sizeof(R) == 4 && d < R(1e-3) * R(D.dhat)) {
         // near-zero distance: evaluate in double and round the results
         double cd[4];
@@ -548,6 +577,25 @@ __global__ void __launch_bounds__(VB) k_gather(Dev<R> D, int par)
 // diagonal is at least the vertex mass; the inertia diagonal where the negative barrier term (b'/d) c_i^2 of
 // Eq. 10 pulls it lower, which keeps P continuous and bounded by 1/m.
 template <typename R> __device__ inline R precond(R d, R m) { return R(1) / (d > m ? d : m); }
+
+__device__ inline float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ inline double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// p_{k+1} = -P g + beta p_k of vertex i (Algorithm 1) from the stored P g (pg) and p_k; the persistent form
+// evaluates it wherever a vertex's direction is needed, with one rounding order, so every evaluation agrees
+// bitwise.  Kinematic vertices have pg = p = 0.
+template <typename R>
+__device__ inline typename V4<R>::T dir_from(const typename V4<R>::T &g, const typename V4<R>::T &p, R b, bool nzb)
+{
+    if (!nzb) return mk4<R>(-g.x, -g.y, -g.z, R(0));
+    return mk4<R>(fma_rn(b, p.x, -g.x), fma_rn(b, p.y, -g.y), fma_rn(b, p.z, -g.z), R(0));
+}
+template <typename R> __device__ inline typename V4<R>::T dir_of(const Dev<R> &D, int i, R b, bool nzb)
+{
+    const typename V4<R>::T g = ldcg4(D.pg + i);
+    if (!nzb) return dir_from<R>(g, g, b, nzb);
+    return dir_from<R>(g, ldcg4(D.p + i), b, nzb);
+}
 
 template <typename R>
 __global__ void __launch_bounds__(VB) k_dots(Dev<R> D, int par)
@@ -673,14 +721,14 @@ __global__ void __launch_bounds__(VB) k_dir(Dev<R> D, int par)
 // ------------------------------------------------------------------------------------------ a6-a7: p^T H p, step
 
 // h^2 V [mu |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF]] (Sec. 3.1 with H2 = 2I, H3 the det Hessian)
+// for the direction values P0..P3 of the tet's vertices.
 template <typename R>
-__device__ inline R tet_pHp(const Dev<R> &D, int e)
+__device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const typename V4<R>::T &P0,
+                                const typename V4<R>::T &P1, const typename V4<R>::T &P2, const typename V4<R>::T &P3)
 {
-    const int4 tv = D.tet[e];
     TetF<R> T;
     tet_F<R>(D, e, tv, T);
     if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return R(0); }
-    const typename V4<R>::T P0 = ldcg4(D.p + tv.x), P1 = ldcg4(D.p + tv.y), P2 = ldcg4(D.p + tv.z), P3 = ldcg4(D.p + tv.w);
     R dp[3][3];
     dp[0][0] = P1.x - P0.x; dp[1][0] = P1.y - P0.y; dp[2][0] = P1.z - P0.z;
     dp[0][1] = P2.x - P0.x; dp[1][1] = P2.y - P0.y; dp[2][1] = P2.z - P0.z;
@@ -709,25 +757,42 @@ __device__ inline R tet_pHp(const Dev<R> &D, int e)
     return D.hv[e] * (mu * n2 + Psi33 * g3 * g3 + Psi3 * h3);
 }
 
-// Eqs. 12-13 with the recorded A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d.
-// in double: B = kappa b'/d is negative, so the two terms cancel in part (pairs are few)
+template <typename R>
+__device__ inline R tet_pHp(const Dev<R> &D, int e)
+{
+    const int4 tv = D.tet[e];
+    return tet_pHp_vec<R>(D, e, tv, ldcg4(D.p + tv.x), ldcg4(D.p + tv.y), ldcg4(D.p + tv.z), ldcg4(D.p + tv.w));
+}
+
+// Eqs. 12-13 with the recorded A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d, for direction values P0..P3, in
+// double: B = kappa b'/d is negative, so the two terms cancel in part (pairs are few)
+template <typename R>
+__device__ inline void load_active(const Dev<R> &D, int k, Active<R> &ap)
+{
+    const int4 *src = reinterpret_cast<const int4 *>(D.act + k);
+    int4 *dst = reinterpret_cast<int4 *>(&ap);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(Active<R>) / sizeof(int4)); ++w) dst[w] = __ldcg(src + w);
+}
+template <typename R>
+__device__ inline double pair_pHp_vec(const Active<R> &ap, const typename V4<R>::T &P0, const typename V4<R>::T &P1,
+                                      const typename V4<R>::T &P2, const typename V4<R>::T &P3)
+{
+    // sum c_i p_i is the relative motion of the pair (sum c_i = 0): it cancels when the pair moves together, so it
+    // is formed in double (the products of two floats are exact there)
+    const double c0 = ap.c[0], c1 = ap.c[1], c2 = ap.c[2], c3 = ap.c[3];
+    const double cx = c0 * double(P0.x) + c1 * double(P1.x) + c2 * double(P2.x) + c3 * double(P3.x);
+    const double cy = c0 * double(P0.y) + c1 * double(P1.y) + c2 * double(P2.y) + c3 * double(P3.y);
+    const double cz = c0 * double(P0.z) + c1 * double(P1.z) + c2 * double(P2.z) + c3 * double(P3.z);
+    const double ct = cx * double(ap.t[0]) + cy * double(ap.t[1]) + cz * double(ap.t[2]);
+    return double(ap.A) * ct * ct + double(ap.B) * (cx * cx + cy * cy + cz * cz);
+}
 template <typename R>
 __device__ inline double pair_pHp(const Dev<R> &D, int k)
 {
     Active<R> ap;
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(D.act + k);
-        int4 *dst = reinterpret_cast<int4 *>(&ap);
-#pragma unroll
-        for (int w = 0; w < (int)(sizeof(Active<R>) / sizeof(int4)); ++w) dst[w] = __ldcg(src + w);
-    }
-    const typename V4<R>::T P0 = ldcg4(D.p + ap.v.x), P1 = ldcg4(D.p + ap.v.y), P2 = ldcg4(D.p + ap.v.z), P3 = ldcg4(D.p + ap.v.w);
-    const R cx = ap.c[0] * P0.x + ap.c[1] * P1.x + ap.c[2] * P2.x + ap.c[3] * P3.x;
-    const R cy = ap.c[0] * P0.y + ap.c[1] * P1.y + ap.c[2] * P2.y + ap.c[3] * P3.y;
-    const R cz = ap.c[0] * P0.z + ap.c[1] * P1.z + ap.c[2] * P2.z + ap.c[3] * P3.z;
-    const R ct = cx * ap.t[0] + cy * ap.t[1] + cz * ap.t[2];
-    const double dct = ct;
-    return double(ap.A) * dct * dct + double(ap.B) * (double(cx) * cx + double(cy) * cy + double(cz) * cz);
+    load_active<R>(D, k, ap);
+    return pair_pHp_vec<R>(ap, ldcg4(D.p + ap.v.x), ldcg4(D.p + ap.v.y), ldcg4(D.p + ap.v.z), ldcg4(D.p + ap.v.w));
 }
 
 // The step rule of Sec. 4.3 and the predicted decrease of Sec. 4.4, in the last block of k_pHp.

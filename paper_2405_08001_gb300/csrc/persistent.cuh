@@ -8,6 +8,11 @@
 // needed).  In the FP32 form partial sums are carried as float-float (about 48 bits) on the FP32 pipes; in the FP64
 // form they are doubles.
 //
+// One iteration has four grid barriers: gradient | beta dots | direction + p^T H p | update.  The direction
+// p_{k+1} = -P g + beta p_k is not a phase of its own: the beta pass stores P g per vertex, and the p^T H p pass
+// forms p_{k+1} of every vertex it touches from P g and p_k (one rounding order everywhere, so the values agree
+// bitwise); the update pass then stores it as the current direction.
+//
 // Barrier waits are bounded: a block that waits longer than the limit sets ERR_TIMEOUT and carries on; later
 // barriers do not wait once the bit is set, so the launch always terminates and the host reports SIM_ERR_TIMEOUT.
 #pragma once
@@ -18,11 +23,18 @@
 namespace pncg {
 
 constexpr int PB = 256;                       // threads per block of the persistent kernel
-constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;   // ~ seconds at 32 ns per poll
+constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // a barrier wait gives up after 4 s
 
-struct GridSync {
+// Arrival counter of the grid barriers, zeroed before each launch.  Every block passes the same sequence of
+// barriers, so the n-th barrier is complete once the counter reaches n * gridDim.x.
+struct Bar {
     unsigned int *count;
-    unsigned int *gen;
+    unsigned int n;
+    // profiling (arrive = null: off): per barrier and block, globaltimer at arrival and at departure, and the
+    // phase the barrier closes
+    unsigned long long *arrive, *depart;
+    int *kind;
+    int max, phase;
 };
 
 __device__ inline unsigned int ld_acquire(const unsigned int *p)
@@ -31,33 +43,43 @@ __device__ inline unsigned int ld_acquire(const unsigned int *p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ inline void red_release_add(unsigned int *p, unsigned int v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ inline unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
-// Arrival: one atomic per block on `count` after a fence; release: the last block resets `count` and bumps `gen`;
-// the others poll `gen` with acquire loads and fence again before the block proceeds (count and gen live on
-// different 128-byte lines, so polling does not queue behind the arrivals).
-__device__ inline void grid_barrier(const GridSync &gs, Ctrl *c)
+// The block's writes are ordered before its arrival by the CTA barrier and the fence; the arrival is one release
+// add (no round trip), and the lead thread polls the counter with acquire loads.
+__device__ inline void grid_barrier(Bar &br, Ctrl *c)
 {
     __syncthreads();
+    br.n += 1;
     if (threadIdx.x == 0) {
-        const unsigned int nb = gridDim.x;
-        const unsigned int g = ld_acquire(gs.gen);
+        const unsigned int target = br.n * gridDim.x;
+        const bool rec = br.arrive && (int)br.n <= br.max;
+        if (rec) br.arrive[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();
         __threadfence();
-        if (atomicAdd(gs.count, 1u) == nb - 1) {
-            atomicExch(gs.count, 0u);
-            __threadfence();
-            atomicAdd(gs.gen, 1u);
-        } else {
-            long long n = 0;
-            while (ld_acquire(gs.gen) == g) {
+        red_release_add(br.count, 1u);
+        unsigned long long t0 = 0;
+        int n = 0;
+        while ((int)(ld_acquire(br.count) - target) < 0) {
+            if ((++n & 31) == 0) {
                 if ((volatile uint32_t &)c->err & ERR_TIMEOUT) break;
-                if (++n > BARRIER_SPIN_LIMIT) {
-                    atomicOr(&c->err, ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
+                const unsigned long long t = global_ns();
+                if (t0 == 0) t0 = t;
+                else if (t - t0 > BARRIER_LIMIT_NS) { atomicOr(&c->err, ERR_TIMEOUT); break; }
             }
         }
-        __threadfence();
+        if (rec) {
+            br.depart[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();
+            if (blockIdx.x == 0) br.kind[br.n - 1] = br.phase;
+        }
     }
     __syncthreads();
 }
@@ -73,6 +95,7 @@ template <> struct Acc<double> {
     __device__ inline void add(const Acc &o) { v += o.v; }
     __device__ inline Acc shfl_down(int o) const { Acc r; r.v = __shfl_down_sync(0xffffffffu, v, o); return r; }
     __device__ inline double value() const { return v; }
+    __device__ inline double head() const { return v; }
 };
 template <> struct Acc<float> {
     float h = 0.0f, l = 0.0f;
@@ -104,6 +127,7 @@ template <> struct Acc<float> {
         return r;
     }
     __device__ inline double value() const { return (double)h + (double)l; }
+    __device__ inline float head() const { return h; }
 };
 
 // partial-sum storage per block and quantity
@@ -115,159 +139,172 @@ __device__ inline void put_part(double *p, const Acc<double> &a) { *p = a.v; }
 __device__ inline void get_part(const float2 *p, Acc<float> &a) { const float2 v = __ldcg(p); a.h = v.x; a.l = v.y; }
 __device__ inline void get_part(const double *p, Acc<double> &a) { a.v = __ldcg(p); }
 
-template <typename R> struct PShared {
-    Acc<R> w[PB / 32][8];
-    double res[8];
-    R fmax_[PB / 32];
+
+// Scalars that the lead thread of each block reads once after a reduction's barrier (instead of every thread
+// reading one hot address): a counter and the error bits.
+struct Fetch {
+    const int *pi = nullptr;
+    const uint32_t *pe = nullptr;
 };
 
-// Grid-wide sum of N per-thread accumulators; the result (double) is returned in every thread of every block.
-// `part` holds N x gridDim.x partials.  Contains one grid barrier.
-template <typename R, int N>
-__device__ inline void grid_sum(Acc<R> (&a)[N], double (&out)[N], typename PartT<R>::T *part, PShared<R> &sh,
-                                const GridSync &gs, Ctrl *c)
+constexpr int NQ = 5;   // most quantities one grid reduction carries
+
+// Shared memory of the persistent kernel's reductions.  The per-thread values of a reduction are stored
+// transposed (one row per quantity), so that warp q reduces quantity q: few (FP64) additions per block.
+template <typename R> struct PShared {
+    Acc<R> t[NQ][PB];
+    R mx[PB];
+    double res[NQ + 1];   // reduced results: sums, then the max
+    double o[4];          // scalars computed by thread 0 and broadcast to the block
+    int oi[2];
+    int fi;
+    uint32_t fe;
+};
+
+// Block part of a grid reduction: N sums (and, with MX, a max of non-negative values) of the block's threads,
+// written as the block's partials (quantity q at part[q * gridDim.x + block], the max in slot N).
+template <typename R, int N, bool MX>
+__device__ inline void block_publish(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R> &sh)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    static_assert(N <= NQ && N + (MX ? 1 : 0) <= PB / 32, "one warp per quantity");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-        for (int o = 16; o > 0; o >>= 1) a[q].add(a[q].shfl_down(o));
-        if (lane == 0) sh.w[warp][q] = a[q];
-    }
+    for (int q = 0; q < N; ++q) sh.t[q][threadIdx.x] = a[q];
+    if (MX) sh.mx[threadIdx.x] = mx;
     __syncthreads();
-    if (threadIdx.x < N) {
-        Acc<R> b;
-        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
-        put_part(part + threadIdx.x * gridDim.x + blockIdx.x, b);
-    }
-    grid_barrier(gs, c);
-    // every block: sum the partials of quantity q in block order (thread t takes blocks t, t + PB, ...)
+    if (warp < N) {
+        Acc<R> s = sh.t[warp][lane];
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-        Acc<R> s;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            Acc<R> v;
-            get_part(part + q * gridDim.x + b, v);
-            s.add(v);
-        }
+        for (int j = 1; j < PB / 32; ++j) s.add(sh.t[warp][lane + 32 * j]);
         for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_down(o));
-        if (lane == 0) sh.w[warp][q] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < N) {
-        Acc<R> b;
-        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
-        sh.res[threadIdx.x] = b.value();
-    }
-    __syncthreads();
+        if (lane == 0) put_part(part + warp * gridDim.x + blockIdx.x, s);
+    } else if (MX && warp == N) {
+        R m = sh.mx[lane];
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = sh.res[q];
+        for (int j = 1; j < PB / 32; ++j) m = fmax(m, sh.mx[lane + 32 * j]);
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (lane == 0) { Acc<R> b; b.add(m); put_part(part + N * gridDim.x + blockIdx.x, b); }
+    }
+}
+
+// After the barrier: every thread loads the partials of blocks t and t + PB (all quantities: one round trip to
+// L2), then the block reduces them transposed like block_publish (warp q sums quantity q, warp N takes the max, in
+// block order within each lane's stride); the results land in sh.res (sums in double), and thread 0 reads the
+// fetched scalars.  Every block computes bitwise the same results.  Ends with a CTA barrier.
+constexpr int MAXG = 2 * PB;   // most blocks a persistent launch may have (the host caps its grid at this)
+template <typename R, int N, bool MX>
+__device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R> &sh, const Fetch *f)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    if (f && threadIdx.x == 0) {
+        if (f->pi) sh.fi = (volatile const int &)*f->pi;
+        if (f->pe) sh.fe = (volatile const uint32_t &)*f->pe;
+    }
+    Acc<R> v[N][MAXG / PB];
+    R m = R(0);
+#pragma unroll
+    for (int j = 0; j < MAXG / PB; ++j) {
+        const int b = threadIdx.x + j * PB;
+        if (b < G) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) get_part(part + q * G + b, v[q][j]);
+            if (MX) { Acc<R> w; get_part(part + N * G + b, w); m = fmax(m, w.head()); }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        Acc<R> s = v[q][0];
+#pragma unroll
+        for (int j = 1; j < MAXG / PB; ++j) s.add(v[q][j]);
+        sh.t[q][threadIdx.x] = s;
+    }
+    if (MX) sh.mx[threadIdx.x] = m;
+    __syncthreads();
+    if (warp < N) {
+        Acc<R> s = sh.t[warp][lane];
+#pragma unroll
+        for (int j = 1; j < PB / 32; ++j) s.add(sh.t[warp][lane + 32 * j]);
+        for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_down(o));
+        if (lane == 0) sh.res[warp] = s.value();
+    } else if (MX && warp == N) {
+        R mm = sh.mx[lane];
+#pragma unroll
+        for (int j = 1; j < PB / 32; ++j) mm = fmax(mm, sh.mx[lane + 32 * j]);
+        for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_down_sync(0xffffffffu, mm, o));
+        if (lane == 0) sh.res[N] = (double)mm;
+    }
     __syncthreads();
 }
 
-// Grid-wide sum of N accumulators and max of one non-negative value with a single barrier; the max travels in the
-// (N)th partial slot (its head carries the value, its tail is zero).
-template <typename R, int N>
-__device__ inline void grid_sum_max(Acc<R> (&a)[N], R mx, double (&out)[N], R &mx_out, typename PartT<R>::T *part,
-                                    PShared<R> &sh, const GridSync &gs, Ctrl *c)
+// Grid-wide sums of N accumulators (and a max): block part, barrier, collection into sh.res.
+template <typename R, int N, bool MX>
+__device__ inline void grid_reduce(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R> &sh, Bar &br,
+                                   Ctrl *c, const Fetch *f = nullptr)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        for (int o = 16; o > 0; o >>= 1) a[q].add(a[q].shfl_down(o));
-        if (lane == 0) sh.w[warp][q] = a[q];
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if (lane == 0) sh.fmax_[warp] = mx;
-    __syncthreads();
-    if (threadIdx.x < N) {
-        Acc<R> b;
-        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
-        put_part(part + threadIdx.x * gridDim.x + blockIdx.x, b);
-    } else if (threadIdx.x == N) {
-        R m = R(0);
-        for (int w = 0; w < nw; ++w) m = fmax(m, sh.fmax_[w]);
-        Acc<R> b;
-        b.add(m);
-        put_part(part + N * gridDim.x + blockIdx.x, b);
-    }
-    grid_barrier(gs, c);
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        Acc<R> s;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            Acc<R> v;
-            get_part(part + q * gridDim.x + b, v);
-            s.add(v);
-        }
-        for (int o = 16; o > 0; o >>= 1) s.add(s.shfl_down(o));
-        if (lane == 0) sh.w[warp][q] = s;
-    }
-    R m = R(0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        Acc<R> v;
-        get_part(part + N * gridDim.x + b, v);
-        m = fmax(m, (R)v.value());
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    if (lane == 0) sh.fmax_[warp] = m;
-    __syncthreads();
-    if (threadIdx.x < N) {
-        Acc<R> b;
-        for (int w = 0; w < nw; ++w) b.add(sh.w[w][threadIdx.x]);
-        sh.res[threadIdx.x] = b.value();
-    } else if (threadIdx.x == N) {
-        R r = R(0);
-        for (int w = 0; w < nw; ++w) r = fmax(r, sh.fmax_[w]);
-        sh.res[N] = (double)r;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = sh.res[q];
-    mx_out = (R)sh.res[N];
-    __syncthreads();
+    block_publish<R, N, MX>(a, mx, part, sh);
+    grid_barrier(br, c);
+    grid_collect<R, N, MX>(part, sh, f);
 }
 
 // Grid-wide max of non-negative values of the element type (exact); one grid barrier.  `part` holds gridDim.x
-// values of type R.
+// values of type R.  Returned in every thread.
 template <typename R>
-__device__ inline R grid_max(R v, R *part, PShared<R> &sh, const GridSync &gs, Ctrl *c)
+__device__ inline R grid_max(R v, R *part, PShared<R> &sh, Bar &br, Ctrl *c)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    if (lane == 0) sh.fmax_[warp] = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sh.mx[threadIdx.x] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        R m = R(0);
-        for (int w = 0; w < nw; ++w) m = fmax(m, sh.fmax_[w]);
-        part[blockIdx.x] = m;
+    if (warp == 0) {
+        R m = sh.mx[lane];
+#pragma unroll
+        for (int j = 1; j < PB / 32; ++j) m = fmax(m, sh.mx[lane + 32 * j]);
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (lane == 0) part[blockIdx.x] = m;
     }
-    grid_barrier(gs, c);
+    grid_barrier(br, c);
     R m = R(0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(part + b));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    if (lane == 0) sh.fmax_[warp] = m;
+#pragma unroll
+    for (int j = 0; j < MAXG / PB; ++j) {
+        const int b = threadIdx.x + j * PB;
+        if (b < (int)gridDim.x) m = fmax(m, __ldcg(part + b));
+    }
+    sh.mx[threadIdx.x] = m;
     __syncthreads();
-    R r = R(0);
-    for (int w = 0; w < nw; ++w) r = fmax(r, sh.fmax_[w]);
+    if (warp == 0) {
+        R mm = sh.mx[lane];
+#pragma unroll
+        for (int j = 1; j < PB / 32; ++j) mm = fmax(mm, sh.mx[lane + 32 * j]);
+        for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_down_sync(0xffffffffu, mm, o));
+        if (lane == 0) sh.res[0] = (double)mm;
+    }
+    __syncthreads();
+    const R r = (R)sh.res[0];
     __syncthreads();
     return r;
 }
 
+// a value that thread 0 reads once for the whole block
+__device__ inline int block_read(const int *p, int *sh)
+{
+    if (threadIdx.x == 0) *sh = (volatile const int &)*p;
+    __syncthreads();
+    const int v = *sh;
+    __syncthreads();
+    return v;
+}
+
 struct PersistArgs {
     int do_predict, k0, n_iters, do_finish;
-    GridSync gs;
-    void *part;            // reduction partials: 2 x 8 x gridDim.x of the partial type, then 2 x gridDim.x floats
+    unsigned int *count;          // barrier arrival counter (zeroed before the launch)
+    void *part;                   // reduction partials: 2 x 8 x gridDim.x of the partial type, then 2 x gridDim.x R
     unsigned long long *stamps;   // profiling (null = off): globaltimer at the end of each phase, seen by block 0
     int *stamp_kind;              // the phase each stamp closes (K_* of sim.h order)
     int max_stamps;
+    unsigned long long *arrive, *depart;   // profiling (null = off): [max_bar][gridDim.x] barrier times
+    int *bar_kind;                // [max_bar] phase closed by each barrier
+    int max_bar;
 };
-
-__device__ inline unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // block 0's lead thread records the end of a phase (after the barrier that closes it)
 struct Stamper {
@@ -291,18 +328,39 @@ struct RedBufs {
     template <typename PT, typename R> __device__ inline R *max_region() { return (R *)((PT *)base + (size_t)16 * n) + (size_t)(max_i++ & 1) * n; }
 };
 
+// the displacement reference of a vertex (its position at the last candidate build): the float copy in the FP32
+// form, the double position in the FP64 form; and the squared displacement of a new position from it
+template <typename R> struct DispRef;
+template <> struct DispRef<float> { typedef float4 T; };
+template <> struct DispRef<double> { typedef double4_32a T; };
+template <typename R> __device__ inline typename DispRef<R>::T disp_ref(const Dev<R> &D, int i);
+template <> __device__ inline float4 disp_ref<float>(const Dev<float> &D, int i) { return ldcg4(D.xbh + i); }
+template <> __device__ inline double4_32a disp_ref<double>(const Dev<double> &D, int i) { return ldcg4(D.xb + i); }
+template <typename R> __device__ inline R disp2_from(const double4_32a &X, const typename DispRef<R>::T &B)
+{
+    if constexpr (sizeof(R) == 4) {   // the float head of the float-float copy, as disp2 forms it
+        const float x = __double2float_rn(X.x) - B.x, y = __double2float_rn(X.y) - B.y, z = __double2float_rn(X.z) - B.z;
+        return x * x + y * y + z * z;
+    } else {
+        return dist2(X, B);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------ the kernel
 
 template <typename R>
-__global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArgs A)
+__global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, PersistArgs A)
 {
     typedef typename V4<R>::T R4;
     typedef typename PartT<R>::T PT;
-    __shared__ PShared<R> sh;
+    __shared__ __align__(16) unsigned char sh_raw[sizeof(PShared<R>)];   // raw storage: Acc has initialisers
+    PShared<R> &sh = *reinterpret_cast<PShared<R> *>(sh_raw);
+    __shared__ int sh_i;
     Ctrl *c = D.ctrl;
     RedBufs rb;
     rb.base = A.part;
     rb.n = gridDim.x;
+    Bar br{A.count, 0u, A.arrive, A.depart, A.bar_kind, A.max_bar, 0};
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -312,13 +370,15 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
     double gPg_prev = (volatile double &)c->gPg_prev;
     double dE0 = (volatile double &)c->dE0;
     int converged = (volatile int &)c->converged;
+    int ncand = (volatile int &)c->n_cand;
     const double disp_lim = 0.5 * D.pad_r * (1.0 - 1e-4);
     Stamper st{A.stamps, A.stamp_kind, A.max_stamps};
-    grid_barrier(A.gs, c);
+    grid_barrier(br, c);
     st.mark(-1);
 
     // ---------------------------------------------------------------- a0: prediction and iteration-0 init
     if (A.do_predict) {
+        br.phase = 0;   // K_PREDICT
         R md = R(0);
         if (!skip_step) {
             for (int i = tid; i < D.nv; i += nthr) {
@@ -341,7 +401,7 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                 md = fmax(md, (R)disp2<R>(D, i, X));
             }
         }
-        const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, A.gs, c);
+        const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
         if (!skip_step && (double)m >= disp_lim * disp_lim) rebuild = 1;
         gPg_prev = 0.0;
         dE0 = 0.0;
@@ -350,7 +410,7 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->iters_done = 0; c->converged = 0;
             c->n_active = 0; c->dE0 = 0.0; c->gPg_prev = 0.0;
         }
-        grid_barrier(A.gs, c);
+        grid_barrier(br, c);
         st.mark(0);   // K_PREDICT
     }
 
@@ -359,8 +419,9 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
         const int par = k & 1;
         // ------------------------------------------------------------ a1: candidate build when needed
         if (rebuild) {
+            br.phase = 1;   // K_BP_BOXES
             if (lead) { c->n_cand = 0; c->n_rebuilds += 1; c->cell_bits = 0u; }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(1);   // K_BP_BOXES (set-up)
             // boxes, bucket counts to zero, build positions
             const int nprim = B.nf + B.ne;
@@ -380,14 +441,16 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                     atomicMax(&c->cell_bits, __float_as_uint(ext));
                 }
             }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(1);   // K_BP_BOXES
             const float s = cell_size(B);
+            br.phase = 2;   // K_BP_COUNT
             for (int j = tid; j < nprim; j += nthr)
                 for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
             // block-local exclusive scans of 1024-bucket chunks (one warp per chunk)
+            br.phase = 3;   // K_BP_SCAN
             {
                 const int nchunk = 2 * B.H / BP_SCAN_N;
                 const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
@@ -407,9 +470,10 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                     if (lane == 0) B.boff[ch] = run;
                 }
             }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(3);   // K_BP_SCAN
             // chunk offsets: every block scans the chunk totals into shared memory
+            br.phase = 4;   // K_BP_FILL
             __shared__ unsigned int choff[1024];
             {
                 const int nchunk = 2 * B.H / BP_SCAN_N;
@@ -432,33 +496,37 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                     B.ebhi[slot] = hi;
                 });
             }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL
             // queries: one warp per query primitive (offsets of the scan stored for bp_query's layout)
             if (blockIdx.x == 0) {
                 const int nchunk = 2 * B.H / BP_SCAN_N;
                 for (int ch = threadIdx.x; ch < nchunk && ch < 1024; ch += blockDim.x) B.boff[ch] = choff[ch];
             }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL (offsets)
+            br.phase = 5;   // K_BP_QUERY
             for (int w = tid >> 5; w < B.ns + B.ne; w += nthr >> 5) bp_query_one(B, w, s);
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(5);   // K_BP_QUERY
+            ncand = block_read(&c->n_cand, &sh_i);
             rebuild = 0;
         }
         // ------------------------------------------------------------ a2-a3: gradient + diagonal
+        br.phase = 6;   // K_GRAD
         if (lead) {
             c->rebuild = 0;
-            if (c->n_cand > D.cand_cap) flag_error(c, ERR_CAPACITY);
+            if (ncand > D.cand_cap) flag_error(c, ERR_CAPACITY);
         }
         for (int e = tid; e < D.nt; e += nthr) tet_grad<R>(D, e, par);
         {
-            const int nc = min((volatile int &)c->n_cand, D.cand_cap);
+            const int nc = min(ncand, D.cand_cap);
             for (int ci = tid; ci < nc; ci += nthr) pair_grad<R>(D, ci, par);
         }
-        grid_barrier(A.gs, c);
+        grid_barrier(br, c);
         st.mark(6);   // K_GRAD
         if (D.segmented) {
+            br.phase = 7;   // K_GATHER
             const int n4 = 4 * D.nt;
             for (int i = tid; i < D.nv; i += nthr) {
                 R s6[6] = {0, 0, 0, 0, 0, 0};
@@ -473,146 +541,201 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
                 D.g[par][i] = G;
                 D.dg[par][i] = Dg;
             }
-            grid_barrier(A.gs, c);
+            grid_barrier(br, c);
             st.mark(7);   // K_GATHER
         }
-        // ------------------------------------------------------------ a4: beta
+        // ------------------------------------------------------------ a4: beta (and P g for the direction)
         double beta = 0.0;
         int restarted = 0;
+        int na;
+        R4 oG, oDg, oPG, oP0;   // this thread's own vertex (i == tid), kept for the direction pass
+        br.phase = 8;   // K_DOTS
         {
             Acc<R> s5[5];
             for (int i = tid; i < D.nv; i += nthr) {
-                const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i), P0 = ldcg4(D.p + i);
+                const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i);
+                R4 P0 = ldcg4(D.p + i);
+                R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
                 if (Dg.w > R(0)) {
                     const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
-                    R t5[5] = {0, 0, 0, 0, 0};
+                    R t5[5] = {0, 0, 0, 0, 0}, pg[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const R P = precond<R>(dv[a], Dg.w);
                         const R g = gv[a], y = g - g0[a];
+                        pg[a] = g * P;
                         if (D.beta_rule == 0) {
-                            t5[0] += g * P * y; t5[1] += g * P * g; t5[2] += g * p0[a];
+                            t5[0] += pg[a] * y; t5[1] += pg[a] * g; t5[2] += g * p0[a];
                         } else {
-                            t5[0] += g * P * y; t5[1] += y * P * y; t5[2] += y * p0[a]; t5[3] += p0[a] * g; t5[4] += g * P * g;
+                            t5[0] += pg[a] * y; t5[1] += y * P * y; t5[2] += y * p0[a]; t5[3] += p0[a] * g; t5[4] += pg[a] * g;
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < 5; ++q) s5[q].add(t5[q]);
+                    PG = mk4<R>(pg[0], pg[1], pg[2], R(0));
+                } else if (P0.x != R(0) || P0.y != R(0) || P0.z != R(0)) {
+                    D.p[i] = PG;   // a kinematic vertex never moves along p
+                    P0 = PG;
                 }
+                D.pg[i] = PG;
+                if (i == tid) { oG = G; oDg = Dg; oPG = PG; oP0 = P0; }
             }
-            double t[5];
-            grid_sum<R, 5>(s5, t, rb.sum_region<PT>(), sh, A.gs, c);
+            Fetch f;
+            f.pi = &c->n_active;
+            grid_reduce<R, 5, false>(s5, R(0), rb.sum_region<PT>(), sh, br, c, &f);
             st.mark(8);   // K_DOTS
-            double gPg, gp_new;
-            if (D.beta_rule == 0) {
-                gPg = t[1];
-                if (k > 0) { beta = gPg_prev > 0.0 ? t[0] / gPg_prev : 0.0; if (beta < 0.0) beta = 0.0; }
-                gp_new = -gPg + beta * t[2];
-            } else {
-                gPg = t[4];
-                if (k > 0) beta = fabs(t[2]) < 1e-30 ? 0.0 : t[0] / t[2] - (t[1] / t[2]) * (t[3] / t[2]);
-                gp_new = -gPg + beta * t[3];
+            // beta and the restart test: scalar FP64 work, done by one thread and broadcast
+            if (threadIdx.x == 0) {
+                const double *t = sh.res;
+                double bt = 0.0, gPg, gp_new;
+                int rs = 0;
+                if (D.beta_rule == 0) {
+                    gPg = t[1];
+                    if (k > 0) { bt = gPg_prev > 0.0 ? t[0] / gPg_prev : 0.0; if (bt < 0.0) bt = 0.0; }
+                    gp_new = -gPg + bt * t[2];
+                } else {
+                    gPg = t[4];
+                    if (k > 0) bt = fabs(t[2]) < 1e-30 ? 0.0 : t[0] / t[2] - (t[1] / t[2]) * (t[3] / t[2]);
+                    gp_new = -gPg + bt * t[3];
+                }
+                if (gp_new >= 0.0 && bt != 0.0) { bt = 0.0; rs = 1; }
+                sh.o[0] = bt;
+                sh.o[1] = gPg;
+                sh.oi[0] = rs;
+                sh.oi[1] = sh.fi;
             }
-            if (gp_new >= 0.0 && beta != 0.0) { beta = 0.0; restarted = 1; }
-            gPg_prev = gPg;
+            __syncthreads();
+            beta = sh.o[0];
+            gPg_prev = sh.o[1];
+            restarted = sh.oi[0];
+            na = sh.oi[1];
         }
-        // ------------------------------------------------------------ a5: direction
-        double gp, pHp_vert, pmax;
+        // ------------------------------------------------------------ a5-a7: direction, p^T H p and the step
+        double alpha;
+        double4_32a uX, uXT;
+        R4 uP;
+        typename DispRef<R>::T uXB;
+        br.phase = 10;   // K_PHP
         {
-            Acc<R> s2[2];
-            R pm = R(0);
             const R b = R(beta);
+            const bool nzb = beta != 0.0;
+            Acc<R> s3[3];   // g . p, p^T M p (+ half-space part), p^T H p of tets and pairs
+            R pm = R(0);
             for (int i = tid; i < D.nv; i += nthr) {
-                const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i);
+                const bool own = i == tid;
+                const R4 Dg = own ? oDg : ldcg4(D.dg[par] + i);
                 R4 Pn = mk4<R>(R(0), R(0), R(0), R(0));
                 if (Dg.w > R(0)) {
-                    const R4 P0 = ldcg4(D.p + i);
-                    if (beta != 0.0) {
-                        Pn.x = -precond<R>(Dg.x, Dg.w) * G.x + b * P0.x;
-                        Pn.y = -precond<R>(Dg.y, Dg.w) * G.y + b * P0.y;
-                        Pn.z = -precond<R>(Dg.z, Dg.w) * G.z + b * P0.z;
-                    } else {
-                        Pn.x = -precond<R>(Dg.x, Dg.w) * G.x;
-                        Pn.y = -precond<R>(Dg.y, Dg.w) * G.y;
-                        Pn.z = -precond<R>(Dg.z, Dg.w) * G.z;
-                    }
+                    const R4 G = own ? oG : ldcg4(D.g[par] + i);
+                    Pn = own ? dir_from<R>(oPG, oP0, b, nzb) : dir_of<R>(D, i, b, nzb);
                     const R px = Pn.x, py = Pn.y, pz = Pn.z;
-                    s2[0].add(G.x * px + G.y * py + G.z * pz);
+                    s3[0].add(G.x * px + G.y * py + G.z * pz);
                     R mp = Dg.w * (px * px + py * py + pz * pz);
                     if (D.has_plane && G.w != R(0)) {
                         const R np = R(D.pn[0]) * px + R(D.pn[1]) * py + R(D.pn[2]) * pz;
                         mp += G.w * np * np;
                     }
-                    s2[1].add(mp);
+                    s3[1].add(mp);
                     const R pn = D.pnorm == 0 ? sqrt(px * px + py * py + pz * pz) : fmax(fabs(px), fmax(fabs(py), fabs(pz)));
                     pm = fmax(pm, pn);
                 }
-                D.p[i] = Pn;
+                D.pnext[i] = Pn;
             }
-            double t[2];
-            R pmr;
-            grid_sum_max<R, 2>(s2, pm, t, pmr, rb.sum_region<PT>(), sh, A.gs, c);
-            gp = t[0];
-            pHp_vert = t[1];
-            pmax = (double)pmr;
-            st.mark(9);   // K_DIR
-        }
-        // ------------------------------------------------------------ a6-a7: p^T H p and the step
-        double alpha;
-        {
-            Acc<R> s1[1];
-            for (int e = tid; e < D.nt; e += nthr) s1[0].add(tet_pHp<R>(D, e));
-            const int na = (volatile int &)c->n_active;
-            for (int kk = tid; kk < na; kk += nthr) s1[0].add_d(pair_pHp<R>(D, kk));
-            double t[1];
-            grid_sum<R, 1>(s1, t, rb.sum_region<PT>(), sh, A.gs, c);
-            st.mark(10);  // K_PHP
-            const double pHp = t[0] + pHp_vert;
-            const double au = pmax > 0.0 ? D.dhat / (2.0 * pmax) : 0.0;
-            const double ab = -gp / pHp;
-            int capped;
-            if (!(pHp > 0.0) || !isfinite(ab)) { alpha = au; capped = 1; }
-            else if (ab < au) { alpha = ab; capped = 0; }
-            else { alpha = au; capped = 1; }
-            const double dE = -alpha * gp - 0.5 * alpha * alpha * pHp;
-            if (!isfinite(alpha) || !isfinite(gp)) { if (lead) flag_error(c, ERR_NONFINITE); alpha = 0.0; }
-            if ((volatile uint32_t &)c->err != 0u || converged) alpha = 0.0;
-            if (lead) {
-                c->beta = beta; c->restarted = restarted; c->gp = gp; c->pmax = pmax; c->pHp_vert = pHp_vert;
-                c->pHp = pHp; c->alpha_bar = ab; c->alpha_up = au; c->alpha = alpha; c->dE = dE; c->capped = capped;
-                c->n_active_last = na;
-                c->gPg_prev = gPg_prev;
-                if (!converged && (volatile uint32_t &)c->err == 0u) {
-                    if (k == 0) c->dE0 = dE;
-                    c->n_capped += capped;
-                    c->iters_done = k + 1;
-                    if (D.trace && k < D.iters) {
-                        double *tr = D.trace + (size_t)k * TRACE_COLS;
-                        tr[0] = beta; tr[1] = gp; tr[2] = pHp; tr[3] = pmax; tr[4] = alpha; tr[5] = dE;
-                        tr[6] = na; tr[7] = capped;
-                    }
+            for (int e = tid; e < D.nt; e += nthr) {
+                const int4 tv = D.tet[e];
+                s3[2].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
+                                         dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
+            }
+            for (int kk = tid; kk < na; kk += nthr) {
+                Active<R> ap;
+                load_active<R>(D, kk, ap);
+                s3[2].add_d(pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
+                                            dir_of<R>(D, ap.v.z, b, nzb), dir_of<R>(D, ap.v.w, b, nzb)));
+            }
+            Fetch f;
+            f.pe = &c->err;
+            PT *part = rb.sum_region<PT>();
+            block_publish<R, 3, true>(s3, pm, part, sh);
+            grid_barrier(br, c);
+            // the update's loads of this thread's own vertex go out before the partial collection and the step rule
+            if (tid < D.nv) {
+                uX = ldcg4(D.x + tid);
+                uP = ldcg4(D.pnext + tid);
+                uXT = ldcg4(D.xtil + tid);
+                uXB = disp_ref<R>(D, tid);
+            }
+            grid_collect<R, 3, true>(part, sh, &f);
+            st.mark(10);  // K_PHP (direction included)
+            // the step rule (Sec. 4.3) and the predicted decrease: scalar FP64 work, done by one thread
+            if (threadIdx.x == 0) {
+                const double gp = sh.res[0], pHp_vert = sh.res[1], pmax = sh.res[3];
+                uint32_t err = sh.fe;
+                const double pHp = sh.res[2] + pHp_vert;
+                const double au = pmax > 0.0 ? D.dhat / (2.0 * pmax) : 0.0;
+                const double ab = -gp / pHp;
+                double a;
+                int capped;
+                if (!(pHp > 0.0) || !isfinite(ab)) { a = au; capped = 1; }
+                else if (ab < au) { a = ab; capped = 0; }
+                else { a = au; capped = 1; }
+                const double dE = -a * gp - 0.5 * a * a * pHp;
+                if (!isfinite(a) || !isfinite(gp)) {
+                    if (lead) flag_error(c, ERR_NONFINITE);
+                    err |= ERR_NONFINITE;
+                    a = 0.0;
                 }
-                c->k = k + 1;
+                if (err != 0u || converged) a = 0.0;
+                if (lead) {
+                    c->beta = beta; c->restarted = restarted; c->gp = gp; c->pmax = pmax; c->pHp_vert = pHp_vert;
+                    c->pHp = pHp; c->alpha_bar = ab; c->alpha_up = au; c->alpha = a; c->dE = dE; c->capped = capped;
+                    c->n_active_last = na;
+                    c->gPg_prev = gPg_prev;
+                    if (!converged && err == 0u) {
+                        if (k == 0) c->dE0 = dE;
+                        c->n_capped += capped;
+                        c->iters_done = k + 1;
+                        if (D.trace && k < D.iters) {
+                            double *tr = D.trace + (size_t)k * TRACE_COLS;
+                            tr[0] = beta; tr[1] = gp; tr[2] = pHp; tr[3] = pmax; tr[4] = a; tr[5] = dE;
+                            tr[6] = na; tr[7] = capped;
+                        }
+                    }
+                    c->k = k + 1;
+                }
+                int cv = converged;
+                double e0 = dE0;
+                if (!cv && err == 0u) {
+                    if (k == 0) e0 = dE;
+                    if (D.eps > 0.0 && dE < D.eps * e0) cv = 1;
+                }
+                if (lead) { c->dE0 = e0; c->converged = cv; }
+                sh.o[2] = a;
+                sh.o[3] = e0;
+                sh.oi[0] = cv;
             }
-            if (!converged && (volatile uint32_t &)c->err == 0u) {
-                if (k == 0) dE0 = dE;
-                if (D.eps > 0.0 && dE < D.eps * dE0) converged = 1;
-            }
-            if (lead) { c->dE0 = dE0; c->converged = converged; }
+            __syncthreads();
+            alpha = sh.o[2];
+            dE0 = sh.o[3];
+            converged = sh.oi[0];
         }
         // ------------------------------------------------------------ a8: update
+        br.phase = 11;   // K_UPDATE
         {
             R md = R(0);
             for (int i = tid; i < D.nv; i += nthr) {
-                double4_32a X = ldcg4(D.x + i);
-                const R4 P = ldcg4(D.p + i);
+                double4_32a X, XT;
+                R4 P;
+                typename DispRef<R>::T XB;
+                if (i == tid) { X = uX; P = uP; XT = uXT; XB = uXB; }
+                else { X = ldcg4(D.x + i); P = ldcg4(D.pnext + i); XT = ldcg4(D.xtil + i); XB = disp_ref<R>(D, i); }
                 X.x += alpha * double(P.x); X.y += alpha * double(P.y); X.z += alpha * double(P.z);
                 put_x<R>(D, i, X);
-                init_vertex<R>(D, i, X, ldcg4(D.xtil + i), par ^ 1);
-                md = fmax(md, (R)disp2<R>(D, i, X));
+                D.p[i] = P;
+                init_vertex<R>(D, i, X, XT, par ^ 1);
+                md = fmax(md, disp2_from<R>(X, XB));
             }
             if (lead) c->n_active = 0;
-            const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, A.gs, c);
+            const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
             st.mark(11);  // K_UPDATE
             if ((double)m >= disp_lim * disp_lim) rebuild = 1;
         }
@@ -621,7 +744,8 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
 
     // ---------------------------------------------------------------- velocity update
     if (A.do_finish) {
-        grid_barrier(A.gs, c);
+        br.phase = 12;   // K_FINISH
+        grid_barrier(br, c);
         const bool bad = (volatile uint32_t &)c->err != 0u;
         for (int i = tid; i < D.nv; i += nthr) {
             const double4_32a X = ldcg4(D.x + i), XT = ldcg4(D.xt + i);
@@ -638,7 +762,7 @@ __global__ void __launch_bounds__(PB) k_persistent(Dev<R> D, BPDev B, PersistArg
             if (bad) { if (c->err_step < 0) c->err_step = (int)c->step; }
             else c->step += 1;
         }
-        grid_barrier(A.gs, c);
+        grid_barrier(br, c);
         st.mark(12);  // K_FINISH
     }
 }

@@ -56,6 +56,8 @@ public:
     virtual sim_status get_candidates(int32_t *idx, int32_t max, int32_t *count) = 0;
     virtual sim_status get_trace(double *buf, int32_t max_iters, int32_t *n) = 0;
     virtual sim_status profile_step(const double *targets, float *ms, int32_t *launches, int n_kernels) = 0;
+    virtual sim_status profile_barriers(const double *targets, uint64_t *arrive, uint64_t *depart, int32_t *kind,
+                                        int32_t max_bar, int32_t *n_bar, int32_t *n_blocks) = 0;
     virtual void sizes(int32_t *out) = 0;
 };
 

@@ -503,6 +503,37 @@ public:
         return sync_and_check();
     }
 
+    // the persistent step with every block's arrival and departure time at every grid barrier
+    sim_status profile_barriers(const double *targets, uint64_t *arrive, uint64_t *depart, int32_t *kind,
+                                int32_t max_bar, int32_t *n_bar, int32_t *n_blocks) override
+    {
+        CK(cudaSetDevice(dev));
+        if (!persist) return fail(SIM_ERR_INVALID_ARG, "barrier profiling needs the persistent step");
+        if (max_bar <= 0 || !arrive || !depart || !kind) return fail(SIM_ERR_INVALID_ARG, "no output buffers");
+        sim_status st = stage_targets(targets);
+        if (st != SIM_OK) return st;
+        const size_t nrec = (size_t)max_bar * pgrid;
+        unsigned long long *da = nullptr, *dd = nullptr;
+        int *dk = nullptr;
+        CK(cudaMalloc(&da, nrec * sizeof(unsigned long long)));
+        CK(cudaMalloc(&dd, nrec * sizeof(unsigned long long)));
+        CK(cudaMalloc(&dk, max_bar * sizeof(int)));
+        cudaError_t e = cudaMemsetAsync(dk, 0x7F, max_bar * sizeof(int), s);   // out-of-range kind marks the end
+        if (e == cudaSuccess) e = launch_persistent(1, 0, M.opt.iters, 1, nullptr, nullptr, 0, da, dd, dk, max_bar);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(arrive, da, nrec * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(depart, dd, nrec * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(kind, dk, max_bar * sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(da); cudaFree(dd); cudaFree(dk);
+        if (e != cudaSuccess) return cuda_fail(e, "profile_barriers", __LINE__);
+        k_host = M.opt.iters;
+        int n = 0;
+        while (n < max_bar && kind[n] >= 0 && kind[n] < (int)N_PROFILED) ++n;
+        *n_bar = n;
+        *n_blocks = pgrid;
+        return sync_and_check();
+    }
+
     void sizes(int32_t *out) override
     {
         out[0] = M.nv; out[1] = M.nt; out[2] = M.nf; out[3] = M.ne; out[4] = M.ns; out[5] = (int32_t)M.excl.size();
@@ -528,7 +559,7 @@ private:
     // persistent form
     bool persist = false;
     int pgrid = 0;
-    GridSync gsync{nullptr, nullptr};
+    unsigned int *bar_count = nullptr;
     void *ppart = nullptr;
     unsigned long long *stamp_buf = nullptr;
     int *stamp_kind = nullptr;
@@ -584,11 +615,15 @@ private:
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R>, PB, 0));
         if (per_sm <= 0) return SIM_OK;
         per_sm = std::min(per_sm, 4);
-        pgrid = per_sm * nsm;
+        pgrid = std::min(per_sm * nsm, MAXG);
         unsigned int *sync;
-        AL2(sync, 64);                    // count and gen on different 128-byte lines
-        gsync.count = sync;
-        gsync.gen = sync + 32;
+        AL2(sync, 32);                    // the barrier arrival counter on a 128-byte line of its own
+        bar_count = sync;
+        R4 *pg, *pnx;
+        AL2(pg, (size_t)M.nv);
+        AL2(pnx, (size_t)M.nv);
+        D.pg = pg;
+        D.pnext = pnx;
         const size_t bytes = 16 * (size_t)pgrid * sizeof(typename PartT<R>::T) + 2 * (size_t)pgrid * sizeof(R);
         char *pp;
         AL2(pp, bytes);
@@ -621,13 +656,14 @@ private:
         AL(D.x, nv); AL(D.xt, nv); AL(D.xtil, nv); AL(D.v, nv); AL(D.xb, nv);
         AL(D.g[0], nv); AL(D.g[1], nv); AL(D.dg[0], nv); AL(D.dg[1], nv); AL(D.p, nv);
         D.xh = D.xl = nullptr;
-        D.Xh = D.Xl = nullptr;
+        D.G0 = nullptr;
         D.xbh = nullptr;
+        D.pg = D.pnext = nullptr;
         if (sizeof(R) == 4) {
             AL(D.xh, nv); AL(D.xl, nv); AL(D.xbh, nv);
-            float4 *a, *b;
-            AL(a, nv); AL(b, nv);
-            D.Xh = a; D.Xl = b;
+            float *g0;
+            AL(g0, 12 * (size_t)nt);
+            D.G0 = g0;
         }
         double *mass; AL(mass, nv); D.mass = mass;
         int *fs; AL(fs, nv); D.fix_slot = fs;
@@ -746,19 +782,23 @@ private:
         if ((st = up(B.edge, ed.data(), sizeof(int4) * M.ne))) return st;
         if ((st = up(B.obj, M.obj.data(), sizeof(int) * nv))) return st;
         if (B.excl && (st = up(B.excl, M.excl.data(), sizeof(unsigned long long) * M.excl.size()))) return st;
-        if (D.Xh) {
-            std::vector<float4> hh(nv), ll(nv);
-            for (int i = 0; i < nv; ++i) {
-                float h3[3], l3[3];
-                for (int a = 0; a < 3; ++a) {
-                    h3[a] = (float)M.X[3 * i + a];
-                    l3[a] = (float)(M.X[3 * i + a] - (double)h3[a]);
-                }
-                hh[i] = make_float4(h3[0], h3[1], h3[2], 0.f);
-                ll[i] = make_float4(l3[0], l3[1], l3[2], 0.f);
+        if (D.G0) {
+            // rest metric Dm^T Dm per tet in double, stored as float-float
+            std::vector<float> g0(12 * (size_t)nt);
+            for (int e = 0; e < nt; ++e) {
+                double dm[3][3];
+                for (int c = 0; c < 3; ++c)
+                    for (int a = 0; a < 3; ++a) dm[a][c] = M.X[3 * (size_t)M.tet[4 * e + c + 1] + a] - M.X[3 * (size_t)M.tet[4 * e] + a];
+                int q = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = i; j < 3; ++j, ++q) {
+                        const double v = dm[0][i] * dm[0][j] + dm[1][i] * dm[1][j] + dm[2][i] * dm[2][j];
+                        const float hi = (float)v;
+                        g0[(size_t)q * nt + e] = hi;
+                        g0[(size_t)(6 + q) * nt + e] = (float)(v - (double)hi);
+                    }
             }
-            if ((st = up(D.Xh, hh.data(), sizeof(float4) * nv))) return st;
-            if ((st = up(D.Xl, ll.data(), sizeof(float4) * nv))) return st;
+            if ((st = up(D.G0, g0.data(), sizeof(float) * 12 * (size_t)nt))) return st;
         }
         refresh_ff();
         std::memset(hctrl, 0, sizeof(Ctrl));
@@ -875,15 +915,17 @@ private:
     }
     void launch_finish() { k_finish<R><<<nvb, VB, 0, s>>>(D); }
     cudaError_t launch_persistent(int do_predict, int k0, int n_iters, int do_finish, unsigned long long *stamps = nullptr,
-                                  int *kinds = nullptr, int max_stamps = 0)
+                                  int *kinds = nullptr, int max_stamps = 0, unsigned long long *arrive = nullptr,
+                                  unsigned long long *depart = nullptr, int *bar_kind = nullptr, int max_bar = 0)
     {
-        cudaError_t e = cudaMemsetAsync(gsync.count, 0, sizeof(unsigned int), s);
+        cudaError_t e = cudaMemsetAsync(bar_count, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
         PersistArgs A;
         A.do_predict = do_predict; A.k0 = k0; A.n_iters = n_iters; A.do_finish = do_finish;
-        A.gs = gsync;
+        A.count = bar_count;
         A.part = ppart;
         A.stamps = stamps; A.stamp_kind = kinds; A.max_stamps = max_stamps;
+        A.arrive = arrive; A.depart = depart; A.bar_kind = bar_kind; A.max_bar = max_bar;
         void *args[] = {(void *)&D, (void *)&B, (void *)&A};
         return cudaLaunchCooperativeKernel((const void *)k_persistent<R>, dim3(pgrid), dim3(PB), args, 0, s);
     }
