@@ -140,9 +140,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, prec_name: str):
+def recorded_traffic(kernel: str, prec_name: str, phases: bool = False):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_twisted_bar_{prec_name}.md")
+    form = "_phases" if phases else ""
+    path = os.path.join(ROOT, "profiles", f"{kernel}{form}_twisted_bar_{prec_name}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -248,7 +249,7 @@ def run_ours(args):
         dom = max((k for k in iter_kernels if prof.get(k, (0, 0))[1] > 0), key=lambda k: prof[k][0])
         per_launch_ms = prof[dom][0] / prof[dom][1]
         abytes = algorithmic_bytes(dom, 1, sizes, stp["n_candidates"], stp["n_active"])
-        traffic = recorded_traffic(dom, "fp32")
+        traffic = recorded_traffic(dom, "fp32", phases=True)
     else:
         # the persistent kernel: one launch per time step; its algorithmic bytes are those of the iteration
         # phases it ran (the candidate build is not counted), its duration the timed step
