@@ -48,7 +48,7 @@ typedef enum {
 enum { SIM_FP64 = 0, SIM_FP32_MIXED = 1 };                 /* sim_options.precision */
 enum { SIM_BETA_PR_PLUS = 0, SIM_BETA_DK = 1 };            /* sim_options.beta */
 enum { SIM_PNORM_VERTEX2 = 0, SIM_PNORM_COMPONENT_INF = 1 }; /* sim_options.pnorm */
-enum { SIM_SCATTER_ATOMIC = 0, SIM_SCATTER_SEGMENTED = 1 }; /* sim_options.scatter */
+enum { SIM_SCATTER_ATOMIC = 0, SIM_SCATTER_SEGMENTED = 1, SIM_SCATTER_BLOCK = 2 }; /* sim_options.scatter */
 
 /* Tetrahedral mesh and initial state (Sec. 3: x holds all vertex positions of the tet meshes). */
 typedef struct {
@@ -83,8 +83,11 @@ typedef struct {
                              since the last build; <= 0 = default 4 dhat */
     int32_t pnorm;        /* norm of p in alpha_upper = dhat / (2 ||p||): SIM_PNORM_VERTEX2 (largest per-vertex
                              Euclidean length, default) or SIM_PNORM_COMPONENT_INF (largest component) */
-    int32_t scatter;      /* gradient / diagonal scatter: SIM_SCATTER_ATOMIC (default) or SIM_SCATTER_SEGMENTED
-                             (per-vertex gather over a vertex-to-(tet, corner) CSR list, deterministic) */
+    int32_t scatter;      /* gradient / diagonal scatter of the tets: SIM_SCATTER_ATOMIC (default: one global
+                             atomic add per tet corner), SIM_SCATTER_BLOCK (each block of 256 consecutive tets
+                             sums its contributions per distinct vertex in shared memory and adds them to the
+                             global accumulators once) or SIM_SCATTER_SEGMENTED (per-vertex gather over a
+                             vertex-to-(tet, corner) CSR list, deterministic) */
     double excl_factor;   /* rest-pose exclusion radius in units of dhat (Sec. 5.1: 1.5; default 1.5; 0 = off) */
     void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = a stream owned by the library */
     int32_t use_graph;    /* 1 (default) = each time step is replayed from a captured CUDA graph */

@@ -19,7 +19,7 @@ SIM_OK, SIM_ERR_INVALID_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_INVERTED, SIM_ER
 SIM_FP64, SIM_FP32_MIXED = 0, 1
 SIM_BETA_PR_PLUS, SIM_BETA_DK = 0, 1
 SIM_PNORM_VERTEX2, SIM_PNORM_COMPONENT_INF = 0, 1
-SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED = 0, 1
+SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED, SIM_SCATTER_BLOCK = 0, 1, 2
 TRACE_COLUMNS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "n_active", "capped")
 
 

@@ -21,6 +21,11 @@ enum { TK_PREDICT = 0, TK_DOTS, TK_DIR, TK_PHP, TK_UPDATE, TK_SCAN, TK_ENERGY, T
 
 constexpr int TRACE_COLS = 8;   // beta, gp, pHp, pmax, alpha, dE, n_active, capped
 
+// block scatter of the tet contributions: chunks of SCATTER_CHUNK consecutive tets (one block of the tet loops);
+// chunks with more than SCATTER_MAXU distinct vertices fall back to global atomics
+constexpr int SCATTER_CHUNK = 256;
+constexpr int SCATTER_MAXU = 512;
+
 // Device-resident control block: every scalar of the iteration lives here, so no host round trip is needed
 // inside a time step.
 struct Ctrl {

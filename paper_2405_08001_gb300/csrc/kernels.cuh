@@ -14,6 +14,7 @@ namespace pncg {
 
 constexpr int VB = 128;   // threads per block, vertex kernels (148 blocks for the 18.8K-vertex bar: every SM busy)
 constexpr int EB = 256;   // threads per block, element / pair kernels
+static_assert(EB == SCATTER_CHUNK, "a tet block is one scatter chunk");
 
 template <typename R> struct Dev {
     typedef typename V4<R>::T R4;
@@ -50,6 +51,10 @@ template <typename R> struct Dev {
     R *contrib;
     const int *v2c_off, *v2c;          // v2c: 4*tet + corner
     int segmented;
+    // block scatter: distinct vertices of each chunk of SCATTER_CHUNK tets and the chunk-local corner indices
+    const int *cv_off, *cv;
+    const ushort4 *tloc;
+    int scatter_block;
     Ctrl *ctrl;
     double *part;                      // reduction partials
     double *trace;                     // [iters][TRACE_COLS]
@@ -260,6 +265,29 @@ template <typename R> __device__ inline void tet_material(const Dev<R> &D, int e
     if (D.escale) { R s = D.escale[e]; mu *= s; lam *= s; }
 }
 
+// The per-tet constants a gradient evaluation streams in (coalesced, structure-of-arrays in memory): indices,
+// D_m^-1, h^2 V, the Young's modulus scale and, in the FP32 form, the float-float rest metric.
+template <typename R> struct TetIn {
+    int4 tv;
+    R w[3][3];
+    R hv, es;
+    float g0[12];   // FP32 form: rest metric entries 00 01 02 11 12 22, heads then tails
+};
+template <typename R> __device__ inline void load_tet_in(const Dev<R> &D, int e, TetIn<R> &in)
+{
+    in.tv = D.tet[e];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) in.w[r][c] = D.Dm[(3 * r + c) * D.nt + e];
+    in.hv = D.hv[e];
+    in.es = D.escale ? D.escale[e] : R(1);
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) in.g0[q] = D.G0[q * D.nt + e];
+    }
+}
+
 // First Piola-Kirchhoff stress of the FP32 form, evaluated from the metric change so that it stays accurate for
 // small strains under any rotation.  With C = F^T F and the Neo-Hookean density of Sec. 3.1 written in C,
 //   P = F C^-1 (mu (C - I) + lambda log J I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
@@ -267,16 +295,17 @@ template <typename R> __device__ inline void tet_material(const Dev<R> &D, int e
 // accumulated in float-float from the float-float current positions and the tet's float-float rest metric, so that
 // rounding never acts on the O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the
 // entries of C - I.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
-__device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 &tv, TetF<float> &T, float P[3][3],
+__device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float> &in, TetF<float> &T, float P[3][3],
                                          float &Psi33)
 {
+    const int4 tv = in.tv;
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
     float4 xh[4], xl[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) { xh[k] = ldcg4(D.xh + vid[k]); xl[k] = ldcg4(D.xl + vid[k]); }
     float g0h[6], g0l[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) { g0h[q] = D.G0[q * D.nt + e]; g0l[q] = D.G0[(6 + q) * D.nt + e]; }
+    for (int q = 0; q < 6; ++q) { g0h[q] = in.g0[q]; g0l[q] = in.g0[6 + q]; }
     ffl ds[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -299,7 +328,10 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) dsf[a][c] = ff_val(ds[a][c]);
-    load_w<float>(D, e, T.w);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
     tet_F_from<float>(dsf, T);
     if (!(T.J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
     // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc)
@@ -320,8 +352,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 
     const float dC = (A[0][0] + A[1][1] + A[2][2]) + (m01 + m02 + m12) + detA;   // det C - 1
     const float detC = 1.0f + dC;
     const float L = 0.5f * log1pf(dC);                                             // log J
-    float mu, lam;
-    tet_material<float>(D, e, mu, lam);
+    const float mu = D.mu * in.es, lam = D.lam * in.es;
     // C^-1 = cof(C) / det C (C symmetric)
     const float c00 = 1.0f + A[0][0], c11 = 1.0f + A[1][1], c22 = 1.0f + A[2][2];
     const float ic = 1.0f / detC;
@@ -342,7 +373,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) S[a][b] = Ci[a][0] * M[0][b] + Ci[a][1] * M[1][b] + Ci[a][2] * M[2][b];
-    const float sc = D.hv[e];
+    const float sc = in.hv;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -352,21 +383,28 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, int e, const int4 
 }
 
 // Element gradient and Jacobi diagonal (Sec. 3.1 split; NH has Psi_22 = 0 and the H3 term has a zero
-// diagonal, so diag_i[a] = h^2 V (mu |w_i|^2 + Psi_33 (cof(F) w_i)_a^2)).
+// diagonal, so diag_i[a] = h^2 V (mu |w_i|^2 + Psi_33 (cof(F) w_i)_a^2)).  The contributions go to the
+// per-(tet, corner) buffer (segmented scatter), to the block's shared accumulators sacc ([6][SCATTER_MAXU],
+// indexed by the chunk-local vertex; block scatter) or straight to the global accumulators.
 template <typename R>
-__device__ inline void tet_grad(const Dev<R> &D, int e, int par)
+__device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> &in, R *sacc = nullptr)
 {
-    const int4 tv = D.tet[e];
+    const int4 tv = in.tv;
     TetF<R> T;
-    R P[3][3], Psi33, mu, lam;
-    const R sc = D.hv[e];
+    R P[3][3], Psi33;
+    const R sc = in.hv;
+    const R mu = D.mu * in.es, lam = D.lam * in.es;
     if constexpr (sizeof(R) == 4) {
-        if (!tet_stress_metric(D, e, tv, T, P, Psi33)) return;
-        tet_material<R>(D, e, mu, lam);
+        if (!tet_stress_metric(D, in, T, P, Psi33)) return;
     } else {
-        tet_F<R>(D, e, tv, T);
+        R ds[3][3];
+        tet_ds<R>(D, tv, ds);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
+        tet_F_from<R>(ds, T);
         if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return; }
-        tet_material<R>(D, e, mu, lam);
         const R L = log(T.J);
         const R Psi3 = (lam * L - mu) / T.J;
         Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
@@ -411,11 +449,55 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par)
             }
         return;
     }
+    if (sacc) {
+        const ushort4 lc = D.tloc[e];
+        const int loc[4] = {lc.x, lc.y, lc.z, lc.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicAdd(sacc + a * SCATTER_MAXU + loc[i], gv[i][a]);
+                atomicAdd(sacc + (3 + a) * SCATTER_MAXU + loc[i], dv[i][a]);
+            }
+        return;
+    }
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         atomic_add4<R>(&D.g[par][vid[i]], gv[i][0], gv[i][1], gv[i][2]);
         atomic_add4<R>(&D.dg[par][vid[i]], dv[i][0], dv[i][1], dv[i][2]);
+    }
+}
+
+// The tets of chunk ch (SCATTER_CHUNK consecutive tets, one per thread of the block): gradient and diagonal,
+// block-scattered when the chunk's distinct vertices fit the shared accumulators.  Called by all threads of a
+// block with a block-uniform ch.
+template <typename R>
+__device__ inline void tet_grad_chunk(const Dev<R> &D, int ch, int par, R *sacc)
+{
+    const int e = ch * SCATTER_CHUNK + (int)threadIdx.x;
+    int u0 = 0, nu = 0;
+    if (D.scatter_block) { u0 = D.cv_off[ch]; nu = D.cv_off[ch + 1] - u0; }
+    const bool blk = D.scatter_block && nu <= SCATTER_MAXU;
+    if (blk) {
+        for (int q = threadIdx.x; q < 6 * SCATTER_MAXU; q += blockDim.x) {
+            if ((q % SCATTER_MAXU) < nu) sacc[q] = R(0);
+        }
+        __syncthreads();
+    }
+    if (e < D.nt) {
+        TetIn<R> in;
+        load_tet_in<R>(D, e, in);
+        tet_grad<R>(D, e, par, in, blk ? sacc : nullptr);
+    }
+    if (blk) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+            const int v = D.cv[u0 + u];
+            atomic_add4<R>(&D.g[par][v], sacc[u], sacc[SCATTER_MAXU + u], sacc[2 * SCATTER_MAXU + u]);
+            atomic_add4<R>(&D.dg[par][v], sacc[3 * SCATTER_MAXU + u], sacc[4 * SCATTER_MAXU + u], sacc[5 * SCATTER_MAXU + u]);
+        }
+        __syncthreads();
     }
 }
 
@@ -545,8 +627,8 @@ __global__ void __launch_bounds__(EB) k_grad(Dev<R> D, int par, int ntb)
         if (c->n_cand > D.cand_cap) flag_error(c, ERR_CAPACITY);
     }
     if ((int)blockIdx.x < ntb) {
-        const int e = blockIdx.x * blockDim.x + threadIdx.x;
-        if (e < D.nt) tet_grad<R>(D, e, par);
+        __shared__ R sacc[6 * SCATTER_MAXU];
+        tet_grad_chunk<R>(D, blockIdx.x, par, sacc);
     } else {
         const int nc = min(D.ctrl->n_cand, D.cand_cap);
         const int stride = (gridDim.x - ntb) * blockDim.x;

@@ -356,6 +356,11 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
     __shared__ __align__(16) unsigned char sh_raw[sizeof(PShared<R>)];   // raw storage: Acc has initialisers
     PShared<R> &sh = *reinterpret_cast<PShared<R> *>(sh_raw);
     __shared__ int sh_i;
+    // one buffer for two phases: the gradient's block-scatter accumulators and the candidate build's chunk offsets
+    constexpr size_t SBUF = sizeof(R) * 6 * SCATTER_MAXU > sizeof(unsigned int) * BP_MAX_CHUNKS
+                                ? sizeof(R) * 6 * SCATTER_MAXU : sizeof(unsigned int) * BP_MAX_CHUNKS;
+    __shared__ __align__(16) unsigned char sbuf[SBUF];
+    static_assert(PB == SCATTER_CHUNK, "a block's tet loop covers one scatter chunk");
     Ctrl *c = D.ctrl;
     RedBufs rb;
     rb.base = A.part;
@@ -477,7 +482,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             // every block scans the chunk totals into shared memory; the buckets' global offsets go to goff for
             // the queries, and the entries to their slots
             br.phase = 4;   // K_BP_FILL
-            __shared__ unsigned int choff[BP_MAX_CHUNKS];
+            unsigned int *choff = reinterpret_cast<unsigned int *>(sbuf);   // [BP_MAX_CHUNKS]
             {
                 const int per = (nchunk + PB - 1) / PB;   // chunks per thread (nchunk <= BP_MAX_CHUNKS)
                 const int c0 = threadIdx.x * per;
@@ -536,7 +541,17 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             c->rebuild = 0;
             if (ncand > D.cand_cap) flag_error(c, ERR_CAPACITY);
         }
-        for (int e = tid; e < D.nt; e += nthr) tet_grad<R>(D, e, par);
+        if (D.scatter_block) {
+            const int nch = (D.nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
+            for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+                tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
+        } else {
+            for (int e = tid; e < D.nt; e += nthr) {
+                TetIn<R> in;
+                load_tet_in<R>(D, e, in);
+                tet_grad<R>(D, e, par, in);
+            }
+        }
         {
             const int nc = min(ncand, D.cand_cap);
             for (int ci = tid; ci < nc; ci += nthr) pair_grad<R>(D, ci, par);

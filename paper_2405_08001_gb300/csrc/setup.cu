@@ -115,7 +115,7 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         return SIM_ERR_INVALID_ARG;
     }
     if (opt.iters <= 0 || opt.beta < 0 || opt.beta > 1 || opt.pnorm < 0 || opt.pnorm > 1 || opt.precision < 0 ||
-        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 1) {
+        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 2) {
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }
@@ -229,6 +229,22 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
     m.v2c.assign(4 * (size_t)nt, 0);
     std::vector<int> cur(m.v2c_off.begin(), m.v2c_off.end() - 1);
     for (int q = 0; q < 4 * nt; ++q) m.v2c[cur[m.tet[q]]++] = q;
+    // block-scatter tables
+    const int nchunk = (nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
+    m.cv_off.assign(nchunk + 1, 0);
+    m.cv.clear();
+    m.tloc.assign(4 * (size_t)nt, 0);
+    std::vector<int> ids;
+    for (int c = 0; c < nchunk; ++c) {
+        const int e0 = c * SCATTER_CHUNK, e1 = std::min(nt, e0 + SCATTER_CHUNK);
+        ids.assign(m.tet.begin() + 4 * (size_t)e0, m.tet.begin() + 4 * (size_t)e1);
+        std::sort(ids.begin(), ids.end());
+        ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+        for (int q = 4 * e0; q < 4 * e1; ++q)
+            m.tloc[q] = (unsigned short)(std::lower_bound(ids.begin(), ids.end(), m.tet[q]) - ids.begin());
+        m.cv.insert(m.cv.end(), ids.begin(), ids.end());
+        m.cv_off[c + 1] = (int)m.cv.size();
+    }
     return SIM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/pncg.h"
+#include "common.cuh"
 
 namespace pncg {
 
@@ -29,7 +30,12 @@ struct HostMesh {
     std::vector<int> fix_slot;             // [nv] slot in the targets array or -1
     std::vector<unsigned long long> excl;  // sorted keys (type << 62 | a << 31 | b) of excluded pairs
     std::vector<int> v2c_off, v2c;         // vertex -> 4 * tet + corner CSR
+    // block scatter: per chunk of SCATTER_CHUNK consecutive tets, its distinct vertices (sorted) and, per tet,
+    // the chunk-local index of each corner
+    std::vector<int> cv_off, cv;           // [nchunk + 1], [sum of distinct counts]
+    std::vector<unsigned short> tloc;      // [nt][4]
 };
+
 
 // Builds the HostMesh; returns SIM_OK or an error with a message.
 sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double dt, double dhat, double kappa,

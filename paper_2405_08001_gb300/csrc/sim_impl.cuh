@@ -686,6 +686,13 @@ private:
         }
         D.beta_rule = M.opt.beta; D.pnorm = M.opt.pnorm; D.iters = M.opt.iters;
         D.segmented = M.opt.scatter == SIM_SCATTER_SEGMENTED;
+        D.scatter_block = M.opt.scatter == SIM_SCATTER_BLOCK;
+        D.cv_off = nullptr; D.cv = nullptr; D.tloc = nullptr;
+        if (D.scatter_block) {
+            int *co; AL(co, M.cv_off.size()); D.cv_off = co;
+            int *cvv; AL(cvv, std::max<size_t>(M.cv.size(), 1)); D.cv = cvv;
+            ushort4 *tl; AL(tl, (size_t)nt); D.tloc = tl;
+        }
         D.contrib = nullptr; D.v2c_off = nullptr; D.v2c = nullptr;
         if (D.segmented) {
             R *cb; AL(cb, 6 * 4 * (size_t)nt); D.contrib = cb;
@@ -778,6 +785,11 @@ private:
         if ((st = up(D.Dm, Dm.data(), sizeof(R) * 9 * nt))) return st;
         if ((st = up(D.hv, hv.data(), sizeof(R) * nt))) return st;
         if (D.escale && (st = up(D.escale, es.data(), sizeof(R) * nt))) return st;
+        if (D.scatter_block) {
+            if ((st = up(D.cv_off, M.cv_off.data(), sizeof(int) * M.cv_off.size()))) return st;
+            if (!M.cv.empty() && (st = up(D.cv, M.cv.data(), sizeof(int) * M.cv.size()))) return st;
+            if ((st = up(D.tloc, M.tloc.data(), sizeof(unsigned short) * 4 * (size_t)nt))) return st;
+        }
         if (D.segmented) {
             if ((st = up(D.v2c_off, M.v2c_off.data(), sizeof(int) * (nv + 1)))) return st;
             if ((st = up(D.v2c, M.v2c.data(), sizeof(int) * 4 * nt))) return st;

@@ -286,18 +286,21 @@ def test_twisted_bar_full_size(B, O, prec):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_equals_eager_and_segmented_is_deterministic(B, prec):
     """Free fall of the drop config (no contact): with the segmented scatter nothing is order-dependent, so graph
-    replay and eager launches give bitwise equal states; the atomic scatter agrees to rounding."""
+    replay and eager launches give bitwise equal states; the atomic and block scatters agree to rounding."""
     sc = S.cube_drop()
     out = {}
-    for name, use_graph, scatter in (("graph", 1, 1), ("eager", 0, 1), ("again", 1, 1), ("atomic", 1, 0)):
+    for name, use_graph, scatter in (("graph", 1, B.SIM_SCATTER_SEGMENTED), ("eager", 0, B.SIM_SCATTER_SEGMENTED),
+                                     ("again", 1, B.SIM_SCATTER_SEGMENTED), ("atomic", 1, B.SIM_SCATTER_ATOMIC),
+                                     ("block", 1, B.SIM_SCATTER_BLOCK)):
         sim = B.Sim(sc, precision=prec, use_graph=use_graph, scatter=scatter)
         sim.step(3)
         out[name] = sim.state()[0]
         sim.close()
     assert np.array_equal(out["graph"], out["eager"])
     assert np.array_equal(out["graph"], out["again"])
-    # 150 iterations amplify the order-dependent rounding of the atomic scatter (about 1e3 times)
-    assert rel(out["atomic"] - sc.x0, out["graph"] - sc.x0) < (1e-9 if prec == 0 else 1e-3)
+    # 150 iterations amplify the order-dependent rounding of the atomic scatters (about 1e3 times)
+    for name in ("atomic", "block"):
+        assert rel(out[name] - sc.x0, out["graph"] - sc.x0) < (1e-9 if prec == 0 else 1e-3), name
 
 
 def test_inverted_input_is_reported_and_state_kept(B):
