@@ -291,6 +291,43 @@ def run_ours(args):
         sim.close()
         e2e = {"value": round(K * iters / te, 2), "unit": UNIT, "ms_per_step": round(1e3 * te / K, 4),
                "h2d_bytes_per_step": int(tg_host[0].numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 8)}
+    # the large pile (ten 16x16x64 bars, 983,040 tets): the same kernels at a size whose working set exceeds L2
+    pile = None
+    if not args.no_pile:
+        psc = S.pile()
+        psim = B.Sim(psc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
+                     persistent=0 if args.phases else 1)
+        PW, PK = 3, 5
+        for s in range(PW):
+            B.sim_step_async(psim.h, 1, None)
+        torch.cuda.synchronize()
+        B.sim_get_state(psim.h, want_x=False, want_v=False)
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(PK)]
+        for s in range(PK):
+            flush.zero_()
+            pev[s][0].record(stream)
+            B.sim_step_async(psim.h, 1, None)
+            pev[s][1].record(stream)
+        torch.cuda.synchronize()
+        pms = sum(a.elapsed_time(b) for a, b in pev) / PK
+        pprof = B.sim_profile_step(psim.h, None)
+        _, _, pst = B.sim_get_state(psim.h, want_x=False, want_v=False)
+        psizes = psim.sizes()
+        pbytes = sum(algorithmic_bytes(k, 1, psizes, pst["n_candidates"], pst["n_active"], persistent=not args.phases)
+                     * pprof[k][1] for k in ("k_grad", "k_pHp", "k_dots", "k_dir", "k_update") if pprof.get(k, (0, 0))[1] > 0)
+        pach = pbytes / (pms * 1e-3) / 1e9
+        pile = {"workload": "large pile: ten 16x16x64-cell bars (983,040 tets, 187,850 verts) stacked criss-cross on "
+                            "a plane, E=2e5 nu=0.4, dt=1/30, dhat=5e-4, 50 NCG iterations per step, FP32-mixed",
+                "value": round(psc.iters / (pms * 1e-3), 2), "unit": UNIT, "ms_per_step": round(pms, 4),
+                "steps": PK, "warmup": PW,
+                "roofline": {"bound": "hbm", "kernel": "k_persistent" if not args.phases else "all iteration kernels",
+                             "achieved": round(pach, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": round(pach / peak, 4), "algorithmic_bytes_per_step": int(pbytes)},
+                "phases_us_per_iteration": {k: round(1e3 * v[0] / v[1], 2) for k, v in pprof.items()
+                                            if v[1] > 0 and k.startswith("k_")},
+                "stats_last_step": {k: pst[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")}}
+        psim.close()
+
     clocks = sampler.stop()
 
     cpu = None
@@ -319,6 +356,7 @@ def run_ours(args):
                          "traffic": traffic, "algorithmic_bytes_per_launch": int(abytes),
                          "us_per_launch": round(per_launch_ms * 1e3, 3)},
             "kernels": kernels,
+            "large_pile": pile,
             "stats_last_step": {k: st32[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")},
             "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clocks, "cpu_baseline": cpu,
         }
@@ -406,6 +444,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="one kernel per phase instead of the persistent step")
+    ap.add_argument("--no-pile", action="store_true", help="skip the large-pile measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
