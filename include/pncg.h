@@ -59,6 +59,12 @@ typedef struct {
     const double *v0;       /* [n_verts][3] host, initial velocities; NULL = 0 */
     const uint8_t *fixed;   /* [n_verts] host, 1 = kinematic (Dirichlet) vertex whose position is prescribed
                                per step and whose g and p entries are held at zero; NULL = none */
+    const int32_t *scene_of_vert; /* [n_verts] host, batching: the independent scene each vertex belongs to,
+                               0 .. n_scenes-1, non-decreasing over the vertices; every tet lies in one scene and
+                               the tets are ordered by scene.  Each scene is its own PNCG problem (own beta,
+                               alpha, max |p_v| and eps rule: the per-object splitting of Sec. 5.2 applied to
+                               independent scenes) and no contact pair spans two scenes.  At most 1024 scenes;
+                               needs the persistent form.  NULL = one scene */
 } sim_mesh;
 
 /* Neo-Hookean material (Sec. 3.1): mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)). */
@@ -282,6 +288,14 @@ const char *sim_status_string(sim_status s);
 
 /* ABI version of the library (incremented on incompatible changes). */
 int32_t sim_abi_version(void);
+
+/*
+ * Batching: the scalars of the most recent iteration per scene, rows {beta, g^T p, p^T H p (with p^T M p),
+ * max_v |p_v|, alpha, Delta E, Delta E of iteration 0, converged, iterations done, restarted, capped}.
+ * out: host [max_scenes][11]; *n_scenes receives the number of scenes (1 without scene_of_vert, whose row repeats
+ * the sim_iter_scalars of sim_get_iterate).  Synchronises.
+ */
+sim_status sim_get_scene_scalars(sim_handle h, double *out, int32_t max_scenes, int32_t *n_scenes);
 
 #ifdef __cplusplus
 }

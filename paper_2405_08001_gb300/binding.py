@@ -25,7 +25,7 @@ TRACE_COLUMNS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "n_active", "capped
 
 class sim_mesh(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_x", C.c_void_p), ("tets", C.c_void_p),
-                ("x0", C.c_void_p), ("v0", C.c_void_p), ("fixed", C.c_void_p)]
+                ("x0", C.c_void_p), ("v0", C.c_void_p), ("fixed", C.c_void_p), ("scene_of_vert", C.c_void_p)]
 
 
 class sim_material(C.Structure):
@@ -102,6 +102,7 @@ def load():
         "sim_get_trace": (C.c_int, [P, P, I32, P]),
         "sim_profile_step": (C.c_int, [P, P, P, P, I32]),
         "sim_profile_barriers": (C.c_int, [P, P, P, P, P, I32, P, P]),
+        "sim_get_scene_scalars": (C.c_int, [P, P, I32, P]),
         "sim_kernel_count": (I32, []),
         "sim_kernel_name": (C.c_char_p, [I32]),
         "sim_get_sizes": (C.c_int, [P, P]),
@@ -155,7 +156,7 @@ def sim_default_options() -> sim_options:
 
 
 def sim_create(rest_x, tets, *, density, youngs, poisson, dt, dhat, kappa, x0=None, v0=None, fixed=None,
-               youngs_per_tet=None, options: sim_options | None = None):
+               youngs_per_tet=None, scene_of_vert=None, options: sim_options | None = None):
     """sim_create with host arrays; returns the opaque handle (a c_void_p value)."""
     lib = load()
     rx = np.ascontiguousarray(rest_x, dtype=np.float64).reshape(-1, 3)
@@ -165,7 +166,8 @@ def sim_create(rest_x, tets, *, density, youngs, poisson, dt, dhat, kappa, x0=No
     m = sim_mesh()
     m.n_verts, m.n_tets = nv, tt.shape[0]
     m.rest_x, m.tets = rx.ctypes.data, tt.ctypes.data
-    for name, arr, dt_ in (("x0", x0, np.float64), ("v0", v0, np.float64), ("fixed", fixed, np.uint8)):
+    for name, arr, dt_ in (("x0", x0, np.float64), ("v0", v0, np.float64), ("fixed", fixed, np.uint8),
+                           ("scene_of_vert", scene_of_vert, np.int32)):
         if arr is not None:
             a = np.ascontiguousarray(arr, dtype=dt_)
             keep.append(a)
@@ -341,6 +343,18 @@ def sim_profile_barriers(h, targets=None, max_barriers=4096, max_blocks=4096):
     return flat_a, flat_d, [names[k] for k in kind[:n]]
 
 
+SCENE_SCALAR_COLS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "dE0", "converged", "iters_done", "restarted",
+                     "capped")
+
+
+def sim_get_scene_scalars(h, max_scenes=1024):
+    """Per-scene scalars of the most recent iteration: a dict of arrays [n_scenes] named by SCENE_SCALAR_COLS."""
+    out = np.zeros((max_scenes, len(SCENE_SCALAR_COLS)))
+    n = C.c_int32(0)
+    _check(load().sim_get_scene_scalars(h, out.ctypes.data, max_scenes, C.byref(n)), h)
+    return {c: out[: n.value, i].copy() for i, c in enumerate(SCENE_SCALAR_COLS)}
+
+
 def sim_pHp_noalloc(x, p, rest_x, tets, mass, youngs, poisson, dt, out, stream=None):
     """Allocation-free p^T H p (inertia + elastic, no contact) on caller-owned CUDA tensors; asynchronous on
     `stream` (a torch.cuda.Stream or None).  out: a 1-element float64 CUDA tensor."""
@@ -388,7 +402,7 @@ class Sim:
         self.h = sim_create(scene.rest_x, scene.tets, density=scene.density, youngs=scene.youngs,
                             poisson=scene.poisson, dt=scene.dt, dhat=scene.dhat, kappa=scene.kappa, x0=scene.x0,
                             v0=scene.v0, fixed=scene.fixed, youngs_per_tet=scene.youngs_per_tet,
-                            options=self.options)
+                            scene_of_vert=scene.scene_of_vert, options=self.options)
         self.nv = scene.n_verts
 
     def close(self):

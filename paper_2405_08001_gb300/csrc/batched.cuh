@@ -1,0 +1,292 @@
+// Batched form of the persistent step: many independent scenes in one launch (the vertices and tets of each scene
+// contiguous, scene ids non-decreasing).  Each scene is its own PNCG problem -- own beta, direction scale, max |p_v|,
+// alpha and eps rule: the per-object splitting of Sec. 5.2 applied to scenes that share no contact -- while the
+// gradient pass, the candidate build and the grid barriers are shared.
+//
+// Per-scene sums: the lanes of a warp take consecutive vertices (tets), so their scene ids are non-decreasing; a
+// segmented warp scan adds up each run of equal ids and the run's last lane adds it to the scene's accumulator
+// with a double atomic.  Accumulators are used round robin over three buffers: reduction r accumulates into buffer
+// r % 3 and zeroes buffer (r + 1) % 3 for the next one, which every block last read before the barrier of
+// reduction r - 1.  After the barrier every block computes all scenes' scalars itself (identical values) into
+// shared memory; block 0 also writes them to the per-scene state.
+#pragma once
+
+// included by persistent.cuh after its accumulators, reductions and barrier
+
+namespace pncg {
+
+template <typename R> __device__ inline unsigned long long max_bits(R v);
+template <> __device__ inline unsigned long long max_bits<float>(float v) { return (unsigned long long)__float_as_uint(v); }
+template <> __device__ inline unsigned long long max_bits<double>(double v) { return (unsigned long long)__double_as_longlong(v); }
+template <typename R> __device__ inline double max_value(unsigned long long b);
+template <> __device__ inline double max_value<float>(unsigned long long b) { return (double)__uint_as_float((unsigned int)b); }
+template <> __device__ inline double max_value<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Segmented sum over the warp's lanes (equal keys contiguous; key < 0 = no item): the last lane of each run adds
+// the run's N sums to acc[key * 8 + q0 + q].
+template <typename R, int N>
+__device__ inline void seg_warp_sum(Acc<R> (&a)[N], int key, double *acc, int q0)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ku = __shfl_up_sync(0xffffffffu, key, o);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const Acc<R> u = a[q].shfl_up(o);
+            if (lane >= o && ku == key) a[q].add(u);
+        }
+    }
+    const int kn = __shfl_down_sync(0xffffffffu, key, 1);
+    if (key >= 0 && (lane == 31 || kn != key)) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) atomicAdd(acc + (size_t)key * 8 + q0 + q, a[q].value());
+    }
+}
+
+// Segmented max of non-negative values, published as bits (monotone for non-negative floats and doubles).
+template <typename R>
+__device__ inline void seg_warp_max(R m, int key, unsigned long long *mx)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ku = __shfl_up_sync(0xffffffffu, key, o);
+        const R mu = __shfl_up_sync(0xffffffffu, m, o);
+        if (lane >= o && ku == key) m = fmax(m, mu);
+    }
+    const int kn = __shfl_down_sync(0xffffffffu, key, 1);
+    if (key >= 0 && (lane == 31 || kn != key)) atomicMax(mx + key, max_bits<R>(m));
+}
+
+// zeroes the accumulators reduction r + 1 will use
+__device__ inline void seg_zero_next(double *sacc, unsigned long long *smax, int nseg, int r, int tid, int nthr)
+{
+    double *a = sacc + (size_t)((r + 1) % 3) * nseg * 8;
+    unsigned long long *m = smax + (size_t)((r + 1) % 3) * nseg;
+    for (int q = tid; q < nseg * 8; q += nthr) a[q] = 0.0;
+    for (int q = tid; q < nseg; q += nthr) m[q] = 0ull;
+}
+
+// Resets the per-scene state at the start of a time step (block 0; iteration 0 reads parity 1).
+template <typename R> __device__ inline void seg_reset(const Dev<R> &D)
+{
+    if (blockIdx.x != 0) return;
+    for (int s = threadIdx.x; s < D.nseg; s += blockDim.x) {
+        D.seg[s].gPg[1] = 0.0;
+        D.seg[s].dE0[1] = 0.0;
+        D.seg[s].converged[1] = 0;
+        D.seg[s].iters_done = 0;
+    }
+}
+
+// Beta, direction + p^T H p, and update phases of iteration k for nseg > 1 scenes (three grid barriers, as in the
+// single-scene form).  sbuf holds the scenes' beta and alpha (2 x MAX_SCENES doubles).  Returns 1 when some vertex
+// has moved far enough since the candidate build to need a new one.
+template <typename R>
+__device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, unsigned char *sbuf, Bar &br,
+                                   Stamper &st, RedBufs &rb, int k, int par, int &sred, double disp_lim)
+{
+    typedef typename V4<R>::T R4;
+    typedef typename PartT<R>::T PT;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const int ns = D.nseg;
+    const int rp = (k - 1) & 1, wp = k & 1;
+    double *sbeta = reinterpret_cast<double *>(sbuf);
+    double *salpha = sbeta + MAX_SCENES;
+
+    // ------------------------------------------------------------ beta (per scene) and P g
+    br.phase = 8;   // K_DOTS
+    {
+        double *acc = D.sacc + (size_t)(sred % 3) * ns * 8;
+        seg_zero_next(D.sacc, D.smax, ns, sred, tid, nthr);
+        for (int base = tid - lane; base < D.nv; base += nthr) {
+            const int i = base + lane;
+            Acc<R> a5[5];
+            int key = -1;
+            if (i < D.nv) {
+                key = D.vscene[i];
+                const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i);
+                const R4 P0 = ldcg4(D.p + i);
+                R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
+                if (Dg.w > R(0)) {
+                    const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
+                    R t5[5] = {0, 0, 0, 0, 0}, pg[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const R P = precond<R>(dv[a], Dg.w);
+                        const R g = gv[a], y = g - g0[a];
+                        pg[a] = g * P;
+                        if (D.beta_rule == 0) {
+                            t5[0] += pg[a] * y; t5[1] += pg[a] * g; t5[2] += g * p0[a];
+                        } else {
+                            t5[0] += pg[a] * y; t5[1] += y * P * y; t5[2] += y * p0[a]; t5[3] += p0[a] * g; t5[4] += pg[a] * g;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) a5[q].add(t5[q]);
+                    PG = mk4<R>(pg[0], pg[1], pg[2], R(0));
+                } else if (P0.x != R(0) || P0.y != R(0) || P0.z != R(0)) {
+                    D.p[i] = PG;   // a kinematic vertex never moves along p
+                }
+                D.pg[i] = PG;
+            }
+            seg_warp_sum<R, 5>(a5, key, acc, 0);
+        }
+        grid_barrier(br, c);
+        if (threadIdx.x == 0) sh.fi = (volatile const int &)c->n_active;
+        for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+            double t[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) t[q] = __ldcg(acc + (size_t)s * 8 + q);
+            const double gprev = __ldcg(&D.seg[s].gPg[rp]);
+            double bt = 0.0, gPg, gp_new;
+            int rs = 0;
+            if (D.beta_rule == 0) {
+                gPg = t[1];
+                if (k > 0) { bt = gprev > 0.0 ? t[0] / gprev : 0.0; if (bt < 0.0) bt = 0.0; }
+                gp_new = -gPg + bt * t[2];
+            } else {
+                gPg = t[4];
+                if (k > 0) bt = fabs(t[2]) < 1e-30 ? 0.0 : t[0] / t[2] - (t[1] / t[2]) * (t[3] / t[2]);
+                gp_new = -gPg + bt * t[3];
+            }
+            if (gp_new >= 0.0 && bt != 0.0) { bt = 0.0; rs = 1; }
+            sbeta[s] = bt;
+            if (blockIdx.x == 0) { D.seg[s].gPg[wp] = gPg; D.seg[s].beta = bt; D.seg[s].restarted = rs; }
+        }
+        __syncthreads();
+        st.mark(8);   // K_DOTS
+        ++sred;
+    }
+    const int na = sh.fi;
+
+    // ------------------------------------------------------------ direction, p^T H p and the step (per scene)
+    br.phase = 10;   // K_PHP
+    {
+        double *acc = D.sacc + (size_t)(sred % 3) * ns * 8;
+        unsigned long long *mx = D.smax + (size_t)(sred % 3) * ns;
+        seg_zero_next(D.sacc, D.smax, ns, sred, tid, nthr);
+        for (int base = tid - lane; base < D.nv; base += nthr) {
+            const int i = base + lane;
+            Acc<R> a2[2];
+            R pmv = R(0);
+            int key = -1;
+            if (i < D.nv) {
+                key = D.vscene[i];
+                const double bd = sbeta[key];
+                const R4 Dg = ldcg4(D.dg[par] + i);
+                R4 Pn = mk4<R>(R(0), R(0), R(0), R(0));
+                if (Dg.w > R(0)) {
+                    const R4 G = ldcg4(D.g[par] + i);
+                    Pn = dir_of<R>(D, i, R(bd), bd != 0.0);
+                    const R px = Pn.x, py = Pn.y, pz = Pn.z;
+                    a2[0].add(G.x * px + G.y * py + G.z * pz);
+                    R mp = Dg.w * (px * px + py * py + pz * pz);
+                    if (D.has_plane && G.w != R(0)) {
+                        const R np = R(D.pn[0]) * px + R(D.pn[1]) * py + R(D.pn[2]) * pz;
+                        mp += G.w * np * np;
+                    }
+                    a2[1].add(mp);
+                    pmv = D.pnorm == 0 ? sqrt(px * px + py * py + pz * pz) : fmax(fabs(px), fmax(fabs(py), fabs(pz)));
+                }
+                D.pnext[i] = Pn;
+            }
+            seg_warp_sum<R, 2>(a2, key, acc, 0);
+            seg_warp_max<R>(pmv, key, mx);
+        }
+        for (int base = tid - lane; base < D.nt; base += nthr) {
+            const int e = base + lane;
+            Acc<R> a1[1];
+            int key = -1;
+            if (e < D.nt) {
+                const int4 tv = D.tet[e];
+                key = D.vscene[tv.x];
+                const double bd = sbeta[key];
+                const R b = R(bd);
+                const bool nzb = bd != 0.0;
+                a1[0].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
+                                         dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
+            }
+            seg_warp_sum<R, 1>(a1, key, acc, 2);
+        }
+        for (int kk = tid; kk < na; kk += nthr) {   // active pairs come in no order: one atomic each
+            Active<R> ap;
+            load_active<R>(D, kk, ap);
+            const int key = D.vscene[ap.v.x];
+            const double bd = sbeta[key];
+            const R b = R(bd);
+            const bool nzb = bd != 0.0;
+            atomicAdd(acc + (size_t)key * 8 + 2,
+                      pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
+                                      dir_of<R>(D, ap.v.z, b, nzb), dir_of<R>(D, ap.v.w, b, nzb)));
+        }
+        grid_barrier(br, c);
+        if (threadIdx.x == 0) sh.fe = (volatile const uint32_t &)c->err;
+        __syncthreads();
+        const uint32_t err = sh.fe;
+        int ncap = 0;
+        for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+            const double gp = __ldcg(acc + (size_t)s * 8), pMp = __ldcg(acc + (size_t)s * 8 + 1);
+            const double pHp = __ldcg(acc + (size_t)s * 8 + 2) + pMp;
+            const double pmax = max_value<R>(__ldcg(mx + s));
+            const double au = pmax > 0.0 ? D.dhat / (2.0 * pmax) : 0.0;
+            const double ab = -gp / pHp;
+            double a;
+            int capped;
+            if (!(pHp > 0.0) || !isfinite(ab)) { a = au; capped = 1; }
+            else if (ab < au) { a = ab; capped = 0; }
+            else { a = au; capped = 1; }
+            const double dE = -a * gp - 0.5 * a * a * pHp;
+            bool bad = err != 0u;
+            if (!isfinite(a) || !isfinite(gp)) { flag_error(c, ERR_NONFINITE); bad = true; }
+            const int cprev = k > 0 ? __ldcg(&D.seg[s].converged[rp]) : 0;
+            double e0 = k > 0 ? __ldcg(&D.seg[s].dE0[rp]) : 0.0;
+            if (bad || cprev) a = 0.0;
+            int cv = cprev;
+            if (!cprev && !bad) {
+                if (k == 0) e0 = dE;
+                if (D.eps > 0.0 && dE < D.eps * e0) cv = 1;
+            }
+            salpha[s] = a;
+            if (blockIdx.x == 0) {
+                SegCtl &g = D.seg[s];
+                g.gp = gp; g.pHp = pHp; g.pmax = pmax; g.alpha = a; g.dE = dE; g.capped = capped;
+                g.dE0[wp] = e0;
+                g.converged[wp] = cv;
+                if (!cprev && !bad) { g.iters_done = k + 1; ncap += capped; }
+            }
+        }
+        if (blockIdx.x == 0 && ncap) atomicAdd(&c->n_capped, ncap);
+        if (lead) {
+            c->k = k + 1;
+            c->n_active_last = na;
+            if (err == 0u) c->iters_done = k + 1;
+        }
+        __syncthreads();
+        st.mark(10);  // K_PHP (direction included)
+        ++sred;
+    }
+
+    // ------------------------------------------------------------ update (per-scene alpha)
+    br.phase = 11;   // K_UPDATE
+    R md = R(0);
+    for (int i = tid; i < D.nv; i += nthr) {
+        double4_32a X = ldcg4(D.x + i);
+        const R4 P = ldcg4(D.pnext + i);
+        const double a = salpha[D.vscene[i]];
+        X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
+        put_x<R>(D, i, X);
+        D.p[i] = P;
+        init_vertex<R>(D, i, X, ldcg4(D.xtil + i), par ^ 1);
+        md = fmax(md, (R)disp2<R>(D, i, X));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->n_active = 0;
+    const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
+    st.mark(11);  // K_UPDATE
+    return (double)m >= disp_lim * disp_lim ? 1 : 0;
+}
+
+} // namespace pncg

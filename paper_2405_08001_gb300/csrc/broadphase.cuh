@@ -41,6 +41,7 @@ struct BPDev {
     unsigned int *goff;     // [2H] global first entry of each bucket (written with the entries, read by queries)
     unsigned int *ctot;     // persistent form: [2H >> cshift_p] entries per scan chunk
     int cshift_p;           // persistent form: log2 of the buckets per scan chunk
+    const int *vscene;      // batching: scene of each vertex (pairs of two scenes are never candidates); or null
     unsigned long long *ekey;
     int *eprim;             // triangle f or -1 - edge
     float4 *eblo, *ebhi;    // the entry's primitive box (streamed with the key instead of gathered)
@@ -266,6 +267,7 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
             if (qx < lo.x || qx > hi.x || qy < lo.y || qy > hi.y || qz < lo.z || qz > hi.z) continue;
             const int4 t = B.tri[f];
             if (t.x == v || t.y == v || t.z == v) continue;
+            if (B.vscene && B.vscene[t.x] != B.vscene[v]) continue;
             if (B.nexcl && t.w == ov && is_excluded(B, ((unsigned long long)j << 31) | (unsigned long long)f)) continue;
             if (!(pair_dist_build(B, false, v, t.x, t.y, t.z) < B.thr)) continue;
             emit(B, make_int4(v, t.x, t.y, t.z));
@@ -351,6 +353,7 @@ __device__ inline void bp_query_one(const BPDev &B, int j, float s)
                 const int bi = cur.bi;
                 const int4 f = B.edge[bi];
                 if (f.x == e.x || f.x == e.y || f.y == e.x || f.y == e.y) break;
+                if (B.vscene && B.vscene[f.x] != B.vscene[e.x]) break;
                 if (B.nexcl && f.z == e.z &&
                     is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)bi))
                     break;

@@ -28,7 +28,7 @@ const char *const kProfiledNames[N_PROFILED] = {"k_predict", "bp_boxes", "bp_cou
 
 extern "C" {
 
-int32_t sim_abi_version(void) { return 1; }
+int32_t sim_abi_version(void) { return 2; }
 
 const char *sim_status_string(sim_status s)
 {
@@ -212,6 +212,12 @@ int32_t sim_kernel_count(void) { return pncg::N_PROFILED; }
 const char *sim_kernel_name(int32_t i)
 {
     return (i >= 0 && i < pncg::N_PROFILED) ? pncg::kProfiledNames[i] : "";
+}
+
+sim_status sim_get_scene_scalars(sim_handle h, double *out, int32_t max_scenes, int32_t *n_scenes)
+{
+    if (guard(h) || !out || !n_scenes || max_scenes <= 0) return SIM_ERR_INVALID_ARG;
+    return h->impl->get_scene_scalars(out, max_scenes, n_scenes);
 }
 
 sim_status sim_get_sizes(sim_handle h, int32_t *out)

@@ -26,6 +26,9 @@ constexpr int TRACE_COLS = 8;   // beta, gp, pHp, pmax, alpha, dE, n_active, cap
 constexpr int SCATTER_CHUNK = 256;
 constexpr int SCATTER_MAXU = 512;
 
+// batching: most independent scenes one handle takes (their beta and alpha live in shared memory)
+constexpr int MAX_SCENES = 1024;
+
 // Device-resident control block: every scalar of the iteration lives here, so no host round trip is needed
 // inside a time step.
 struct Ctrl {
@@ -73,6 +76,17 @@ template <> struct V4<double> { typedef double4_32a T; };
 template <typename R> __host__ __device__ inline typename V4<R>::T mk4(R a, R b, R c, R d);
 template <> __host__ __device__ inline float4 mk4<float>(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 template <> __host__ __device__ inline double4_32a mk4<double>(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
+
+// Per-scene state of the batched form (independent scenes in one launch).  The state carried between
+// iterations is double-buffered by iteration parity: iteration k reads entry (k - 1) & 1 and writes k & 1, so the
+// block that writes never races the blocks still reading the previous value.
+struct SegCtl {
+    double gPg[2];         // g^T P g (PR+ denominator of the next iteration)
+    double dE0[2];         // Delta E of iteration 0 (eps rule)
+    int32_t converged[2];
+    int32_t restarted, capped, iters_done, pad;
+    double beta, gp, pHp, pmax, alpha, dE;   // the most recent iteration, for reporting
+};
 
 // active contact pair recorded by the gradient pass for the p^T H p pass of the same iteration
 template <typename R> struct alignas(16) Active {

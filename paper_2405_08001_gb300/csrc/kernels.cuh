@@ -55,6 +55,13 @@ template <typename R> struct Dev {
     const int *cv_off, *cv;
     const ushort4 *tloc;
     int scatter_block;
+    // batching: nseg independent scenes (1 = none), the scene of each vertex, per-scene state and the per-scene
+    // reduction accumulators ([3][nseg][8] sums, [3][nseg] maxima as bits; used round robin)
+    int nseg;
+    const int *vscene;
+    SegCtl *seg;
+    double *sacc;
+    unsigned long long *smax;
     Ctrl *ctrl;
     double *part;                      // reduction partials
     double *trace;                     // [iters][TRACE_COLS]

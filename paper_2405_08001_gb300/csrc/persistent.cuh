@@ -94,6 +94,7 @@ template <> struct Acc<double> {
     __device__ inline void add_d(double x) { v += x; }
     __device__ inline void add(const Acc &o) { v += o.v; }
     __device__ inline Acc shfl_down(int o) const { Acc r; r.v = __shfl_down_sync(0xffffffffu, v, o); return r; }
+    __device__ inline Acc shfl_up(int o) const { Acc r; r.v = __shfl_up_sync(0xffffffffu, v, o); return r; }
     __device__ inline double value() const { return v; }
     __device__ inline double head() const { return v; }
 };
@@ -124,6 +125,13 @@ template <> struct Acc<float> {
         Acc r;
         r.h = __shfl_down_sync(0xffffffffu, h, o);
         r.l = __shfl_down_sync(0xffffffffu, l, o);
+        return r;
+    }
+    __device__ inline Acc shfl_up(int o) const
+    {
+        Acc r;
+        r.h = __shfl_up_sync(0xffffffffu, h, o);
+        r.l = __shfl_up_sync(0xffffffffu, l, o);
         return r;
     }
     __device__ inline double value() const { return (double)h + (double)l; }
@@ -346,6 +354,12 @@ template <typename R> __device__ inline R disp2_from(const double4_32a &X, const
     }
 }
 
+} // namespace pncg
+
+#include "batched.cuh"
+
+namespace pncg {
+
 // ------------------------------------------------------------------------------------------------ the kernel
 
 template <typename R>
@@ -360,12 +374,14 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
     constexpr size_t SBUF = sizeof(R) * 6 * SCATTER_MAXU > sizeof(unsigned int) * BP_MAX_CHUNKS
                                 ? sizeof(R) * 6 * SCATTER_MAXU : sizeof(unsigned int) * BP_MAX_CHUNKS;
     __shared__ __align__(16) unsigned char sbuf[SBUF];
+    static_assert(SBUF >= 2 * MAX_SCENES * sizeof(double), "the batched form keeps per-scene beta and alpha here");
     static_assert(PB == SCATTER_CHUNK, "a block's tet loop covers one scatter chunk");
     Ctrl *c = D.ctrl;
     RedBufs rb;
     rb.base = A.part;
     rb.n = gridDim.x;
     Bar br{A.count, 0u, A.arrive, A.depart, A.bar_kind, A.max_bar, 0};
+    int sred = 0;   // batched form: per-scene reductions done in this launch (round robin accumulators)
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -415,6 +431,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->iters_done = 0; c->converged = 0;
             c->n_active = 0; c->dE0 = 0.0; c->gPg_prev = 0.0;
         }
+        if (D.nseg > 1) seg_reset<R>(D);
         grid_barrier(br, c);
         st.mark(0);   // K_PREDICT
     }
@@ -576,6 +593,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             }
             grid_barrier(br, c);
             st.mark(7);   // K_GATHER
+        }
+        if (D.nseg > 1) {   // batched scenes: per-scene beta, alpha (batched.cuh)
+            if (batched_tail<R>(D, c, sh, sbuf, br, st, rb, k, par, sred, disp_lim)) rebuild = 1;
+            continue;
         }
         // ------------------------------------------------------------ a4: beta (and P g for the direction)
         double beta = 0.0;

@@ -229,6 +229,33 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
     m.v2c.assign(4 * (size_t)nt, 0);
     std::vector<int> cur(m.v2c_off.begin(), m.v2c_off.end() - 1);
     for (int q = 0; q < 4 * nt; ++q) m.v2c[cur[m.tet[q]]++] = q;
+    // batching: scenes (validated: ids 0 .. S-1, non-decreasing over the vertices, every id present, each tet
+    // inside one scene, tets ordered by scene)
+    m.nseg = 1;
+    m.vscene.clear();
+    if (mesh->scene_of_vert) {
+        const int32_t *sc = mesh->scene_of_vert;
+        if (sc[0] != 0) { err = "scene_of_vert must start at 0"; return SIM_ERR_INVALID_ARG; }
+        for (int i = 1; i < nv; ++i)
+            if (sc[i] != sc[i - 1] && sc[i] != sc[i - 1] + 1) {
+                err = "scene_of_vert must be non-decreasing in steps of 1 (vertex " + std::to_string(i) + ")";
+                return SIM_ERR_INVALID_ARG;
+            }
+        m.nseg = sc[nv - 1] + 1;
+        if (m.nseg > MAX_SCENES) { err = "at most " + std::to_string(MAX_SCENES) + " scenes"; return SIM_ERR_INVALID_ARG; }
+        int prev = 0;
+        for (int e = 0; e < nt; ++e) {
+            const int *v = &m.tet[4 * (size_t)e];
+            const int s0 = sc[v[0]];
+            if (sc[v[1]] != s0 || sc[v[2]] != s0 || sc[v[3]] != s0) {
+                err = "tet " + std::to_string(e) + " spans two scenes";
+                return SIM_ERR_INVALID_ARG;
+            }
+            if (s0 < prev) { err = "tets must be ordered by scene (tet " + std::to_string(e) + ")"; return SIM_ERR_INVALID_ARG; }
+            prev = s0;
+        }
+        if (m.nseg > 1) m.vscene.assign(sc, sc + nv);
+    }
     // block-scatter tables
     const int nchunk = (nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
     m.cv_off.assign(nchunk + 1, 0);

@@ -34,7 +34,11 @@ struct HostMesh {
     // the chunk-local index of each corner
     std::vector<int> cv_off, cv;           // [nchunk + 1], [sum of distinct counts]
     std::vector<unsigned short> tloc;      // [nt][4]
+    // batching: independent scenes (nseg == 1 without scene_of_vert)
+    int nseg = 1;
+    std::vector<int> vscene;               // [nv] scene of each vertex (empty when nseg == 1)
 };
+
 
 
 // Builds the HostMesh; returns SIM_OK or an error with a message.
@@ -62,6 +66,7 @@ public:
     virtual sim_status get_candidates(int32_t *idx, int32_t max, int32_t *count) = 0;
     virtual sim_status get_trace(double *buf, int32_t max_iters, int32_t *n) = 0;
     virtual sim_status profile_step(const double *targets, float *ms, int32_t *launches, int n_kernels) = 0;
+    virtual sim_status get_scene_scalars(double *out, int32_t max_scenes, int32_t *n_scenes) = 0;
     virtual sim_status profile_barriers(const double *targets, uint64_t *arrive, uint64_t *depart, int32_t *kind,
                                         int32_t max_bar, int32_t *n_bar, int32_t *n_blocks) = 0;
     virtual void sizes(int32_t *out) = 0;

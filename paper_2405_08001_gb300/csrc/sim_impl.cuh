@@ -143,6 +143,9 @@ public:
         cap = M.opt.candidate_capacity > 0 ? M.opt.candidate_capacity : std::max(1 << 14, 16 * (M.ns + M.ne));
         sim_status st = alloc_all();
         if (st != SIM_OK) return st;
+        if (M.nseg > 1 && !persist)
+            return fail(SIM_ERR_INVALID_ARG, "batched scenes need the persistent form (options.persistent = 1 on a "
+                                             "device with cooperative launch)");
         return upload_initial();
     }
 
@@ -534,6 +537,31 @@ public:
         return sync_and_check();
     }
 
+    sim_status get_scene_scalars(double *out, int32_t max_scenes, int32_t *n_scenes) override
+    {
+        CK(cudaSetDevice(dev));
+        sim_status r = sync_and_check();
+        const int n = std::min(max_scenes, M.nseg);
+        *n_scenes = M.nseg;
+        if (M.nseg == 1) {
+            double row[11] = {hctrl->beta, hctrl->gp, hctrl->pHp, hctrl->pmax, hctrl->alpha, hctrl->dE, hctrl->dE0,
+                              (double)hctrl->converged, (double)hctrl->iters_done, (double)hctrl->restarted,
+                              (double)hctrl->capped};
+            std::memcpy(out, row, sizeof row);
+            return r;
+        }
+        std::vector<SegCtl> h(M.nseg);
+        CK(cudaMemcpy(h.data(), D.seg, sizeof(SegCtl) * M.nseg, cudaMemcpyDeviceToHost));
+        const int lp = (hctrl->k - 1) & 1;   // parity of the last completed iteration
+        for (int i = 0; i < n; ++i) {
+            const SegCtl &g = h[i];
+            double row[11] = {g.beta, g.gp, g.pHp, g.pmax, g.alpha, g.dE, g.dE0[lp], (double)g.converged[lp],
+                              (double)g.iters_done, (double)g.restarted, (double)g.capped};
+            std::memcpy(out + 11 * (size_t)i, row, sizeof row);
+        }
+        return r;
+    }
+
     void sizes(int32_t *out) override
     {
         out[0] = M.nv; out[1] = M.nt; out[2] = M.nf; out[3] = M.ne; out[4] = M.ns; out[5] = (int32_t)M.excl.size();
@@ -687,6 +715,14 @@ private:
         D.beta_rule = M.opt.beta; D.pnorm = M.opt.pnorm; D.iters = M.opt.iters;
         D.segmented = M.opt.scatter == SIM_SCATTER_SEGMENTED;
         D.scatter_block = M.opt.scatter == SIM_SCATTER_BLOCK;
+        D.nseg = M.nseg;
+        D.vscene = nullptr; D.seg = nullptr; D.sacc = nullptr; D.smax = nullptr;
+        if (M.nseg > 1) {
+            int *vs; AL(vs, (size_t)nv); D.vscene = vs;
+            AL(D.seg, (size_t)M.nseg);
+            AL(D.sacc, 3 * 8 * (size_t)M.nseg);
+            AL(D.smax, 3 * (size_t)M.nseg);
+        }
         D.cv_off = nullptr; D.cv = nullptr; D.tloc = nullptr;
         if (D.scatter_block) {
             int *co; AL(co, M.cv_off.size()); D.cv_off = co;
@@ -739,6 +775,7 @@ private:
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
         B.excl = ex; B.nexcl = (int)M.excl.size();
+        B.vscene = D.vscene;
         B.infl = M.dhat + D.pad_r;
         B.thr = (float)(B.infl * 1.001);
         B.ctrl = c;
@@ -785,6 +822,7 @@ private:
         if ((st = up(D.Dm, Dm.data(), sizeof(R) * 9 * nt))) return st;
         if ((st = up(D.hv, hv.data(), sizeof(R) * nt))) return st;
         if (D.escale && (st = up(D.escale, es.data(), sizeof(R) * nt))) return st;
+        if (D.vscene && (st = up(D.vscene, M.vscene.data(), sizeof(int) * nv))) return st;
         if (D.scatter_block) {
             if ((st = up(D.cv_off, M.cv_off.data(), sizeof(int) * M.cv_off.size()))) return st;
             if (!M.cv.empty() && (st = up(D.cv, M.cv.data(), sizeof(int) * M.cv.size()))) return st;
@@ -940,6 +978,11 @@ private:
     {
         cudaError_t e = cudaMemsetAsync(bar_count, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return e;
+        if (D.nseg > 1) {   // the batched form's round-robin accumulators start at zero
+            e = cudaMemsetAsync(D.sacc, 0, sizeof(double) * 3 * 8 * (size_t)D.nseg, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(D.smax, 0, sizeof(unsigned long long) * 3 * (size_t)D.nseg, s);
+            if (e != cudaSuccess) return e;
+        }
         PersistArgs A;
         A.do_predict = do_predict; A.k0 = k0; A.n_iters = n_iters; A.do_finish = do_finish;
         A.count = bar_count;

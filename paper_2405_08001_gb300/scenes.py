@@ -122,6 +122,33 @@ class Scene:
             return None
         return np.ascontiguousarray(np.stack([self.targets(first_step + s) for s in range(n_steps)]))
 
+    @property
+    def n_scenes(self) -> int:
+        return 1 if self.scene_of_vert is None else int(self.scene_of_vert[-1]) + 1
+
+    def scene_ranges(self):
+        """Per scene: (first vertex, end vertex, first tet, end tet) of a batch (scenes are contiguous)."""
+        if self.scene_of_vert is None:
+            return [(0, self.n_verts, 0, self.n_tets)]
+        sv = self.scene_of_vert
+        st = sv[self.tets[:, 0]]
+        out = []
+        for s in range(self.n_scenes):
+            v = np.nonzero(sv == s)[0]
+            t = np.nonzero(st == s)[0]
+            out.append((int(v[0]), int(v[-1]) + 1, int(t[0]), int(t[-1]) + 1))
+        return out
+
+    def subscene(self, s: int) -> "Scene":
+        """Scene s of a batch as a problem of its own (vertex indices rebased)."""
+        v0, v1, t0, t1 = self.scene_ranges()[s]
+        return Scene(name=f"{self.name}[{s}]", rest_x=self.rest_x[v0:v1].copy(), tets=(self.tets[t0:t1] - v0).astype(np.int32),
+                     x0=self.x0[v0:v1].copy(), v0=self.v0[v0:v1].copy(), youngs=self.youngs, poisson=self.poisson,
+                     density=self.density, dt=self.dt, dhat=self.dhat, kappa=self.kappa, gravity=self.gravity,
+                     plane=self.plane, fixed=None if self.fixed is None else self.fixed[v0:v1].copy(),
+                     youngs_per_tet=None if self.youngs_per_tet is None else self.youngs_per_tet[t0:t1].copy(),
+                     iters=self.iters, steps=self.steps)
+
 
 def cube_drop(n: int = 8, side: float = 0.1, drop: float = 0.02, youngs: float = 1e5, poisson: float = 0.4,
               density: float = 1000.0, dt: float = 1.0 / 60.0, dhat: float = 1e-3, kappa: float = 1e4,
@@ -247,6 +274,38 @@ def pile(n_bars: int = 10, cells=(16, 16, 64), size=(0.1, 0.1, 0.4), seed: int =
     return Scene(name=f"pile{n_bars}", rest_x=X, tets=T, x0=X.copy(), v0=np.zeros_like(X), youngs=youngs,
                  poisson=poisson, density=1000.0, dt=dt, dhat=dhat, kappa=kappa, gravity=(0.0, 0.0, -9.8),
                  plane=((0.0, 0.0, 1.0), 0.0), iters=iters, steps=steps)
+
+
+def batched(n_scenes: int = 256, seed: int = 2, n_min: int = 4, n_max: int = 16, cell: float = 0.0125,
+            e_min: float = 5e4, e_max: float = 5e5, poisson: float = 0.4, dt: float = 1.0 / 60.0, dhat: float = 1e-3,
+            kappa: float = 1e4, iters: int = 50, steps: int = 60, spacing: float = 0.5) -> Scene:
+    """Independent cubes of n^3 Kuhn cells, n ~ U{n_min..n_max}, each with a uniform-random rotation (normalised
+    Gaussian quaternion), its lowest vertex U[0.01, 0.05] m above the plane z = 0 and its own Young's modulus
+    E ~ U[e_min, e_max]; laid out on a square grid `spacing` apart so that no two scenes overlap.  Vertices and
+    tets are ordered scene by scene (scene_of_vert)."""
+    rng = np.random.default_rng(seed)
+    cols = int(math.ceil(math.sqrt(n_scenes)))
+    Xs, Ts, Es, Ss = [], [], [], []
+    off = 0
+    for s in range(n_scenes):
+        n = int(rng.integers(n_min, n_max + 1))
+        side = n * cell
+        X, T = kuhn_grid(n, n, n, size=(side, side, side))
+        R = random_rotation(rng)
+        X = (X - 0.5 * side) @ R.T
+        h = rng.uniform(0.01, 0.05)
+        r, q = divmod(s, cols)
+        X = X - np.array([0.0, 0.0, X[:, 2].min()]) + np.array([q * spacing, r * spacing, h])
+        Xs.append(X)
+        Ts.append(T + off)
+        Es.append(np.full(T.shape[0], rng.uniform(e_min, e_max)))
+        Ss.append(np.full(X.shape[0], s, dtype=np.int32))
+        off += X.shape[0]
+    X = np.concatenate(Xs)
+    return Scene(name=f"batched{n_scenes}", rest_x=X, tets=np.concatenate(Ts).astype(np.int32), x0=X.copy(),
+                 v0=np.zeros_like(X), youngs=1.0, poisson=poisson, density=1000.0, dt=dt, dhat=dhat, kappa=kappa,
+                 gravity=(0.0, 0.0, -9.8), plane=((0.0, 0.0, 1.0), 0.0), youngs_per_tet=np.concatenate(Es),
+                 scene_of_vert=np.concatenate(Ss), iters=iters, steps=steps)
 
 
 def perturbed(scene: Scene, seed: int, scale: float) -> np.ndarray:
