@@ -100,8 +100,11 @@ typedef struct {
     int32_t candidate_capacity; /* initial candidate-buffer capacity in pairs; <= 0 = automatic */
     int32_t persistent;   /* 1 (default) = each time step (and each sim_iterate call) is one cooperative launch
                              whose blocks stay resident and meet at grid barriers between the phases of
-                             Algorithm 1; 0 = one kernel per phase.  Falls back to 0 when the device cannot
-                             launch cooperative kernels. */
+                             Algorithm 1; 0 = one kernel per phase; 2 = autotuned: the second time step runs
+                             persistent and the third per phase, each timed on the GPU (those two steps
+                             synchronise), and the faster form runs from then on (sim_stats.launch_form).  Falls
+                             back to 0 when the device cannot launch cooperative kernels; batched scenes always run
+                             persistent. */
 } sim_options;
 
 /* Statistics of the last completed time step. */
@@ -114,6 +117,8 @@ typedef struct {
     int32_t n_capped;      /* iterations of the last step that took alpha = alpha_upper */
     int32_t n_surface_tris, n_surface_edges, n_surface_verts;
     double dE0, dE_last;   /* Delta E of the first and the last iteration */
+    int32_t launch_form;   /* the form time steps run in now: 1 = persistent, 0 = one kernel per phase */
+    int32_t n_scenes;      /* independent scenes (1 without scene_of_vert) */
 } sim_stats;
 
 /* Scalars of the most recent iteration (Algorithm 1). */

@@ -161,14 +161,59 @@ public:
         for (int k = 0; k < n; ++k) {
             sim_status st = stage_targets(targets ? targets + (size_t)k * 3 * M.nfix : nullptr);
             if (st != SIM_OK) return st;
+            if (tune_phase > 0 && tune_phase < 3 && steps_run >= 1) {
+                st = tuned_step();
+                if (st != SIM_OK) return st;
+                ++steps_run;
+                continue;
+            }
             if (gexec) { CK(cudaGraphLaunch(gexec, s)); k_host = M.opt.iters; }
             else {
                 st = launch_step();
                 if (st != SIM_OK) return st;
             }
+            ++steps_run;
         }
         if (!sync) return SIM_OK;
         return sync_and_check();
+    }
+
+    // Launch-form autotuning (options.persistent = 2): one time step in each form, timed on the GPU with events on
+    // the solver's stream; the faster form is kept.  Both steps are ordinary time steps of the simulation.
+    void drop_graph()
+    {
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+    }
+    sim_status tuned_step()
+    {
+        const bool want_persist = tune_phase == 1;
+        if (persist != want_persist) { persist = want_persist; drop_graph(); }
+        if (M.opt.use_graph && !gexec) {
+            sim_status st = capture();
+            if (st != SIM_OK) return st;
+        }
+        if (!tune_ev[0]) {
+            CK(cudaEventCreate(&tune_ev[0]));
+            CK(cudaEventCreate(&tune_ev[1]));
+        }
+        CK(cudaEventRecord(tune_ev[0], s));
+        if (gexec) { CK(cudaGraphLaunch(gexec, s)); k_host = M.opt.iters; }
+        else {
+            sim_status st = launch_step();
+            if (st != SIM_OK) return st;
+        }
+        CK(cudaEventRecord(tune_ev[1], s));
+        CK(cudaEventSynchronize(tune_ev[1]));
+        CK(cudaEventElapsedTime(&tune_ms[tune_phase - 1], tune_ev[0], tune_ev[1]));
+        if (tune_phase == 1) {
+            tune_phase = 2;
+        } else {
+            tune_phase = 3;
+            const bool best = tune_ms[0] <= tune_ms[1];
+            if (persist != best) { persist = best; drop_graph(); }
+        }
+        return SIM_OK;
     }
 
     sim_status begin_step(const double *targets) override
@@ -222,6 +267,8 @@ public:
             st->n_surface_tris = M.nf; st->n_surface_edges = M.ne; st->n_surface_verts = M.ns;
             st->dE0 = hctrl->dE0;
             st->dE_last = hctrl->dE;
+            st->launch_form = persist ? 1 : 0;
+            st->n_scenes = M.nseg;
         }
         return r;
     }
@@ -586,6 +633,10 @@ private:
     std::vector<cudaEvent_t> prof_ev;
     // persistent form
     bool persist = false;
+    int tune_phase = 0;          // autotuning: 1 = next tuned step runs persistent, 2 = per phase, 3 = done
+    float tune_ms[2] = {0.0f, 0.0f};
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    long long steps_run = 0;
     int pgrid = 0;
     unsigned int *bar_count = nullptr;
     void *ppart = nullptr;
@@ -618,6 +669,7 @@ private:
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         for (auto e : prof_ev) cudaEventDestroy(e);
+        for (auto &e : tune_ev) if (e) { cudaEventDestroy(e); e = nullptr; }
         prof_ev.clear();
         gexec = nullptr; graph = nullptr;
         for (void *p : allocs) cudaFree(p);
@@ -657,6 +709,7 @@ private:
         AL2(pp, bytes);
         ppart = pp;
         persist = true;
+        tune_phase = (M.opt.persistent == 2 && M.nseg == 1) ? 1 : 0;
         return SIM_OK;
     }
 

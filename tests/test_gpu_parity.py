@@ -338,3 +338,21 @@ def test_persistent_launch_equals_per_phase_kernels(B, prec):
         assert st["step"] == 3 and st["iters_done"] == sc.iters
         sim.close()
     assert rel(out[0] - sc.x0, out[1] - sc.x0) < (1e-9 if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_launch_form(B, prec):
+    """options.persistent = 2: the second and third steps run in the two launch forms, timed; the faster one is
+    kept.  In free fall the autotuned run ends where a fixed-form run ends (to rounding)."""
+    sc = S.cube_drop()
+    auto = B.Sim(sc, precision=prec, persistent=2)
+    auto.step(4)
+    xa, _, sa = auto.state()
+    assert sa["launch_form"] in (0, 1)
+    auto.close()
+    fixed = B.Sim(sc, precision=prec, persistent=1)
+    fixed.step(4)
+    xf, _, sf = fixed.state()
+    assert sf["launch_form"] == 1
+    fixed.close()
+    assert rel(xa - sc.x0, xf - sc.x0) < (1e-9 if prec == 0 else 1e-3)
