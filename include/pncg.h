@@ -295,6 +295,30 @@ const char *sim_status_string(sim_status s);
 int32_t sim_abi_version(void);
 
 /*
+ * Differentiation (the adjoint of a time step, read as the exact minimiser of Algorithm 1's incremental potential
+ * E(x; x~, theta); the paper has no adjoint).
+ *
+ * sim_eval_hvp: out = H(x) v, H the Hessian of E at x as the p^T H p pass sees it (Sec. 3.1 Neo-Hookean terms,
+ * the barrier with the closest points frozen, Eqs. 12-13, the half-space barrier and the lumped mass), candidates
+ * and active pairs taken at x.  Rows and columns of kinematic vertices are dropped (their out entries are 0).
+ * x, v, out: [n_verts][3], host or device.  The handle's state is kept.  Synchronises.
+ */
+sim_status sim_eval_hvp(sim_handle h, const double *x, const double *v, double *out);
+
+/*
+ * sim_adjoint_step: the reverse of one time step x_t -> x_{t+1} (v_{t+1} = (x_{t+1} - x_t)/h).  Given the loss's
+ * adjoints ax1 = dL/dx_{t+1} and av1 = dL/dv_{t+1}, solves H(x_{t+1}) lambda = ax1 + av1/h by Jacobi-preconditioned
+ * linear CG (the preconditioner of Sec. 4.2) to a relative residual tol or max_iters iterations, and writes
+ *   ax0 = dL/dx_t = M lambda - av1/h,   av0 = dL/dv_t = h M lambda
+ * (kinematic vertices: ax0 = -av1/h, av0 = 0) and, when dE is not NULL, adds dL/dE_e = -lambda_e . dg_e/dE_e to
+ * dE[e] for every tet (the per-tet Young's modulus; g_e the tet's elastic gradient).
+ * x1, ax1, av1, ax0, av0: [n_verts][3]; dE: [n_tets]; host or device.  *iters and *residual (nullable) receive the
+ * CG iterations and the final relative residual.  The handle's state is kept.  Synchronises.
+ */
+sim_status sim_adjoint_step(sim_handle h, const double *x1, const double *ax1, const double *av1, double *ax0,
+                            double *av0, double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual);
+
+/*
  * Batching: the scalars of the most recent iteration per scene, rows {beta, g^T p, p^T H p (with p^T M p),
  * max_v |p_v|, alpha, Delta E, Delta E of iteration 0, converged, iterations done, restarted, capped}.
  * out: host [max_scenes][11]; *n_scenes receives the number of scenes (1 without scene_of_vert, whose row repeats

@@ -103,6 +103,8 @@ def load():
         "sim_profile_step": (C.c_int, [P, P, P, P, I32]),
         "sim_profile_barriers": (C.c_int, [P, P, P, P, P, I32, P, P]),
         "sim_get_scene_scalars": (C.c_int, [P, P, I32, P]),
+        "sim_eval_hvp": (C.c_int, [P, P, P, P]),
+        "sim_adjoint_step": (C.c_int, [P, P, P, P, P, P, P, D, I32, P, P]),
         "sim_kernel_count": (I32, []),
         "sim_kernel_name": (C.c_char_p, [I32]),
         "sim_get_sizes": (C.c_int, [P, P]),
@@ -341,6 +343,34 @@ def sim_profile_barriers(h, targets=None, max_barriers=4096, max_blocks=4096):
     flat_a = arrive.reshape(-1)[: n * g].reshape(n, g).copy()
     flat_d = depart.reshape(-1)[: n * g].reshape(n, g).copy()
     return flat_a, flat_d, [names[k] for k in kind[:n]]
+
+
+def sim_eval_hvp(h, x, v, out=None):
+    """H(x) v (the incremental potential's Hessian with frozen contact closest points) -> [n_verts, 3]."""
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x, n=3 * nv)
+    pv, kv = _ptr(v, n=3 * nv)
+    po, o = _out(out, nv)
+    _check(load().sim_eval_hvp(h, px, pv, po), h)
+    return o
+
+
+def sim_adjoint_step(h, x1, ax1, av1, dE=None, tol=1e-10, max_iters=2000, ax0=None, av0=None):
+    """Reverse of one time step ending at x1: returns (dL/dx_t, dL/dv_t, CG iterations, relative residual) and adds
+    dL/dE_e to dE (a float64 [n_tets] array or tensor, updated in place) when given."""
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x1, n=3 * nv)
+    pa, ka = _ptr(ax1, n=3 * nv)
+    pb, kb = _ptr(av1, n=3 * nv)
+    p0, a0 = _out(ax0, nv)
+    p1, a1 = _out(av0, nv)
+    pe, ke = (None, None) if dE is None else _ptr(dE)
+    if dE is not None and not hasattr(dE, "data_ptr") and ke is not dE:
+        raise TypeError("dE must be a C-contiguous float64 array (it is updated in place)")
+    it = C.c_int32(0)
+    res = C.c_double(0.0)
+    _check(load().sim_adjoint_step(h, px, pa, pb, p0, p1, pe, float(tol), int(max_iters), C.byref(it), C.byref(res)), h)
+    return a0, a1, it.value, res.value
 
 
 SCENE_SCALAR_COLS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "dE0", "converged", "iters_done", "restarted",

@@ -214,6 +214,19 @@ const char *sim_kernel_name(int32_t i)
     return (i >= 0 && i < pncg::N_PROFILED) ? pncg::kProfiledNames[i] : "";
 }
 
+sim_status sim_eval_hvp(sim_handle h, const double *x, const double *v, double *out)
+{
+    if (guard(h)) return SIM_ERR_INVALID_ARG;
+    return h->impl->eval_hvp(x, v, out);
+}
+
+sim_status sim_adjoint_step(sim_handle h, const double *x1, const double *ax1, const double *av1, double *ax0,
+                            double *av0, double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual)
+{
+    if (guard(h)) return SIM_ERR_INVALID_ARG;
+    return h->impl->adjoint_step(x1, ax1, av1, ax0, av0, dE, tol, max_iters, iters, residual);
+}
+
 sim_status sim_get_scene_scalars(sim_handle h, double *out, int32_t max_scenes, int32_t *n_scenes)
 {
     if (guard(h) || !out || !n_scenes || max_scenes <= 0) return SIM_ERR_INVALID_ARG;

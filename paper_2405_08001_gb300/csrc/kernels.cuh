@@ -394,7 +394,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
 // per-(tet, corner) buffer (segmented scatter), to the block's shared accumulators sacc ([6][SCATTER_MAXU],
 // indexed by the chunk-local vertex; block scatter) or straight to the global accumulators.
 template <typename R>
-__device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> &in, R *sacc = nullptr)
+__device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4][3], R dv[4][3])
 {
     const int4 tv = in.tv;
     TetF<R> T;
@@ -402,7 +402,7 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
     const R sc = in.hv;
     const R mu = D.mu * in.es, lam = D.lam * in.es;
     if constexpr (sizeof(R) == 4) {
-        if (!tet_stress_metric(D, in, T, P, Psi33)) return;
+        if (!tet_stress_metric(D, in, T, P, Psi33)) return false;
     } else {
         R ds[3][3];
         tet_ds<R>(D, tv, ds);
@@ -411,7 +411,7 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
 #pragma unroll
             for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
         tet_F_from<R>(ds, T);
-        if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return; }
+        if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return false; }
         const R L = log(T.J);
         const R Psi3 = (lam * L - mu) / T.J;
         Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
@@ -420,7 +420,6 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
 #pragma unroll
             for (int b = 0; b < 3; ++b) P[a][b] = sc * (mu * T.F[a][b] + Psi3 * T.cf[a][b]);
     }
-    R gv[4][3], dv[4][3];
 #pragma unroll
     for (int i = 1; i < 4; ++i) {
         const R *w = T.w[i - 1];
@@ -444,6 +443,15 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
             dv[0][a] = sc * (mu * ww + Psi33 * cw * cw);
         }
     }
+    return true;
+}
+
+template <typename R>
+__device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> &in, R *sacc = nullptr)
+{
+    const int4 tv = in.tv;
+    R gv[4][3], dv[4][3];
+    if (!tet_grad_eval<R>(D, in, gv, dv)) return;
     if (D.segmented) {
         const int q0 = 4 * e;
         const int n4 = 4 * D.nt;

@@ -123,6 +123,7 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
     m.nv = nv; m.nt = nt; m.h = dt; m.dhat = dhat; m.kappa = kappa; m.opt = opt;
     const double nu = mat->poisson;
     const double Eb = mat->youngs_per_tet ? 1.0 : mat->youngs;
+    m.nu = nu;
     m.mu = Eb / (2.0 * (1.0 + nu));
     m.lam = Eb * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     const double *X = mesh->rest_x;

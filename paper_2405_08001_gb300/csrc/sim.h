@@ -16,6 +16,7 @@ namespace pncg {
 struct HostMesh {
     int nv = 0, nt = 0, nf = 0, ne = 0, ns = 0, nfix = 0;
     double h = 0, dhat = 0, kappa = 0, mu = 0, lam = 0;
+    double nu = 0;                         // Poisson ratio
     sim_options opt;
     std::vector<double> X, x0, v0;         // [nv][3] rest, initial positions and velocities
     std::vector<double> mass;              // [nv]
@@ -67,6 +68,9 @@ public:
     virtual sim_status get_trace(double *buf, int32_t max_iters, int32_t *n) = 0;
     virtual sim_status profile_step(const double *targets, float *ms, int32_t *launches, int n_kernels) = 0;
     virtual sim_status get_scene_scalars(double *out, int32_t max_scenes, int32_t *n_scenes) = 0;
+    virtual sim_status eval_hvp(const double *x, const double *v, double *out) = 0;
+    virtual sim_status adjoint_step(const double *x1, const double *ax1, const double *av1, double *ax0, double *av0,
+                                    double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual) = 0;
     virtual sim_status profile_barriers(const double *targets, uint64_t *arrive, uint64_t *depart, int32_t *kind,
                                         int32_t max_bar, int32_t *n_bar, int32_t *n_blocks) = 0;
     virtual void sizes(int32_t *out) = 0;

@@ -9,6 +9,7 @@
 #include "broadphase.cuh"
 #include "kernels.cuh"
 #include "persistent.cuh"
+#include "adjoint.cuh"
 #include "sim.h"
 
 namespace pncg {
@@ -609,6 +610,96 @@ public:
         return r;
     }
 
+    // ------------------------------------------------------------------------------------------ differentiation
+    sim_status adj_alloc()
+    {
+        if (adj_b) return SIM_OK;
+        const size_t n3 = 3 * (size_t)M.nv;
+        AL3(adj_b, n3); AL3(adj_x, n3); AL3(adj_r, n3); AL3(adj_z, n3); AL3(adj_p, n3); AL3(adj_q, n3);
+        AL3(adj_av, n3); AL3(adj_ax, n3); AL3(adj_cg, (size_t)CG_N);
+        AL3(adj_dE, (size_t)M.nt);
+        return SIM_OK;
+    }
+    // q = H p at the positions of the last eval_setup
+    void launch_hvp(const double *v, double *out)
+    {
+        const int nb = (M.nv + 127) / 128;
+        k_hvp_vert<R><<<nb, 128, 0, s>>>(D, 0, v, out);
+        k_hvp_tet<R><<<(M.nt + EB - 1) / EB, EB, 0, s>>>(D, v, out);
+        k_hvp_pair<R><<<ncb, EB, 0, s>>>(D, v, out);
+    }
+    sim_status eval_hvp(const double *x, const double *v, double *out) override
+    {
+        CK(cudaSetDevice(dev));
+        if (!x || !v || !out) return fail(SIM_ERR_INVALID_ARG, "x, v and out are required");
+        sim_status r = adj_alloc();
+        if (r) return r;
+        r = eval_setup(x, nullptr);
+        if (r) return r;
+        const size_t bytes = sizeof(double) * 3 * (size_t)M.nv;
+        CK(cudaMemcpyAsync(adj_p, v, bytes, cudaMemcpyDefault, s));
+        launch_hvp(adj_p, adj_q);
+        CK(cudaMemcpyAsync(out, adj_q, bytes, cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        eval_restore();
+        return sync_and_check();
+    }
+    sim_status adjoint_step(const double *x1, const double *ax1, const double *av1, double *ax0, double *av0,
+                            double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual) override
+    {
+        CK(cudaSetDevice(dev));
+        if (!x1 || !ax1 || !av1 || !ax0 || !av0 || max_iters <= 0 || !(tol > 0))
+            return fail(SIM_ERR_INVALID_ARG, "x1, the adjoints and a positive tolerance and iteration cap are required");
+        sim_status r = adj_alloc();
+        if (r) return r;
+        r = eval_setup(x1, nullptr);   // H at x_{t+1}: candidates, active pairs and the gradient pass there
+        if (r) return r;
+        const size_t n3 = 3 * (size_t)M.nv, bytes = sizeof(double) * n3;
+        const int nb = (M.nv + VB - 1) / VB;
+        CK(cudaMemcpyAsync(adj_ax, ax1, bytes, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(adj_av, av1, bytes, cudaMemcpyDefault, s));
+        k_adj_rhs<R><<<nb, VB, 0, s>>>(D, adj_ax, adj_av, adj_b);
+        unsigned int *tk = &dctrl->ticket[TK_MISC];
+        k_cg_init<R><<<nb, VB, 0, s>>>(D, 0, adj_b, adj_x, adj_r, adj_z, adj_p, adj_cg, tk);
+        double hcg[CG_N] = {0};
+        CK(cudaMemcpyAsync(hcg, adj_cg, sizeof hcg, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double bb = hcg[CG_BB];
+        int it = 0;
+        double rr = hcg[CG_RR];
+        while (it < max_iters && bb > 0.0 && rr > tol * tol * bb) {
+            const int batch = std::min(8, max_iters - it);
+            for (int j = 0; j < batch; ++j) {
+                launch_hvp(adj_p, adj_q);
+                k_cg_pq<<<nb, VB, 0, s>>>((int)n3, adj_p, adj_q, D.part, adj_cg, tk);
+                k_cg_update<R><<<nb, VB, 0, s>>>(D, 0, adj_x, adj_r, adj_z, adj_p, adj_q, adj_cg, tk);
+                k_cg_dir<<<nb, VB, 0, s>>>((int)n3, adj_z, adj_p, adj_cg);
+            }
+            it += batch;
+            CK(cudaMemcpyAsync(hcg, adj_cg, sizeof hcg, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rr = hcg[CG_RR];
+        }
+        if (iters) *iters = it;
+        if (residual) *residual = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+        k_adj_out<R><<<nb, VB, 0, s>>>(D, adj_x, adj_av, adj_ax, adj_b);
+        CK(cudaMemcpyAsync(ax0, adj_ax, bytes, cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(av0, adj_b, bytes, cudaMemcpyDefault, s));
+        if (dE) {
+            CK(cudaMemcpyAsync(adj_dE, dE, sizeof(double) * M.nt, cudaMemcpyDefault, s));
+            // the elastic gradient is linear in E_e: its derivative is the gradient with E_e = 1
+            Dev<R> D1 = D;
+            D1.mu = R(1.0 / (2.0 * (1.0 + M.nu)));
+            D1.lam = R(M.nu / ((1.0 + M.nu) * (1.0 - 2.0 * M.nu)));
+            D1.escale = nullptr;
+            k_adj_youngs<R><<<(M.nt + EB - 1) / EB, EB, 0, s>>>(D1, adj_x, adj_dE);
+            CK(cudaMemcpyAsync(dE, adj_dE, sizeof(double) * M.nt, cudaMemcpyDefault, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        eval_restore();
+        return sync_and_check();
+    }
+
     void sizes(int32_t *out) override
     {
         out[0] = M.nv; out[1] = M.nt; out[2] = M.nf; out[3] = M.ne; out[4] = M.ns; out[5] = (int32_t)M.excl.size();
@@ -641,6 +732,8 @@ private:
     unsigned int *bar_count = nullptr;
     void *ppart = nullptr;
     unsigned long long *stamp_buf = nullptr;
+    double *adj_b = nullptr, *adj_x = nullptr, *adj_r = nullptr, *adj_z = nullptr, *adj_p = nullptr, *adj_q = nullptr;
+    double *adj_av = nullptr, *adj_ax = nullptr, *adj_cg = nullptr, *adj_dE = nullptr;
     int *stamp_kind = nullptr;
 
     sim_status fail(sim_status st, const std::string &m) { err = m; return st; }
