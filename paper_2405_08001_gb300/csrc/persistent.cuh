@@ -159,6 +159,8 @@ constexpr int NQ = 5;   // most quantities one grid reduction carries
 
 // Shared memory of the persistent kernel's reductions.  The per-thread values of a reduction are stored
 // transposed (one row per quantity), so that warp q reduces quantity q: few (FP64) additions per block.
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
 template <typename R> struct PShared {
     Acc<R> t[NQ][PB];
     R mx[PB];
@@ -370,9 +372,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
     __shared__ __align__(16) unsigned char sh_raw[sizeof(PShared<R>)];   // raw storage: Acc has initialisers
     PShared<R> &sh = *reinterpret_cast<PShared<R> *>(sh_raw);
     __shared__ int sh_i;
-    // one buffer for two phases: the gradient's block-scatter accumulators and the candidate build's chunk offsets
-    constexpr size_t SBUF = sizeof(R) * 6 * SCATTER_MAXU > sizeof(unsigned int) * BP_MAX_CHUNKS
-                                ? sizeof(R) * 6 * SCATTER_MAXU : sizeof(unsigned int) * BP_MAX_CHUNKS;
+    // one buffer for several phases: the gradient's block-scatter accumulators, the candidate build's chunk
+    // offsets, then the warps' query batches
+    constexpr size_t SBUF = cmax(cmax(sizeof(R) * 6 * SCATTER_MAXU, sizeof(unsigned int) * BP_MAX_CHUNKS),
+                                 sizeof(BPQWarp) * (PB / 32));
     __shared__ __align__(16) unsigned char sbuf[SBUF];
     static_assert(SBUF >= 2 * MAX_SCENES * sizeof(double), "the batched form keeps per-scene beta and alpha here");
     static_assert(PB == SCATTER_CHUNK, "a block's tet loop covers one scatter chunk");
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         if (rebuild) {
             br.phase = 1;   // K_BP_BOXES
             // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
-            if (lead) { c->n_cand = 0; c->n_rebuilds += 1; }
+            if (lead) { c->n_cand = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
             const int nprim = B.nf + B.ne;
             float ext_max = 0.0f;
             for (int j = tid; j < max(max(nprim, B.nv), 2 * B.H); j += nthr) {
@@ -464,10 +467,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             const float ext = (float)grid_max<R>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
             if (lead) c->cell_bits = __float_as_uint(ext);
             st.mark(1);   // K_BP_BOXES
-            const float s = ext * 1.0001f;   // as cell_size() forms it from cell_bits
+            const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
             br.phase = 2;   // K_BP_COUNT
             for (int j = tid; j < nprim; j += nthr)
-                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), s, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
+                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
             grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
             // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane
@@ -529,24 +532,24 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 __syncthreads();
             }
             for (int b = tid; b < 2 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
-            for (int j = tid; j < nprim; j += nthr) {
-                const int prim = j < B.nf ? j : -1 - (j - B.nf);
-                const float4 lo = __ldcg(B.blo + j), hi = __ldcg(B.bhi + j);
-                for_cells(B, lo, hi, s, [&](int i, int jj, int kk) {
-                    const unsigned int b = prim_bucket(B, j, i, jj, kk);
-                    const unsigned int slot = choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u);
-                    if (slot >= (unsigned int)B.ecap) { atomicOr(&c->err, ERR_RANGE); return; }
-                    B.ekey[slot] = cell_key(i, jj, kk);
-                    B.eprim[slot] = prim;
-                    B.eblo[slot] = lo;
-                    B.ebhi[slot] = hi;
-                });
-            }
+            for (int j = tid; j < nprim; j += nthr)
+                fill_prim(B, j, cg, [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); });
             grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL
-            // queries: one warp per query primitive
+            // queries: batches of query primitives, the warp's batch data in sbuf; a warp takes its own batch, then
+            // whichever batches are left (edge batches come first and scan about twice the entries of point batches)
             br.phase = 5;   // K_BP_QUERY
-            for (int w = tid >> 5; w < B.ns + B.ne; w += nthr >> 5) bp_query_one(B, w, s);
+            {
+                BPQWarp &W = reinterpret_cast<BPQWarp *>(sbuf)[threadIdx.x >> 5];
+                const int nb = bpq_batches(B), nw = nthr >> 5;
+                int w = tid >> 5;
+                while (w < nb) {
+                    bpq_batch(B, w, cg, W);
+                    int nx = 0;
+                    if ((threadIdx.x & 31) == 0) nx = nw + (int)atomicAdd(&c->ticket[TK_QUERY], 1u);
+                    w = __shfl_sync(0xffffffffu, nx, 0);
+                }
+            }
             grid_barrier(br, c);
             st.mark(5);   // K_BP_QUERY
             ncand = block_read(&c->n_cand, &sh_i);

@@ -915,8 +915,9 @@ private:
             B.cshift_p = cs;
             AL(B.ctot, (2 * (size_t)H) >> cs);
         }
-        AL(B.ekey, 8 * (size_t)(M.nf + M.ne)); AL(B.eprim, 8 * (size_t)(M.nf + M.ne));
+        AL(B.ekey, 8 * (size_t)(M.nf + M.ne));
         AL(B.eblo, 8 * (size_t)(M.nf + M.ne)); AL(B.ebhi, 8 * (size_t)(M.nf + M.ne));
+        AL(B.ev, 3 * 8 * (size_t)(M.nf + M.ne));
         B.ecap = 8 * (M.nf + M.ne);
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
@@ -927,7 +928,7 @@ private:
         B.ctrl = c;
         bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), 2 * H) + BP_B - 1) / BP_B));
         bpb_prims = std::max(1, (M.nf + M.ne + BP_B - 1) / BP_B);
-        bpb_query = std::max(1, (32 * (M.ns + M.ne) + BP_B - 1) / BP_B);   // one warp per query primitive
+        bpb_query = std::max(1, (32 * ((M.ne + BPQ_QE - 1) / BPQ_QE + (M.ns + BPQ_QP - 1) / BPQ_QP) + BP_B - 1) / BP_B);   // one warp per query batch
         {
             sim_status st = setup_persistent();
             if (st != SIM_OK) return st;
