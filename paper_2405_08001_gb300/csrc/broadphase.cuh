@@ -43,11 +43,16 @@ struct BPDev {
     unsigned int *ctot;     // persistent form: [2H >> cshift_p] entries per scan chunk
     int cshift_p;           // persistent form: log2 of the buckets per scan chunk
     const int *vscene;      // batching: scene of each vertex (pairs of two scenes are never candidates); or null
-    unsigned long long *ekey;
-    float4 *eblo, *ebhi;    // the entry's primitive box (streamed with the key instead of gathered); eblo.w holds
-                            // the primitive (triangle f or -1 - edge) and ebhi.w its scene, as int bits
-    float4 *ev;             // [3][ecap] the primitive's vertices relative to the entry's cell corner (w: the
-                            // vertex index as int bits); edges use the first two rows
+    // entries, one per (primitive, cell of its box), in bucket order: everything the cheap tests of a query read
+    // sits in two 16-byte records, the positions for the distance in the ev rows
+    uint4 *erA;             // (cell key low, cell key high, v0, v1)
+    uint4 *erB;             // (box x/y low corners, box x/y high corners, box z low | high << 16, w) with the box
+                            // relative to the cell's corner in 16-bit steps of s / 16384 (rounded outwards); w is
+                            // v2 for a triangle, and for an edge the bits of the cell's offset from its box's lowest
+                            // cell (x | y << 1 | z << 2)
+    float4 *ev;             // [3][ecap] the primitive's vertices relative to the entry's cell corner; edges use
+                            // the first two rows
+    int *eprim;             // triangle f or edge index (read only where rest-pose exclusions exist)
     int ecap;               // entry capacity (8 per primitive)
     int4 *cand;
     int cap;
@@ -74,8 +79,32 @@ __device__ inline unsigned long long cell_key(int ix, int iy, int iz)
 }
 // the hash grid: cell size s and its reciprocal; every cell index of a build comes from floor(q * inv), which is
 // monotone in q, so a point inside a box lies in one of the box's cells
-struct CellGrid { float s, inv; };
-__device__ inline CellGrid grid_of(float s) { return {s, 1.0f / s}; }
+struct CellGrid { float s, inv, qs; };   // qs: steps of the 16-bit box coordinates per unit length
+__device__ inline CellGrid grid_of(float s) { return {s, 1.0f / s, 16384.0f / s}; }
+
+// 16-bit box coordinate of v in [-s, 2s) relative to a cell corner, rounded down (lo) or up (hi) with one step to
+// spare, which covers the float rounding of v
+__device__ inline unsigned int qbox_lo(float v, const CellGrid &g)
+{
+    return (unsigned int)fminf(fmaxf(floorf((v + g.s) * g.qs) - 1.0f, 0.0f), 65535.0f);
+}
+__device__ inline unsigned int qbox_hi(float v, const CellGrid &g)
+{
+    return (unsigned int)fminf(fmaxf(ceilf((v + g.s) * g.qs) + 1.0f, 0.0f), 65535.0f);
+}
+// packed box (lo.x | lo.y << 16, hi.x | hi.y << 16, lo.z | hi.z << 16) of [lo, hi] relative to a cell corner
+__device__ inline uint3 qbox(float lx, float ly, float lz, float hx, float hy, float hz, const CellGrid &g)
+{
+    return make_uint3(qbox_lo(lx, g) | qbox_lo(ly, g) << 16, qbox_hi(hx, g) | qbox_hi(hy, g) << 16,
+                      qbox_lo(lz, g) | qbox_hi(hz, g) << 16);
+}
+// do two packed boxes overlap (closed intervals on every axis)
+__device__ inline bool qbox_meet(uint3 a, uint3 b)
+{
+    const unsigned int xy = __vcmpleu2(a.x, b.y) & __vcmpleu2(b.x, a.y);
+    const unsigned int z = __vcmpleu2(__byte_perm(a.z, b.z, 0x5410), __byte_perm(b.z, a.z, 0x7632));
+    return (xy & z) == 0xffffffffu;
+}
 
 __device__ inline bool cell_of(float q, const CellGrid &g, int &i)
 {
@@ -122,13 +151,13 @@ __device__ inline bool box_cells(float4 lo, float4 hi, const CellGrid &g, int l[
            cell_of(hi.y, g, h[1]) && cell_of(hi.z, g, h[2]);
 }
 
-// Writes primitive j's entries, one per cell of its box: the cell key, the box with the primitive and its scene in
-// the w components, and the vertices relative to the entry's cell corner (formed once in double against the box's
-// lowest cell, then shifted by whole cells in float).  slot_of(b) reserves a slot of bucket b.
+// Writes primitive j's entries, one per cell of its box: the records of the cheap tests and the vertices relative
+// to the entry's cell corner (formed once in double against the box's lowest cell, then shifted by whole cells in
+// float).  slot_of(b) reserves a slot of bucket b; the slots of all cells are reserved before any entry is written.
 template <typename F> __device__ inline void fill_prim(const BPDev &B, int j, const CellGrid &g, F slot_of)
 {
     const float s = g.s;
-    float4 lo = __ldcg(B.blo + j), hi = __ldcg(B.bhi + j);
+    const float4 lo = __ldcg(B.blo + j), hi = __ldcg(B.bhi + j);
     int l[3], h[3];
     if (!box_cells(lo, hi, g, l, h)) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
     int v[3], nvp;
@@ -136,21 +165,44 @@ template <typename F> __device__ inline void fill_prim(const BPDev &B, int j, co
     float4 r[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) r[q] = rel_corner(ldcg4(B.x + v[q]), l[0], l[1], l[2], s, v[q]);
-    lo.w = __int_as_float(j < B.nf ? j : -1 - (j - B.nf));
-    hi.w = __int_as_float(B.vscene ? B.vscene[v[0]] : 0);
-    for (int i = l[0]; i <= h[0]; ++i)
-        for (int jj = l[1]; jj <= h[1]; ++jj)
-            for (int kk = l[2]; kk <= h[2]; ++kk) {
-                const unsigned int slot = slot_of(prim_bucket(B, j, i, jj, kk));
-                if (slot >= (unsigned int)B.ecap) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
-                B.ekey[slot] = cell_key(i, jj, kk);
-                B.eblo[slot] = lo;
-                B.ebhi[slot] = hi;
-                const float ox = (float)(i - l[0]) * s, oy = (float)(jj - l[1]) * s, oz = (float)(kk - l[2]) * s;
+    // the inflated box relative to the lowest cell's corner (a pre-filter only: the 16-bit form rounds outwards)
+    const float inf = (float)B.infl;
+    const float mnx = fminf(fminf(r[0].x, r[1].x), r[2].x) - inf, mxx = fmaxf(fmaxf(r[0].x, r[1].x), r[2].x) + inf;
+    const float mny = fminf(fminf(r[0].y, r[1].y), r[2].y) - inf, mxy = fmaxf(fmaxf(r[0].y, r[1].y), r[2].y) + inf;
+    const float mnz = fminf(fminf(r[0].z, r[1].z), r[2].z) - inf, mxz = fmaxf(fmaxf(r[0].z, r[1].z), r[2].z) + inf;
+    const bool tri = j < B.nf;
+    const int prim = tri ? j : j - B.nf;
+    auto put = [&](unsigned int slot, int dx, int dy, int dz) {
+        if (slot >= (unsigned int)B.ecap) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
+        const unsigned long long key = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
+        const float ox = (float)dx * s, oy = (float)dy * s, oz = (float)dz * s;
+        const uint3 bx = qbox(mnx - ox, mny - oy, mnz - oz, mxx - ox, mxy - oy, mxz - oz, g);
+        B.erA[slot] = make_uint4((unsigned int)key, (unsigned int)(key >> 32), (unsigned int)v[0], (unsigned int)v[1]);
+        const unsigned int dbits = min(dx, 1) | min(dy, 1) << 1 | min(dz, 1) << 2;
+        B.erB[slot] = make_uint4(bx.x, bx.y, bx.z, tri ? (unsigned int)v[2] : dbits);
+        B.eprim[slot] = prim;
 #pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (q < nvp) B.ev[(size_t)q * B.ecap + slot] = make_float4(r[q].x - ox, r[q].y - oy, r[q].z - oz, r[q].w);
-            }
+        for (int q = 0; q < 3; ++q)
+            if (q < nvp) B.ev[(size_t)q * B.ecap + slot] = make_float4(r[q].x - ox, r[q].y - oy, r[q].z - oz, 0.0f);
+    };
+    const int nx = h[0] - l[0] + 1, ny = h[1] - l[1] + 1, nz = h[2] - l[2] + 1;
+    if (nx <= 2 && ny <= 2 && nz <= 2) {
+        unsigned int slot[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if ((c & 1) < nx && ((c >> 1) & 1) < ny && (c >> 2) < nz)
+                slot[c] = slot_of(prim_bucket(B, j, l[0] + (c & 1), l[1] + ((c >> 1) & 1), l[2] + (c >> 2)));
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if ((c & 1) < nx && ((c >> 1) & 1) < ny && (c >> 2) < nz) put(slot[c], c & 1, (c >> 1) & 1, c >> 2);
+    } else {
+        // a box wider than two cells (only when rounding at coordinates far from the origin widens it): the grid
+        // cannot hold the build, which is flagged; the counted entries are still written, so every bucket is whole
+        atomicOr(&B.ctrl->err, ERR_RANGE);
+        for (int i = l[0]; i <= h[0]; ++i)
+            for (int jj = l[1]; jj <= h[1]; ++jj)
+                for (int kk = l[2]; kk <= h[2]; ++kk) put(slot_of(prim_bucket(B, j, i, jj, kk)), i - l[0], jj - l[1], kk - l[2]);
+    }
 }
 
 static __global__ void __launch_bounds__(BP_B) bp_boxes(BPDev B)
@@ -267,12 +319,20 @@ __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
 }
 
 // ---------------------------------------------------------------------------------------------------- queries
-// A warp takes a batch of BPQ_QB queries of one kind (points, or edges) and scans the entries of all their buckets
-// as one list, 64 per round (two per lane, loaded together), so the batch pays the latency of its headers once and
-// no lane idles at the end of a short bucket.  The batch's per-query data (cells and their keys, first entries,
-// prefix counts) sit in the warp's shared area.  A round applies only the cheap tests (cell key, box, order,
-// scene) to the entry's key and box; the entries that pass queue up in shared memory and get the exact distance 32
-// at a time, with every lane busy.  Found pairs collect in shared memory and are appended with one atomic per 32.
+// A warp takes a batch of queries of one kind (points, or edges) and scans the entries of all their buckets as one
+// list, 64 per round (two per lane, loaded together), so the batch pays the latency of its headers once and no
+// lane idles at the end of a short bucket.  The batch's per-query data (each cell's key, first entry and the
+// query's box relative to the cell's corner; prefix counts) sit in the warp's shared area.  A round reads the two
+// 16-byte records of each entry and applies the cheap tests: cell key, shared vertex, edge order, the cell rule of
+// edge pairs and the overlap of the 16-bit boxes.  The entries that pass queue up in shared memory and get the
+// exact distance 32 at a time, with every lane busy.  Found pairs collect in shared memory and are appended with one
+// atomic per 32.
+//
+// Edge pairs: each unordered pair is tested from one side only, the edge whose lower vertex index is smaller (two
+// edges without a shared vertex have different lower vertices), and in one cell only, the cell of the lower corner
+// of the intersection of the two inflated boxes.  The cell index is monotone in the coordinate, so that cell is,
+// per axis, the larger of the two boxes' lowest cells; in a cell the pair shares, it is this cell exactly when on
+// no axis both edges sit in their box's second cell (offset bits of the query's cell AND the entry's = 0).
 constexpr int BPQ_QB = 8;       // most queries of a warp batch (lanes 0..7 form the headers)
 constexpr int BPQ_QE = 6;       // edges per batch (an edge's box covers about twice the cells of a point)
 constexpr int BPQ_QP = 8;       // points per batch
@@ -281,13 +341,15 @@ constexpr int BPQ_OUT = 64;     // found pairs held before an append
 
 struct BPQWarp {
     unsigned long long ckey[BPQ_QB][8];   // key of each cell of each query (a point has one)
+    uint4 qbx[BPQ_QB][8];           // the query's box relative to each cell's corner, packed as the entries' boxes;
+                                    // w: the cell's offset bits (edge)
     unsigned int cinc[BPQ_QB][8];   // edge: inclusive prefix over its cells of their entry counts
     unsigned int cst[BPQ_QB][8];    // first entry of each cell
     float4 qa[BPQ_QB];              // point: relative to its cell's corner (w: vertex); edge: first end relative to
                                     // the corner of its box's lowest cell (w: its vertex)
-    float4 qb[BPQ_QB];              // point: float position; edge: second end as qa
-    float4 lo[BPQ_QB], hi[BPQ_QB];  // edge: its box
+    float4 qb[BPQ_QB];              // edge: second end as qa
     int4 aux[BPQ_QB];               // x: point index j or edge index a; y: scene; z: object; w: edge nx | ny << 2
+    int2 qv[BPQ_QB];                // point: (v, v); edge: (lower, higher vertex index)
     unsigned int qinc[BPQ_QB];      // inclusive prefix over the batch of the queries' entry counts
     uint2 pend[BPQ_PEND];           // (entry, query | cell << 3)
     int4 out[BPQ_OUT];
@@ -345,6 +407,7 @@ __device__ inline void bpq_shift(BPQWarp &W, int &np)
 }
 
 __device__ inline v3<float> f3sub(const float4 &a, const float4 &b) { return mkv(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ inline unsigned long long key_of(const uint4 &A) { return (unsigned long long)A.y << 32 | A.x; }
 
 // the batch's prefix counts: lane t < BPQ_QB brings its query's count; returns the batch total and leaves every
 // lane the first BPQ_QB - 1 prefixes
@@ -386,7 +449,8 @@ __device__ inline void cell_offset(int w, int c, int &dx, int &dy, int &dz)
 
 // ---- point-triangle
 
-// cheap tests of item it of a point batch: the entry is of the point's cell, its box holds the point, same scene
+// cheap tests of item it of a point batch: the entry is of the point's cell, the triangle does not hold the point,
+// and its box holds it
 __device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, const unsigned int (&qi)[BPQ_QB - 1], unsigned int it,
                                  unsigned int total, unsigned int &q, unsigned int &t)
 {
@@ -394,11 +458,11 @@ __device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, const unsigne
     unsigned int r;
     t = bpq_owner(W, qi, it, r);
     q = W.cst[t][0] + r;
-    const unsigned long long ek = __ldcg(B.ekey + q);
-    const float4 lo = __ldcg(B.eblo + q), hi = __ldcg(B.ebhi + q);
-    const float4 p = W.qb[t];
-    return ek == W.ckey[t][0] && !(p.x < lo.x || p.x > hi.x || p.y < lo.y || p.y > hi.y || p.z < lo.z || p.z > hi.z) &&
-           __float_as_int(hi.w) == W.aux[t].y;
+    const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
+    const uint4 Q = W.qbx[t][0];
+    const unsigned int v = (unsigned int)W.qv[t].x;
+    return key_of(A) == W.ckey[t][0] && A.z != v && A.w != v && E.w != v &&
+           qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
 // exact tests of the first n queued point-triangle entries (all lanes call)
@@ -412,13 +476,14 @@ __device__ inline void pt_exact(const BPDev &B, BPQWarp &W, int n, float thr, in
         const unsigned int q = pd.x;
         const int t = pd.y & 7;
         const float4 t0 = __ldcg(B.ev + q), t1 = __ldcg(B.ev + B.ecap + q), t2 = __ldcg(B.ev + 2 * (size_t)B.ecap + q);
+        const uint4 A = __ldcg(B.erA + q);
+        const int a2 = (int)__ldcg(&B.erB[q].w);
         const float4 qa = W.qa[t];
-        const int v = __float_as_int(qa.w);
-        const int a0 = __float_as_int(t0.w), a1 = __float_as_int(t1.w), a2 = __float_as_int(t2.w);
-        if (a0 == v || a1 == v || a2 == v) break;
+        const int4 ax = W.aux[t];
+        const int a0 = (int)A.z, a1 = (int)A.w;
+        if (B.vscene && B.vscene[a0] != ax.y) break;
         if (B.nexcl) {
-            const int f = __float_as_int(__ldcg(B.eblo + q).w);
-            const int4 ax = W.aux[t];
+            const int f = __ldcg(B.eprim + q);
             if (B.tri[f].w == ax.z && is_excluded(B, ((unsigned long long)ax.x << 31) | (unsigned long long)f)) break;
         }
         float cc[4];
@@ -426,7 +491,7 @@ __device__ inline void pt_exact(const BPDev &B, BPQWarp &W, int n, float thr, in
         const float d = pt_coeffs<float>(f3sub(qa, t0), f3sub(t1, t0), f3sub(t2, t0), cc, tv);
         if (!(d < thr)) break;
         found = true;
-        cnd = make_int4(v, a0, a1, a2);
+        cnd = make_int4(__float_as_int(qa.w), a0, a1, a2);
     } while (false);
     bpq_emit(B, W, nout, found, cnd);
 }
@@ -446,15 +511,18 @@ __device__ inline void bpq_points(const BPDev &B, int b, int nb, const CellGrid 
         if (!cell_of(qx, g, ix) || !cell_of(qy, g, iy) || !cell_of(qz, g, iz)) {
             atomicOr(&B.ctrl->err, ERR_RANGE);
         } else {
-            const unsigned int b = cell_hash(ix, iy, iz, B.H);
-            const unsigned int st = __ldcg(B.goff + b), len = __ldcg(B.cnt + b);
+            const unsigned int bk = cell_hash(ix, iy, iz, B.H);
+            const unsigned int st = __ldcg(B.goff + bk), len = __ldcg(B.cnt + bk);
             tot = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
             W.cst[lane][0] = st;
         }
+        const float4 p = rel_corner(X, ix, iy, iz, g.s, v);
+        const uint3 bx = qbox(p.x, p.y, p.z, p.x, p.y, p.z, g);
         W.ckey[lane][0] = cell_key(ix, iy, iz);
-        W.qa[lane] = rel_corner(X, ix, iy, iz, g.s, v);
-        W.qb[lane] = make_float4(qx, qy, qz, 0.0f);
+        W.qbx[lane][0] = make_uint4(bx.x, bx.y, bx.z, 0u);
+        W.qa[lane] = p;
         W.aux[lane] = make_int4(j, B.vscene ? B.vscene[v] : 0, B.obj[v], 0);
+        W.qv[lane] = make_int2(v, v);
     }
     unsigned int qi[BPQ_QB - 1];
     const unsigned int total = bpq_prefix(W, tot, qi);
@@ -475,10 +543,10 @@ __device__ inline void bpq_points(const BPDev &B, int b, int nb, const CellGrid 
 
 // ---- edge-edge
 
-// cheap tests of item it of an edge batch: the entry is of its cell, numbered above the query edge, of the same
-// scene, its box meets the query's, and the cell holds the lower corner of the two boxes' intersection
+// cheap tests of item it of an edge batch: the entry is of its cell, shares no vertex with the query edge and has
+// the larger lower vertex, the cell is the pair's cell, and the boxes meet
 __device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, const unsigned int (&qi)[BPQ_QB - 1], unsigned int it,
-                                 unsigned int total, const CellGrid &g, unsigned int &q, unsigned int &tc)
+                                 unsigned int total, unsigned int &q, unsigned int &tc)
 {
     if (it >= total) return false;
     unsigned int r;
@@ -488,18 +556,12 @@ __device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, const unsigne
     const int c = (ci0.x <= r) + (ci0.y <= r) + (ci0.z <= r) + (ci0.w <= r) + (ci1.x <= r) + (ci1.y <= r) + (ci1.z <= r);
     q = W.cst[t][c] + r - (c ? W.cinc[t][c - 1] : 0u);
     tc = (unsigned int)t | (unsigned int)c << 3;
-    const unsigned long long ek = __ldcg(B.ekey + q);
-    const float4 ilo = __ldcg(B.eblo + q), ihi = __ldcg(B.ebhi + q);
-    if (ek != W.ckey[t][c]) return false;
-    const int4 ax = W.aux[t];
-    if (-1 - __float_as_int(ilo.w) <= ax.x || __float_as_int(ihi.w) != ax.y) return false;
-    const float4 lo = W.lo[t], hi = W.hi[t];
-    if (lo.x > ihi.x || hi.x < ilo.x || lo.y > ihi.y || hi.y < ilo.y || lo.z > ihi.z || hi.z < ilo.z) return false;
-    int kx, ky, kz;
-    cell_of(fmaxf(lo.x, ilo.x), g, kx);
-    cell_of(fmaxf(lo.y, ilo.y), g, ky);
-    cell_of(fmaxf(lo.z, ilo.z), g, kz);
-    return cell_key(kx, ky, kz) == ek;
+    const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
+    const uint4 Q = W.qbx[t][c];
+    const int2 qv = W.qv[t];
+    const int fmn = min((int)A.z, (int)A.w), fmx = max((int)A.z, (int)A.w);
+    return key_of(A) == W.ckey[t][c] && fmn > qv.x && fmn != qv.y && fmx != qv.y && (Q.w & E.w) == 0u &&
+           qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
 // exact tests of the first n queued edge-edge entries (all lanes call)
@@ -513,13 +575,13 @@ __device__ inline void ee_exact(const BPDev &B, BPQWarp &W, int n, float s, floa
         const unsigned int q = pd.x;
         const int t = pd.y & 7, c = pd.y >> 3;
         const float4 v0 = __ldcg(B.ev + q), v1 = __ldcg(B.ev + B.ecap + q);
+        const uint4 A = __ldcg(B.erA + q);
         const float4 pa = W.qa[t], pb = W.qb[t];
-        const int ea = __float_as_int(pa.w), eb = __float_as_int(pb.w);
-        const int f0 = __float_as_int(v0.w), f1 = __float_as_int(v1.w);
-        if (f0 == ea || f0 == eb || f1 == ea || f1 == eb) break;
         const int4 ax = W.aux[t];
+        const int f0 = (int)A.z, f1 = (int)A.w;
+        if (B.vscene && B.vscene[f0] != ax.y) break;
         if (B.nexcl) {
-            const int bi = -1 - __float_as_int(__ldcg(B.eblo + q).w);
+            const int bi = __ldcg(B.eprim + q);
             if (B.edge[bi].z == ax.z &&
                 is_excluded(B, (1ull << 62) | ((unsigned long long)ax.x << 31) | (unsigned long long)bi))
                 break;
@@ -534,14 +596,13 @@ __device__ inline void ee_exact(const BPDev &B, BPQWarp &W, int n, float s, floa
         const float d = ee_coeffs<float>(f3sub(ra, v0), f3sub(rb, v0), f3sub(v1, v0), cc, tv);
         if (!(d < thr)) break;
         found = true;
-        cnd = make_int4(-1 - ea, eb, f0, f1);
+        cnd = make_int4(-1 - __float_as_int(pa.w), __float_as_int(pb.w), f0, f1);
     } while (false);
     bpq_emit(B, W, nout, found, cnd);
 }
 
 // Edge-edge batch b of nb: edges b, b + nb, b + 2 nb, ... (strided), each against the edge table buckets of the
-// cells of its own box (at most 2 per axis: a box is no wider than a cell).  A pair is found from the
-// lower-numbered edge only, in the cell holding the lower corner of the intersection of the two boxes.
+// cells of its own box (at most 2 per axis: a box is no wider than a cell).
 __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
 {
     const int lane = threadIdx.x & 31;
@@ -565,6 +626,9 @@ __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &
             if (nx > 2 || ny > 2 || ncell > 8) { atomicOr(&B.ctrl->err, ERR_RANGE); ncell = 0; nx = ny = 1; }
         }
         const int w = nx | ny << 2;
+        const float4 pa = rel_corner(XA, l[0], l[1], l[2], g.s, e.x), pb = rel_corner(XB, l[0], l[1], l[2], g.s, e.y);
+        const float mnx = fminf(pa.x, pb.x), mny = fminf(pa.y, pb.y), mnz = fminf(pa.z, pb.z);
+        const float mxx = fmaxf(pa.x, pb.x), mxy = fmaxf(pa.y, pb.y), mxz = fmaxf(pa.z, pb.z);
         unsigned int st[8], len[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -573,10 +637,13 @@ __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &
             if (c < ncell) {
                 int dx, dy, dz;
                 cell_offset(w, c, dx, dy, dz);
-                const unsigned int b = cell_hash(l[0] + dx, l[1] + dy, l[2] + dz, B.H) + (unsigned int)B.H;
-                st[c] = __ldcg(B.goff + b);
-                len[c] = __ldcg(B.cnt + b);
+                const unsigned int bk = cell_hash(l[0] + dx, l[1] + dy, l[2] + dz, B.H) + (unsigned int)B.H;
+                st[c] = __ldcg(B.goff + bk);
+                len[c] = __ldcg(B.cnt + bk);
+                const float ox = (float)dx * g.s, oy = (float)dy * g.s, oz = (float)dz * g.s;
+                const uint3 bx = qbox(mnx - ox, mny - oy, mnz - oz, mxx - ox, mxy - oy, mxz - oz, g);
                 W.ckey[lane][c] = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
+                W.qbx[lane][c] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2));
             }
         }
 #pragma unroll
@@ -586,19 +653,18 @@ __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &
             W.cst[lane][c] = st[c];
             W.cinc[lane][c] = tot;   // cells past ncell repeat the total, so no item maps to them
         }
-        W.qa[lane] = rel_corner(XA, l[0], l[1], l[2], g.s, e.x);
-        W.qb[lane] = rel_corner(XB, l[0], l[1], l[2], g.s, e.y);
-        W.lo[lane] = lo;
-        W.hi[lane] = hi;
+        W.qa[lane] = pa;
+        W.qb[lane] = pb;
         W.aux[lane] = make_int4(a, B.vscene ? B.vscene[e.x] : 0, e.z, w);
+        W.qv[lane] = make_int2(min(e.x, e.y), max(e.x, e.y));
     }
     unsigned int qi[BPQ_QB - 1];
     const unsigned int total = bpq_prefix(W, tot, qi);
     int np = 0, nout = 0;
     for (unsigned int base = 0; base < total; base += 64) {
         unsigned int q0 = 0, c0 = 0, q1 = 0, c1 = 0;
-        const bool p0 = ee_filter(B, W, qi, base + lane, total, g, q0, c0);
-        const bool p1 = ee_filter(B, W, qi, base + 32 + lane, total, g, q1, c1);
+        const bool p0 = ee_filter(B, W, qi, base + lane, total, q0, c0);
+        const bool p1 = ee_filter(B, W, qi, base + 32 + lane, total, q1, c1);
         bpq_push(W, np, p0, q0, c0);
         if (np >= 32) { __syncwarp(); ee_exact(B, W, 32, g.s, thr, nout); bpq_shift(W, np); }
         bpq_push(W, np, p1, q1, c1);

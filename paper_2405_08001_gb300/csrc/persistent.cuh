@@ -469,7 +469,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             st.mark(1);   // K_BP_BOXES
             const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
             br.phase = 2;   // K_BP_COUNT
-            for (int j = tid; j < nprim; j += nthr)
+            // primitives in contiguous runs of pblk per block, so that every SM takes a share (there are fewer
+            // primitives than threads)
+            const int pblk = (nprim + (int)gridDim.x - 1) / (int)gridDim.x;
+            for (int t = threadIdx.x, j = blockIdx.x * pblk + t; t < pblk && j < nprim; t += PB, j += PB)
                 for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
             grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 __syncthreads();
             }
             for (int b = tid; b < 2 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
-            for (int j = tid; j < nprim; j += nthr)
+            for (int t = threadIdx.x, j = blockIdx.x * pblk + t; t < pblk && j < nprim; t += PB, j += PB)
                 fill_prim(B, j, cg, [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); });
             grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL

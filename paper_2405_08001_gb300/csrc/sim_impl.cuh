@@ -915,9 +915,8 @@ private:
             B.cshift_p = cs;
             AL(B.ctot, (2 * (size_t)H) >> cs);
         }
-        AL(B.ekey, 8 * (size_t)(M.nf + M.ne));
-        AL(B.eblo, 8 * (size_t)(M.nf + M.ne)); AL(B.ebhi, 8 * (size_t)(M.nf + M.ne));
-        AL(B.ev, 3 * 8 * (size_t)(M.nf + M.ne));
+        AL(B.erA, 8 * (size_t)(M.nf + M.ne)); AL(B.erB, 8 * (size_t)(M.nf + M.ne));
+        AL(B.ev, 3 * 8 * (size_t)(M.nf + M.ne)); AL(B.eprim, 8 * (size_t)(M.nf + M.ne));
         B.ecap = 8 * (M.nf + M.ne);
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
