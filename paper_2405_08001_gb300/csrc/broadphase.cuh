@@ -16,6 +16,9 @@
 //               the entries that pass: only pairs with d < (dhat + r)(1 + 1e-3) become candidates
 #pragma once
 
+#include <cuda_fp16.h>
+#include <string.h>
+
 #include "common.cuh"
 #include "geometry.cuh"
 
@@ -46,10 +49,9 @@ struct BPDev {
     // entries, one per (primitive, cell of its box), in bucket order: everything the cheap tests of a query read
     // sits in two 16-byte records, the positions for the distance in the ev rows
     uint4 *erA;             // (cell key low, cell key high, v0, v1)
-    uint4 *erB;             // (box x/y low corners, box x/y high corners, box z low | high << 16, w) with the box
-                            // relative to the cell's corner in 16-bit steps of s / 16384 (rounded outwards); w is
-                            // v2 for a triangle, and for an edge the bits of the cell's offset from its box's lowest
-                            // cell (x | y << 1 | z << 2)
+    uint4 *erB;             // (box (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z) as half pairs, w) with the box relative
+                            // to the cell's corner in units of s, rounded outwards; w is v2 for a triangle, and for
+                            // an edge the bits of the cell's offset from its box's lowest cell (x | y << 1 | z << 2)
     float4 *ev;             // [3][ecap] the primitive's vertices relative to the entry's cell corner; edges use
                             // the first two rows
     int *eprim;             // triangle f or edge index (read only where rest-pose exclusions exist)
@@ -79,31 +81,27 @@ __device__ inline unsigned long long cell_key(int ix, int iy, int iz)
 }
 // the hash grid: cell size s and its reciprocal; every cell index of a build comes from floor(q * inv), which is
 // monotone in q, so a point inside a box lies in one of the box's cells
-struct CellGrid { float s, inv, qs; };   // qs: steps of the 16-bit box coordinates per unit length
-__device__ inline CellGrid grid_of(float s) { return {s, 1.0f / s, 16384.0f / s}; }
+struct CellGrid { float s, inv; };
+__device__ inline CellGrid grid_of(float s) { return {s, 1.0f / s}; }
 
-// 16-bit box coordinate of v in [-s, 2s) relative to a cell corner, rounded down (lo) or up (hi) with one step to
-// spare, which covers the float rounding of v
-__device__ inline unsigned int qbox_lo(float v, const CellGrid &g)
-{
-    return (unsigned int)fminf(fmaxf(floorf((v + g.s) * g.qs) - 1.0f, 0.0f), 65535.0f);
-}
-__device__ inline unsigned int qbox_hi(float v, const CellGrid &g)
-{
-    return (unsigned int)fminf(fmaxf(ceilf((v + g.s) * g.qs) + 1.0f, 0.0f), 65535.0f);
-}
-// packed box (lo.x | lo.y << 16, hi.x | hi.y << 16, lo.z | hi.z << 16) of [lo, hi] relative to a cell corner
+__device__ inline __half2 u2h(unsigned int u) { __half2 h; memcpy(&h, &u, 4); return h; }
+__device__ inline unsigned int h2u(__half2 h) { unsigned int u; memcpy(&u, &h, 4); return u; }
+
+// A box [l, h] relative to a cell corner, in units of s, as half pairs ((l.x, l.y), (h.x, h.y), (l.z, h.z)) rounded
+// outwards; 1e-6 covers the rounding of the float scaling.  Only a pre-filter reads it.
 __device__ inline uint3 qbox(float lx, float ly, float lz, float hx, float hy, float hz, const CellGrid &g)
 {
-    return make_uint3(qbox_lo(lx, g) | qbox_lo(ly, g) << 16, qbox_hi(hx, g) | qbox_hi(hy, g) << 16,
-                      qbox_lo(lz, g) | qbox_hi(hz, g) << 16);
+    const float e = 1e-6f;
+    const __half2 l = __halves2half2(__float2half_rd(lx * g.inv - e), __float2half_rd(ly * g.inv - e));
+    const __half2 h = __halves2half2(__float2half_ru(hx * g.inv + e), __float2half_ru(hy * g.inv + e));
+    const __half2 z = __halves2half2(__float2half_rd(lz * g.inv - e), __float2half_ru(hz * g.inv + e));
+    return make_uint3(h2u(l), h2u(h), h2u(z));
 }
-// do two packed boxes overlap (closed intervals on every axis)
+// do two such boxes meet (closed intervals on every axis)
 __device__ inline bool qbox_meet(uint3 a, uint3 b)
 {
-    const unsigned int xy = __vcmpleu2(a.x, b.y) & __vcmpleu2(b.x, a.y);
-    const unsigned int z = __vcmpleu2(__byte_perm(a.z, b.z, 0x5410), __byte_perm(b.z, a.z, 0x7632));
-    return (xy & z) == 0xffffffffu;
+    return __hble2(u2h(a.x), u2h(b.y)) & __hble2(u2h(b.x), u2h(a.y)) &
+           __hble2(u2h(__byte_perm(a.z, b.z, 0x5410)), u2h(__byte_perm(b.z, a.z, 0x7632)));
 }
 
 __device__ inline bool cell_of(float q, const CellGrid &g, int &i)
@@ -461,7 +459,7 @@ __device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, const unsigne
     const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
     const uint4 Q = W.qbx[t][0];
     const unsigned int v = (unsigned int)W.qv[t].x;
-    return key_of(A) == W.ckey[t][0] && A.z != v && A.w != v && E.w != v &&
+    return (key_of(A) == W.ckey[t][0]) & (A.z != v) & (A.w != v) & (E.w != v) &
            qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
@@ -560,7 +558,7 @@ __device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, const unsigne
     const uint4 Q = W.qbx[t][c];
     const int2 qv = W.qv[t];
     const int fmn = min((int)A.z, (int)A.w), fmx = max((int)A.z, (int)A.w);
-    return key_of(A) == W.ckey[t][c] && fmn > qv.x && fmn != qv.y && fmx != qv.y && (Q.w & E.w) == 0u &&
+    return (key_of(A) == W.ckey[t][c]) & (fmn > qv.x) & (fmn != qv.y) & (fmx != qv.y) & ((Q.w & E.w) == 0u) &
            qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
@@ -602,62 +600,72 @@ __device__ inline void ee_exact(const BPDev &B, BPQWarp &W, int n, float s, floa
 }
 
 // Edge-edge batch b of nb: edges b, b + nb, b + 2 nb, ... (strided), each against the edge table buckets of the
-// cells of its own box (at most 2 per axis: a box is no wider than a cell).
+// cells of its own box (at most 2 per axis: a box is no wider than a cell).  The headers take two passes of four
+// edges, eight lanes per edge (one per cell), each lane forming its edge's box and cells itself.
 __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
 {
-    const int lane = threadIdx.x & 31;
-    unsigned int tot = 0;
-    if (lane < BPQ_QE && b + lane * nb < B.ne) {
-        const int a = b + lane * nb;
-        const int4 e = B.edge[a];
-        const double4_32a XA = ldcg4(B.x + e.x), XB = ldcg4(B.x + e.y);
-        const float4 lo = make_float4(__double2float_rd(fmin(XA.x, XB.x)), __double2float_rd(fmin(XA.y, XB.y)),
-                                      __double2float_rd(fmin(XA.z, XB.z)), 0.f);
-        const float4 hi = make_float4(__double2float_ru(fmax(XA.x, XB.x)), __double2float_ru(fmax(XA.y, XB.y)),
-                                      __double2float_ru(fmax(XA.z, XB.z)), 0.f);
-        int l[3] = {0, 0, 0}, h[3] = {0, 0, 0};
-        int nx = 1, ny = 1, ncell = 0;
-        if (!box_cells(lo, hi, g, l, h)) {
-            atomicOr(&B.ctrl->err, ERR_RANGE);
-        } else {
-            nx = h[0] - l[0] + 1;
-            ny = h[1] - l[1] + 1;
-            ncell = nx * ny * (h[2] - l[2] + 1);
-            if (nx > 2 || ny > 2 || ncell > 8) { atomicOr(&B.ctrl->err, ERR_RANGE); ncell = 0; nx = ny = 1; }
-        }
-        const int w = nx | ny << 2;
-        const float4 pa = rel_corner(XA, l[0], l[1], l[2], g.s, e.x), pb = rel_corner(XB, l[0], l[1], l[2], g.s, e.y);
-        const float mnx = fminf(pa.x, pb.x), mny = fminf(pa.y, pb.y), mnz = fminf(pa.z, pb.z);
-        const float mxx = fmaxf(pa.x, pb.x), mxy = fmaxf(pa.y, pb.y), mxz = fmaxf(pa.z, pb.z);
-        unsigned int st[8], len[8];
+    const int lane = threadIdx.x & 31, c = lane & 7;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            st[c] = 0u;
-            len[c] = 0u;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int t = pass * 4 + (lane >> 3);
+        const int a = b + t * nb;
+        unsigned int st = 0u, ln = 0u;
+        if (t < BPQ_QE && a < B.ne) {
+            const int4 e = B.edge[a];
+            const double4_32a XA = ldcg4(B.x + e.x), XB = ldcg4(B.x + e.y);
+            const float4 lo = make_float4(__double2float_rd(fmin(XA.x, XB.x)), __double2float_rd(fmin(XA.y, XB.y)),
+                                          __double2float_rd(fmin(XA.z, XB.z)), 0.f);
+            const float4 hi = make_float4(__double2float_ru(fmax(XA.x, XB.x)), __double2float_ru(fmax(XA.y, XB.y)),
+                                          __double2float_ru(fmax(XA.z, XB.z)), 0.f);
+            int l[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+            int nx = 1, ny = 1, ncell = 0;
+            if (!box_cells(lo, hi, g, l, h)) {
+                if (c == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
+            } else {
+                nx = h[0] - l[0] + 1;
+                ny = h[1] - l[1] + 1;
+                ncell = nx * ny * (h[2] - l[2] + 1);
+                if (nx > 2 || ny > 2 || ncell > 8) {
+                    if (c == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
+                    ncell = 0; nx = ny = 1;
+                }
+            }
+            const int w = nx | ny << 2;
+            const float4 pa = rel_corner(XA, l[0], l[1], l[2], g.s, e.x), pb = rel_corner(XB, l[0], l[1], l[2], g.s, e.y);
             if (c < ncell) {
                 int dx, dy, dz;
                 cell_offset(w, c, dx, dy, dz);
                 const unsigned int bk = cell_hash(l[0] + dx, l[1] + dy, l[2] + dz, B.H) + (unsigned int)B.H;
-                st[c] = __ldcg(B.goff + bk);
-                len[c] = __ldcg(B.cnt + bk);
+                st = __ldcg(B.goff + bk);
+                const unsigned int len = __ldcg(B.cnt + bk);
+                ln = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
                 const float ox = (float)dx * g.s, oy = (float)dy * g.s, oz = (float)dz * g.s;
-                const uint3 bx = qbox(mnx - ox, mny - oy, mnz - oz, mxx - ox, mxy - oy, mxz - oz, g);
-                W.ckey[lane][c] = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
-                W.qbx[lane][c] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2));
+                const uint3 bx = qbox(fminf(pa.x, pb.x) - ox, fminf(pa.y, pb.y) - oy, fminf(pa.z, pb.z) - oz,
+                                      fmaxf(pa.x, pb.x) - ox, fmaxf(pa.y, pb.y) - oy, fmaxf(pa.z, pb.z) - oz, g);
+                W.ckey[t][c] = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
+                W.qbx[t][c] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2));
+            }
+            if (c == 0) {
+                W.qa[t] = pa;
+                W.qb[t] = pb;
+                W.aux[t] = make_int4(a, B.vscene ? B.vscene[e.x] : 0, e.z, w);
+                W.qv[t] = make_int2(min(e.x, e.y), max(e.x, e.y));
             }
         }
+        // inclusive prefix over the edge's cells (cells past its count repeat the total: no item maps to them)
+        unsigned int inc = ln;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const unsigned int ln = st[c] < (unsigned int)B.ecap ? min(len[c], (unsigned int)B.ecap - st[c]) : 0u;
-            tot += ln;
-            W.cst[lane][c] = st[c];
-            W.cinc[lane][c] = tot;   // cells past ncell repeat the total, so no item maps to them
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o, 8);
+            if (c >= o) inc += n;
         }
-        W.qa[lane] = pa;
-        W.qb[lane] = pb;
-        W.aux[lane] = make_int4(a, B.vscene ? B.vscene[e.x] : 0, e.z, w);
-        W.qv[lane] = make_int2(min(e.x, e.y), max(e.x, e.y));
+        if (t < BPQ_QE) {
+            W.cst[t][c] = st;
+            W.cinc[t][c] = inc;
+        }
     }
+    __syncwarp();
+    const unsigned int tot = lane < BPQ_QE ? W.cinc[lane][7] : 0u;
     unsigned int qi[BPQ_QB - 1];
     const unsigned int total = bpq_prefix(W, tot, qi);
     int np = 0, nout = 0;

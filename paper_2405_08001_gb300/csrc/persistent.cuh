@@ -161,6 +161,17 @@ constexpr int NQ = 5;   // most quantities one grid reduction carries
 // transposed (one row per quantity), so that warp q reduces quantity q: few (FP64) additions per block.
 __host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 
+// The block's contiguous share [b0, b1) of n items, about n / gridDim.x each.  Vertices, tets and pairs are fewer
+// than (or not many more than) the grid's threads, so a grid-stride loop would leave the later blocks idle and pile
+// the work, and the FP64 vertex arithmetic, on the SMs of the first ones.
+struct Share { int b0, b1; };
+__device__ inline Share share_of(int n)
+{
+    const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int b0 = min(n, (int)blockIdx.x * per);
+    return {b0, min(n, b0 + per)};
+}
+
 template <typename R> struct PShared {
     Acc<R> t[NQ][PB];
     R mx[PB];
@@ -388,6 +399,8 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthr = gridDim.x * blockDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const Share vs = share_of(D.nv), ts = share_of(D.nt);
+    const int ov = vs.b0 + (int)threadIdx.x;   // this thread's own vertex (the first of its share), when < vs.b1
     // state every block reads before anyone can change it
     int rebuild = (volatile int &)c->rebuild;
     const bool skip_step = (volatile uint32_t &)c->err != 0u;
@@ -405,7 +418,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         br.phase = 0;   // K_PREDICT
         R md = R(0);
         if (!skip_step) {
-            for (int i = tid; i < D.nv; i += nthr) {
+            for (int i = ov; i < vs.b1; i += PB) {
                 double4_32a X = D.x[i];
                 const double4_32a V = D.v[i];
                 D.xt[i] = X;
@@ -569,22 +582,22 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
                 tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
         } else {
-            for (int e = tid; e < D.nt; e += nthr) {
+            for (int e = ts.b0 + (int)threadIdx.x; e < ts.b1; e += PB) {
                 TetIn<R> in;
                 load_tet_in<R>(D, e, in);
                 tet_grad<R>(D, e, par, in);
             }
         }
         {
-            const int nc = min(ncand, D.cand_cap);
-            for (int ci = tid; ci < nc; ci += nthr) pair_grad<R>(D, ci, par);
+            const Share cs = share_of(min(ncand, D.cand_cap));
+            for (int ci = cs.b0 + (int)threadIdx.x; ci < cs.b1; ci += PB) pair_grad<R>(D, ci, par);
         }
         grid_barrier(br, c);
         st.mark(6);   // K_GRAD
         if (D.segmented) {
             br.phase = 7;   // K_GATHER
             const int n4 = 4 * D.nt;
-            for (int i = tid; i < D.nv; i += nthr) {
+            for (int i = ov; i < vs.b1; i += PB) {
                 R s6[6] = {0, 0, 0, 0, 0, 0};
                 for (int q = D.v2c_off[i]; q < D.v2c_off[i + 1]; ++q) {
                     const int cc = D.v2c[q];
@@ -608,11 +621,11 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         double beta = 0.0;
         int restarted = 0;
         int na;
-        R4 oG, oDg, oPG, oP0;   // this thread's own vertex (i == tid), kept for the direction pass
+        R4 oG, oDg, oPG, oP0;   // this thread's own vertex (i == ov), kept for the direction pass
         br.phase = 8;   // K_DOTS
         {
             Acc<R> s5[5];
-            for (int i = tid; i < D.nv; i += nthr) {
+            for (int i = ov; i < vs.b1; i += PB) {
                 const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i);
                 R4 P0 = ldcg4(D.p + i);
                 R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
@@ -638,7 +651,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                     P0 = PG;
                 }
                 D.pg[i] = PG;
-                if (i == tid) { oG = G; oDg = Dg; oPG = PG; oP0 = P0; }
+                if (i == ov) { oG = G; oDg = Dg; oPG = PG; oP0 = P0; }
             }
             Fetch f;
             f.pi = &c->n_active;
@@ -681,8 +694,8 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             const bool nzb = beta != 0.0;
             Acc<R> s3[3];   // g . p, p^T M p (+ half-space part), p^T H p of tets and pairs
             R pm = R(0);
-            for (int i = tid; i < D.nv; i += nthr) {
-                const bool own = i == tid;
+            for (int i = ov; i < vs.b1; i += PB) {
+                const bool own = i == ov;
                 const R4 Dg = own ? oDg : ldcg4(D.dg[par] + i);
                 R4 Pn = mk4<R>(R(0), R(0), R(0), R(0));
                 if (Dg.w > R(0)) {
@@ -701,12 +714,13 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 }
                 D.pnext[i] = Pn;
             }
-            for (int e = tid; e < D.nt; e += nthr) {
+            for (int e = ts.b0 + (int)threadIdx.x; e < ts.b1; e += PB) {
                 const int4 tv = D.tet[e];
                 s3[2].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
                                          dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
             }
-            for (int kk = tid; kk < na; kk += nthr) {
+            const Share as = share_of(na);
+            for (int kk = as.b0 + (int)threadIdx.x; kk < as.b1; kk += PB) {
                 Active<R> ap;
                 load_active<R>(D, kk, ap);
                 s3[2].add_d(pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
@@ -718,11 +732,11 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             block_publish<R, 3, true>(s3, pm, part, sh);
             grid_barrier(br, c);
             // the update's loads of this thread's own vertex go out before the partial collection and the step rule
-            if (tid < D.nv) {
-                uX = ldcg4(D.x + tid);
-                uP = ldcg4(D.pnext + tid);
-                uXT = ldcg4(D.xtil + tid);
-                uXB = disp_ref<R>(D, tid);
+            if (ov < vs.b1) {
+                uX = ldcg4(D.x + ov);
+                uP = ldcg4(D.pnext + ov);
+                uXT = ldcg4(D.xtil + ov);
+                uXB = disp_ref<R>(D, ov);
             }
             grid_collect<R, 3, true>(part, sh, &f);
             st.mark(10);  // K_PHP (direction included)
@@ -782,11 +796,11 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         br.phase = 11;   // K_UPDATE
         {
             R md = R(0);
-            for (int i = tid; i < D.nv; i += nthr) {
+            for (int i = ov; i < vs.b1; i += PB) {
                 double4_32a X, XT;
                 R4 P;
                 typename DispRef<R>::T XB;
-                if (i == tid) { X = uX; P = uP; XT = uXT; XB = uXB; }
+                if (i == ov) { X = uX; P = uP; XT = uXT; XB = uXB; }
                 else { X = ldcg4(D.x + i); P = ldcg4(D.pnext + i); XT = ldcg4(D.xtil + i); XB = disp_ref<R>(D, i); }
                 X.x += alpha * double(P.x); X.y += alpha * double(P.y); X.z += alpha * double(P.z);
                 put_x<R>(D, i, X);
@@ -807,7 +821,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         br.phase = 12;   // K_FINISH
         grid_barrier(br, c);
         const bool bad = (volatile uint32_t &)c->err != 0u;
-        for (int i = tid; i < D.nv; i += nthr) {
+        for (int i = ov; i < vs.b1; i += PB) {
             const double4_32a X = ldcg4(D.x + i), XT = ldcg4(D.xt + i);
             if (bad) {
                 put_x<R>(D, i, XT);
