@@ -317,13 +317,14 @@ __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
 }
 
 // ---------------------------------------------------------------------------------------------------- queries
-// A warp takes a batch of queries of one kind (points, or edges) and scans the entries of all their buckets as one
-// list, 64 per round (two per lane, loaded together), so the batch pays the latency of its headers once and no
-// lane idles at the end of a short bucket.  The batch's per-query data (each cell's key, first entry and the
-// query's box relative to the cell's corner; prefix counts) sit in the warp's shared area.  A round reads the two
-// 16-byte records of each entry and applies the cheap tests: cell key, shared vertex, edge order, the cell rule of
-// edge pairs and the overlap of the 16-bit boxes.  The entries that pass queue up in shared memory and get the
-// exact distance 32 at a time, with every lane busy.  Found pairs collect in shared memory and are appended with one
+// A warp takes a batch of queries of one kind (points, or edges).  Its header lists the batch's non-empty
+// (query, cell) segments in shared memory: the bucket's first entry, the segment's first item in the batch, the
+// cell's key and the query's box relative to the cell's corner.  The warp then scans all the segments' entries as
+// one list, 64 per round (two windows of 32, one item per lane each, loaded together); a lane finds its segment
+// from the window's segment starts, gathered into one bit mask by a warp OR.  A round reads the two 16-byte records
+// of each entry and applies the cheap tests: cell key, shared vertex, edge order, the cell rule of edge pairs and
+// the overlap of the half-precision boxes.  The entries that pass queue up in shared memory and get the exact
+// distance 32 at a time, with every lane busy.  Found pairs collect in shared memory and are appended with one
 // atomic per 32.
 //
 // Edge pairs: each unordered pair is tested from one side only, the edge whose lower vertex index is smaller (two
@@ -331,24 +332,21 @@ __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
 // of the intersection of the two inflated boxes.  The cell index is monotone in the coordinate, so that cell is,
 // per axis, the larger of the two boxes' lowest cells; in a cell the pair shares, it is this cell exactly when on
 // no axis both edges sit in their box's second cell (offset bits of the query's cell AND the entry's = 0).
-constexpr int BPQ_QB = 8;       // most queries of a warp batch (lanes 0..7 form the headers)
 constexpr int BPQ_QE = 6;       // edges per batch (an edge's box covers about twice the cells of a point)
 constexpr int BPQ_QP = 8;       // points per batch
+constexpr int BPQ_SEG = 48;     // (query, cell) segments of a batch: 6 edges x 8 cells, or 8 points
 constexpr int BPQ_PEND = 64;    // entries past the cheap tests, awaiting the distance
 constexpr int BPQ_OUT = 64;     // found pairs held before an append
 
 struct BPQWarp {
-    unsigned long long ckey[BPQ_QB][8];   // key of each cell of each query (a point has one)
-    uint4 qbx[BPQ_QB][8];           // the query's box relative to each cell's corner, packed as the entries' boxes;
-                                    // w: the cell's offset bits (edge)
-    unsigned int cinc[BPQ_QB][8];   // edge: inclusive prefix over its cells of their entry counts
-    unsigned int cst[BPQ_QB][8];    // first entry of each cell
-    float4 qa[BPQ_QB];              // point: relative to its cell's corner (w: vertex); edge: first end relative to
+    uint4 sa[BPQ_SEG];              // (first entry, first item, query's lower vertex, higher vertex; a point: v, v)
+    unsigned long long sk[BPQ_SEG]; // the cell's key
+    uint4 sb[BPQ_SEG];              // the query's box relative to the cell's corner (as the entries'), w: the cell's
+                                    // offset bits (edge) | query << 8 | cell << 11
+    float4 qa[BPQ_QP];              // point: relative to its cell's corner (w: vertex); edge: first end relative to
                                     // the corner of its box's lowest cell (w: its vertex)
-    float4 qb[BPQ_QB];              // edge: second end as qa
-    int4 aux[BPQ_QB];               // x: point index j or edge index a; y: scene; z: object; w: edge nx | ny << 2
-    int2 qv[BPQ_QB];                // point: (v, v); edge: (lower, higher vertex index)
-    unsigned int qinc[BPQ_QB];      // inclusive prefix over the batch of the queries' entry counts
+    float4 qb[BPQ_QE];              // edge: second end as qa
+    int4 aux[BPQ_QP];               // x: point index j or edge index a; y: scene; z: object; w: edge nx | ny << 2
     uint2 pend[BPQ_PEND];           // (entry, query | cell << 3)
     int4 out[BPQ_OUT];
 };
@@ -407,32 +405,41 @@ __device__ inline void bpq_shift(BPQWarp &W, int &np)
 __device__ inline v3<float> f3sub(const float4 &a, const float4 &b) { return mkv(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ inline unsigned long long key_of(const uint4 &A) { return (unsigned long long)A.y << 32 | A.x; }
 
-// the batch's prefix counts: lane t < BPQ_QB brings its query's count; returns the batch total and leaves every
-// lane the first BPQ_QB - 1 prefixes
-__device__ inline unsigned int bpq_prefix(BPQWarp &W, unsigned int tot, unsigned int (&qi)[BPQ_QB - 1])
+// Appends the lanes' segments to the batch's list (all lanes call; ln = 0 for none): returns the segment slot of
+// a lane with a segment; nseg and nitem (warp-uniform) grow by the segments and their entries.
+__device__ inline int bpq_add_segments(unsigned int ln, int &nseg, unsigned int &nitem, unsigned int &first)
 {
     const int lane = threadIdx.x & 31;
-    unsigned int inc = tot;
+    const unsigned int m = __ballot_sync(0xffffffffu, ln > 0u);
+    unsigned int inc = ln;
 #pragma unroll
-    for (int o = 1; o < BPQ_QB; o <<= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
         const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += n;
     }
-    if (lane < BPQ_QB) W.qinc[lane] = inc;
-#pragma unroll
-    for (int q = 0; q < BPQ_QB - 1; ++q) qi[q] = __shfl_sync(0xffffffffu, inc, q);
-    __syncwarp();
-    return __shfl_sync(0xffffffffu, inc, BPQ_QB - 1);
+    first = nitem + inc - ln;
+    const int slot = nseg + __popc(m & lanemask_lt());
+    nseg += __popc(m);
+    nitem += __shfl_sync(0xffffffffu, inc, 31);
+    return slot;
 }
 
-// the query owning item it of the batch, and the item's index within it
-__device__ inline int bpq_owner(const BPQWarp &W, const unsigned int (&qi)[BPQ_QB - 1], unsigned int it, unsigned int &r)
+// The segment of item it of the window [base, base + 32) that starts in segment k0 (all lanes call): the lanes
+// bring the starts of segments k0 + 1 .. k0 + 32 (at most 32 start inside a window of 32 items, all segments being
+// non-empty), one warp OR gathers them into a mask of window offsets.  Returns the lane's segment; k_next is the
+// segment of the window's last item.
+__device__ inline int bpq_window(const BPQWarp &W, int nseg, unsigned int base, int k0, int &k_next)
 {
-    int t = 0;
-#pragma unroll
-    for (int q = 0; q < BPQ_QB - 1; ++q) t += qi[q] <= it ? 1 : 0;
-    r = it - (t ? W.qinc[t - 1] : 0u);
-    return t;
+    const int lane = threadIdx.x & 31;
+    const int k = k0 + 1 + lane;
+    unsigned int bit = 0u;
+    if (k < nseg) {
+        const unsigned int off = W.sa[k].y - base;   // > 0: the segment starts after base
+        if (off < 32u) bit = 1u << off;
+    }
+    const unsigned int M = __reduce_or_sync(0xffffffffu, bit);
+    k_next = k0 + __popc(M);
+    return k0 + __popc(M & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
 }
 
 // offset of cell c among the cells of an edge's box (nx, ny packed in w)
@@ -447,19 +454,18 @@ __device__ inline void cell_offset(int w, int c, int &dx, int &dy, int &dz)
 
 // ---- point-triangle
 
-// cheap tests of item it of a point batch: the entry is of the point's cell, the triangle does not hold the point,
-// and its box holds it
-__device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, const unsigned int (&qi)[BPQ_QB - 1], unsigned int it,
-                                 unsigned int total, unsigned int &q, unsigned int &t)
+// cheap tests of an entry q of segment k of a point batch: the entry is of the point's cell, the triangle does not
+// hold the point, and its box holds it
+__device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, bool valid, int k, unsigned int it, unsigned int &q,
+                                 unsigned int &tc)
 {
-    if (it >= total) return false;
-    unsigned int r;
-    t = bpq_owner(W, qi, it, r);
-    q = W.cst[t][0] + r;
+    if (!valid) return false;
+    const uint4 S = W.sa[k];
+    q = S.x + (it - S.y);
     const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
-    const uint4 Q = W.qbx[t][0];
-    const unsigned int v = (unsigned int)W.qv[t].x;
-    return (key_of(A) == W.ckey[t][0]) & (A.z != v) & (A.w != v) & (E.w != v) &
+    const uint4 Q = W.sb[k];
+    tc = Q.w >> 8;
+    return (key_of(A) == W.sk[k]) & (A.z != S.z) & (A.w != S.z) & (E.w != S.z) &
            qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
@@ -499,36 +505,47 @@ __device__ inline void pt_exact(const BPDev &B, BPQWarp &W, int n, float thr, in
 __device__ inline void bpq_points(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
 {
     const int lane = threadIdx.x & 31;
-    unsigned int tot = 0;
+    unsigned int ln = 0u, st = 0u;
+    unsigned long long key = 0ull;
+    uint3 bx = make_uint3(0u, 0u, 0u);
+    int v = 0;
     if (lane < BPQ_QP && b + lane * nb < B.ns) {
         const int j = b + lane * nb;
-        const int v = B.svert[j];
+        v = B.svert[j];
         const double4_32a X = ldcg4(B.x + v);
-        const float qx = (float)X.x, qy = (float)X.y, qz = (float)X.z;
         int ix = 0, iy = 0, iz = 0;
-        if (!cell_of(qx, g, ix) || !cell_of(qy, g, iy) || !cell_of(qz, g, iz)) {
+        if (!cell_of((float)X.x, g, ix) || !cell_of((float)X.y, g, iy) || !cell_of((float)X.z, g, iz)) {
             atomicOr(&B.ctrl->err, ERR_RANGE);
         } else {
             const unsigned int bk = cell_hash(ix, iy, iz, B.H);
-            const unsigned int st = __ldcg(B.goff + bk), len = __ldcg(B.cnt + bk);
-            tot = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
-            W.cst[lane][0] = st;
+            st = __ldcg(B.goff + bk);
+            const unsigned int len = __ldcg(B.cnt + bk);
+            ln = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
         }
         const float4 p = rel_corner(X, ix, iy, iz, g.s, v);
-        const uint3 bx = qbox(p.x, p.y, p.z, p.x, p.y, p.z, g);
-        W.ckey[lane][0] = cell_key(ix, iy, iz);
-        W.qbx[lane][0] = make_uint4(bx.x, bx.y, bx.z, 0u);
+        bx = qbox(p.x, p.y, p.z, p.x, p.y, p.z, g);
+        key = cell_key(ix, iy, iz);
         W.qa[lane] = p;
         W.aux[lane] = make_int4(j, B.vscene ? B.vscene[v] : 0, B.obj[v], 0);
-        W.qv[lane] = make_int2(v, v);
     }
-    unsigned int qi[BPQ_QB - 1];
-    const unsigned int total = bpq_prefix(W, tot, qi);
-    int np = 0, nout = 0;
+    int nseg = 0;
+    unsigned int total = 0u, first;
+    const int slot = bpq_add_segments(ln, nseg, total, first);
+    if (ln > 0u) {
+        W.sa[slot] = make_uint4(st, first, (unsigned int)v, (unsigned int)v);
+        W.sk[slot] = key;
+        W.sb[slot] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)lane << 8);
+    }
+    __syncwarp();
+    int np = 0, nout = 0, k0 = 0;
     for (unsigned int base = 0; base < total; base += 64) {
+        int k1, k2;
+        const int ka = bpq_window(W, nseg, base, k0, k1);
+        const int kb = bpq_window(W, nseg, base + 32, k1, k2);
+        k0 = k2;
         unsigned int q0 = 0, t0 = 0, q1 = 0, t1 = 0;
-        const bool p0 = pt_filter(B, W, qi, base + lane, total, q0, t0);
-        const bool p1 = pt_filter(B, W, qi, base + 32 + lane, total, q1, t1);
+        const bool p0 = pt_filter(B, W, base + lane < total, ka, base + lane, q0, t0);
+        const bool p1 = pt_filter(B, W, base + 32 + lane < total, kb, base + 32 + lane, q1, t1);
         bpq_push(W, np, p0, q0, t0);
         if (np >= 32) { __syncwarp(); pt_exact(B, W, 32, thr, nout); bpq_shift(W, np); }
         bpq_push(W, np, p1, q1, t1);
@@ -541,24 +558,19 @@ __device__ inline void bpq_points(const BPDev &B, int b, int nb, const CellGrid 
 
 // ---- edge-edge
 
-// cheap tests of item it of an edge batch: the entry is of its cell, shares no vertex with the query edge and has
-// the larger lower vertex, the cell is the pair's cell, and the boxes meet
-__device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, const unsigned int (&qi)[BPQ_QB - 1], unsigned int it,
-                                 unsigned int total, unsigned int &q, unsigned int &tc)
+// cheap tests of an entry of segment k of an edge batch: the entry is of its cell, shares no vertex with the query
+// edge and has the larger lower vertex, the cell is the pair's cell, and the boxes meet
+__device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, bool valid, int k, unsigned int it, unsigned int &q,
+                                 unsigned int &tc)
 {
-    if (it >= total) return false;
-    unsigned int r;
-    const int t = bpq_owner(W, qi, it, r);
-    const uint4 ci0 = *reinterpret_cast<const uint4 *>(&W.cinc[t][0]);
-    const uint4 ci1 = *reinterpret_cast<const uint4 *>(&W.cinc[t][4]);
-    const int c = (ci0.x <= r) + (ci0.y <= r) + (ci0.z <= r) + (ci0.w <= r) + (ci1.x <= r) + (ci1.y <= r) + (ci1.z <= r);
-    q = W.cst[t][c] + r - (c ? W.cinc[t][c - 1] : 0u);
-    tc = (unsigned int)t | (unsigned int)c << 3;
+    if (!valid) return false;
+    const uint4 S = W.sa[k];
+    q = S.x + (it - S.y);
     const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
-    const uint4 Q = W.qbx[t][c];
-    const int2 qv = W.qv[t];
+    const uint4 Q = W.sb[k];
+    tc = Q.w >> 8;
     const int fmn = min((int)A.z, (int)A.w), fmx = max((int)A.z, (int)A.w);
-    return (key_of(A) == W.ckey[t][c]) & (fmn > qv.x) & (fmn != qv.y) & (fmx != qv.y) & ((Q.w & E.w) == 0u) &
+    return (key_of(A) == W.sk[k]) & (fmn > (int)S.z) & (fmn != (int)S.w) & (fmx != (int)S.w) & ((Q.w & E.w & 7u) == 0u) &
            qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
 }
 
@@ -605,13 +617,20 @@ __device__ inline void ee_exact(const BPDev &B, BPQWarp &W, int n, float s, floa
 __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
 {
     const int lane = threadIdx.x & 31, c = lane & 7;
+    int nseg = 0;
+    unsigned int total = 0u;
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
         const int t = pass * 4 + (lane >> 3);
         const int a = b + t * nb;
         unsigned int st = 0u, ln = 0u;
+        unsigned long long key = 0ull;
+        uint4 sb = make_uint4(0u, 0u, 0u, 0u);
+        int vlo = 0, vhi = 0;
         if (t < BPQ_QE && a < B.ne) {
             const int4 e = B.edge[a];
+            vlo = min(e.x, e.y);
+            vhi = max(e.x, e.y);
             const double4_32a XA = ldcg4(B.x + e.x), XB = ldcg4(B.x + e.y);
             const float4 lo = make_float4(__double2float_rd(fmin(XA.x, XB.x)), __double2float_rd(fmin(XA.y, XB.y)),
                                           __double2float_rd(fmin(XA.z, XB.z)), 0.f);
@@ -642,37 +661,33 @@ __device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &
                 const float ox = (float)dx * g.s, oy = (float)dy * g.s, oz = (float)dz * g.s;
                 const uint3 bx = qbox(fminf(pa.x, pb.x) - ox, fminf(pa.y, pb.y) - oy, fminf(pa.z, pb.z) - oz,
                                       fmaxf(pa.x, pb.x) - ox, fmaxf(pa.y, pb.y) - oy, fmaxf(pa.z, pb.z) - oz, g);
-                W.ckey[t][c] = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
-                W.qbx[t][c] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2));
+                key = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
+                sb = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2) | (unsigned int)t << 8 | (unsigned int)c << 11);
             }
             if (c == 0) {
                 W.qa[t] = pa;
                 W.qb[t] = pb;
                 W.aux[t] = make_int4(a, B.vscene ? B.vscene[e.x] : 0, e.z, w);
-                W.qv[t] = make_int2(min(e.x, e.y), max(e.x, e.y));
             }
         }
-        // inclusive prefix over the edge's cells (cells past its count repeat the total: no item maps to them)
-        unsigned int inc = ln;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o, 8);
-            if (c >= o) inc += n;
-        }
-        if (t < BPQ_QE) {
-            W.cst[t][c] = st;
-            W.cinc[t][c] = inc;
+        unsigned int first;
+        const int slot = bpq_add_segments(ln, nseg, total, first);
+        if (ln > 0u) {
+            W.sa[slot] = make_uint4(st, first, (unsigned int)vlo, (unsigned int)vhi);
+            W.sk[slot] = key;
+            W.sb[slot] = sb;
         }
     }
     __syncwarp();
-    const unsigned int tot = lane < BPQ_QE ? W.cinc[lane][7] : 0u;
-    unsigned int qi[BPQ_QB - 1];
-    const unsigned int total = bpq_prefix(W, tot, qi);
-    int np = 0, nout = 0;
+    int np = 0, nout = 0, k0 = 0;
     for (unsigned int base = 0; base < total; base += 64) {
+        int k1, k2;
+        const int ka = bpq_window(W, nseg, base, k0, k1);
+        const int kb = bpq_window(W, nseg, base + 32, k1, k2);
+        k0 = k2;
         unsigned int q0 = 0, c0 = 0, q1 = 0, c1 = 0;
-        const bool p0 = ee_filter(B, W, qi, base + lane, total, q0, c0);
-        const bool p1 = ee_filter(B, W, qi, base + 32 + lane, total, q1, c1);
+        const bool p0 = ee_filter(B, W, base + lane < total, ka, base + lane, q0, c0);
+        const bool p1 = ee_filter(B, W, base + 32 + lane < total, kb, base + 32 + lane, q1, c1);
         bpq_push(W, np, p0, q0, c0);
         if (np >= 32) { __syncwarp(); ee_exact(B, W, 32, g.s, thr, nout); bpq_shift(W, np); }
         bpq_push(W, np, p1, q1, c1);

@@ -37,12 +37,13 @@ struct Bar {
     int max, phase;
 };
 
-__device__ inline unsigned int ld_acquire(const unsigned int *p)
+__device__ inline unsigned int ld_relaxed(const unsigned int *p)
 {
     unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ inline void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ inline void red_release_add(unsigned int *p, unsigned int v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -54,8 +55,10 @@ __device__ inline unsigned long long global_ns()
     return t;
 }
 
-// The block's writes are ordered before its arrival by the CTA barrier and the fence; the arrival is one release
-// add (no round trip), and the lead thread polls the counter with acquire loads.
+// The block's writes are ordered before its arrival by the CTA barrier and the release add (a release operation is a
+// cumulative fence followed by the add, so no separate fence is needed; the add needs no round trip).  The lead
+// thread polls the counter with relaxed loads and, once it has seen every arrival, orders the block's later reads
+// after the other blocks' writes with one acquire fence, before the CTA barrier hands on to the block.
 __device__ inline void grid_barrier(Bar &br, Ctrl *c)
 {
     __syncthreads();
@@ -64,11 +67,10 @@ __device__ inline void grid_barrier(Bar &br, Ctrl *c)
         const unsigned int target = br.n * gridDim.x;
         const bool rec = br.arrive && (int)br.n <= br.max;
         if (rec) br.arrive[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();
-        __threadfence();
         red_release_add(br.count, 1u);
         unsigned long long t0 = 0;
         int n = 0;
-        while ((int)(ld_acquire(br.count) - target) < 0) {
+        while ((int)(ld_relaxed(br.count) - target) < 0) {
             if ((++n & 31) == 0) {
                 if ((volatile uint32_t &)c->err & ERR_TIMEOUT) break;
                 const unsigned long long t = global_ns();
@@ -76,6 +78,7 @@ __device__ inline void grid_barrier(Bar &br, Ctrl *c)
                 else if (t - t0 > BARRIER_LIMIT_NS) { atomicOr(&c->err, ERR_TIMEOUT); break; }
             }
         }
+        fence_acq_rel();
         if (rec) {
             br.depart[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();
             if (blockIdx.x == 0) br.kind[br.n - 1] = br.phase;
@@ -462,30 +465,26 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             if (lead) { c->n_cand = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
             const int nprim = B.nf + B.ne;
             float ext_max = 0.0f;
-            for (int j = tid; j < max(max(nprim, B.nv), 2 * B.H); j += nthr) {
-                if (j < 2 * B.H) B.cnt[j] = 0u;
-                if (j < B.nv) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
-                if (j < nprim) {
-                    int v[3];
-                    int nvp;
-                    if (j < B.nf) { const int4 t = B.tri[j]; v[0] = t.x; v[1] = t.y; v[2] = t.z; nvp = 3; }
-                    else { const int4 e = B.edge[j - B.nf]; v[0] = e.x; v[1] = e.y; nvp = 2; }
-                    float4 lo, hi;
-                    box_of(B.x, v, nvp, B.infl, lo, hi);
-                    B.blo[j] = lo;
-                    B.bhi[j] = hi;
-                    ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
-                }
+            for (int j = tid; j < 2 * B.H; j += nthr) B.cnt[j] = 0u;
+            for (int j = ov; j < vs.b1; j += PB) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
+            const Share ps = share_of(nprim);
+            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) {
+                int v[3];
+                int nvp;
+                if (j < B.nf) { const int4 t = B.tri[j]; v[0] = t.x; v[1] = t.y; v[2] = t.z; nvp = 3; }
+                else { const int4 e = B.edge[j - B.nf]; v[0] = e.x; v[1] = e.y; nvp = 2; }
+                float4 lo, hi;
+                box_of(B.x, v, nvp, B.infl, lo, hi);
+                B.blo[j] = lo;
+                B.bhi[j] = hi;
+                ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
             }
             const float ext = (float)grid_max<R>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
             if (lead) c->cell_bits = __float_as_uint(ext);
             st.mark(1);   // K_BP_BOXES
             const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
             br.phase = 2;   // K_BP_COUNT
-            // primitives in contiguous runs of pblk per block, so that every SM takes a share (there are fewer
-            // primitives than threads)
-            const int pblk = (nprim + (int)gridDim.x - 1) / (int)gridDim.x;
-            for (int t = threadIdx.x, j = blockIdx.x * pblk + t; t < pblk && j < nprim; t += PB, j += PB)
+            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
                 for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
             grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
@@ -548,7 +547,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 __syncthreads();
             }
             for (int b = tid; b < 2 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
-            for (int t = threadIdx.x, j = blockIdx.x * pblk + t; t < pblk && j < nprim; t += PB, j += PB)
+            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
                 fill_prim(B, j, cg, [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); });
             grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL

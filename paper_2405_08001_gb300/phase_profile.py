@@ -45,15 +45,18 @@ def main():
         B.sim_step(sim.h, 1, tg[s])
     acc = collections.defaultdict(list)
     nblocks = 0
+    spans = []
     for s in range(args.warmup, args.warmup + args.steps):
         a, d, kinds = B.sim_profile_barriers(sim.h, tg[s])
         nblocks = a.shape[1]
+        spans.append(float(a[-1].astype(np.int64).max() - d[0].astype(np.int64).min()))
         for k, v in phase_table(a, d, kinds).items():
             acc[k].append(v)
     sim.close()
     print(f"{args.scene} {args.precision}: {args.steps} steps after {args.warmup} warm-up steps, {nblocks} blocks; "
           f"times in microseconds, per phase instance")
     print(f"{'phase':12s} {'per step':>8s} {'span':>8s} {'median':>8s} {'max':>8s} {'release':>8s} {'late':>8s}")
+    print(f"step span (first barrier's release to the last arrival): {np.mean(spans) / 1e3:.1f} us")
     for k, parts in acc.items():
         v = np.concatenate(parts)
         print(f"{k:12s} {len(v) / args.steps:8.1f} {v[:, 0].mean() / 1e3:8.2f} {v[:, 1].mean() / 1e3:8.2f} "
