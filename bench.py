@@ -160,15 +160,31 @@ def recorded_traffic(kernel: str, prec_name: str, phases: bool = False):
         return None
 
 
-def time_steps(B, torch, sim, targets, first, K, flush):
-    """Times K time steps one by one with CUDA events on the solver's stream; returns per-step milliseconds."""
+def window(W, K, cfg_steps):
+    """First step of the timed window: the window ends with the configured run's last step (where the twisted
+    bar carries the most contact candidates), after at least W untimed warm-up steps."""
+    return max(W, cfg_steps - K)
+
+
+def time_steps(B, torch, sim, targets, first, K, flush, cfg_steps):
+    """Times K time steps one by one with CUDA events on the solver's stream; returns per-step milliseconds.  The
+    steps are first .. cfg_steps - 1; a longer K starts over at `first` from the state saved there (the restore is
+    not timed), so every timed step is a step of the configured run."""
     stream = torch.cuda.current_stream()
+    span = max(1, cfg_steps - first)
+    saved = None
+    if K > span:
+        torch.cuda.synchronize()
+        x0, v0, _ = B.sim_get_state(sim.h)
+        saved = (x0, v0)
     times = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     for s in range(K):
+        if s > 0 and s % span == 0:
+            B.sim_set_state(sim.h, *saved)
         flush.zero_()
         ev[s][0].record(stream)
-        B.sim_step_async(sim.h, 1, targets[first + s])
+        B.sim_step_async(sim.h, 1, targets[first + s % span])
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     for a, b in ev:
@@ -191,7 +207,9 @@ def run_ours(args):
     sc = S.twisted_bar()
     iters = sc.iters
     W, K = args.warmup, args.steps
-    n_total = W + K + 4
+    cfg_steps = sc.steps
+    first = window(W, K, cfg_steps)
+    n_total = max(first + K, cfg_steps) + 4
     # a dedicated stream: the solver, the events and the L2 flush all run on it (the legacy default stream could
     # not be captured into the solver's CUDA graph)
     stream = torch.cuda.Stream()
@@ -204,14 +222,15 @@ def run_ours(args):
 
     def one_form(prec, K_, form=1):
         sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else form)
-        for s in range(W):
+        first_ = window(W, K_, cfg_steps)
+        for s in range(first_):
             B.sim_step_async(sim.h, 1, targets[s])
         torch.cuda.synchronize()
         B.sim_get_state(sim.h, want_x=False, want_v=False)     # raises on a kernel error
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        times = time_steps(B, torch, sim, targets, W, K_, flush)
+        times = time_steps(B, torch, sim, targets, first_, K_, flush, cfg_steps)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -226,10 +245,12 @@ def run_ours(args):
         total_ms = float(t.item())
     value = ws * K * iters / (total_ms / 1e3)
 
-    # kernel-by-kernel GPU times of three more steps (after the timed region) for the roofline
+    # kernel-by-kernel GPU times of three more steps (after the timed region) for the roofline; they continue the
+    # run from the state the timed window left
+    after = first + (K - 1) % max(1, cfg_steps - first) + 1
     prof = {}
     for s in range(3):
-        for k, (ms, n) in B.sim_profile_step(sim32.h, targets[W + K + s]).items():
+        for k, (ms, n) in B.sim_profile_step(sim32.h, targets[after + s]).items():
             a, b = prof.get(k, (0.0, 0))
             prof[k] = (a + ms, b + n)
     _, _, stp = B.sim_get_state(sim32.h, want_x=False, want_v=False)
@@ -281,14 +302,19 @@ def run_ours(args):
         sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
         tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
         x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
-        for s in range(W):
+        for s in range(first):
             B.sim_step(sim.h, 1, tg_host[s])
             B.sim_get_state(sim.h, x_out=x_host, want_v=False)
-        t0 = time.perf_counter()
+        span = max(1, cfg_steps - first)
+        saved = B.sim_get_state(sim.h)[:2] if K > span else None
+        te = 0.0
         for s in range(K):
-            B.sim_step(sim.h, 1, tg_host[W + s])
+            if s > 0 and s % span == 0:
+                B.sim_set_state(sim.h, *saved)   # not timed, as in the device-timed window
+            t0 = time.perf_counter()
+            B.sim_step(sim.h, 1, tg_host[first + s % span])
             B.sim_get_state(sim.h, x_out=x_host, want_v=False)
-        te = time.perf_counter() - t0
+            te += time.perf_counter() - t0
         sim.close()
         e2e = {"value": round(K * iters / te, 2), "unit": UNIT, "ms_per_step": round(1e3 * te / K, 4),
                "h2d_bytes_per_step": int(tg_host[0].numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 8)}
@@ -385,6 +411,10 @@ def run_ours(args):
                        "float-float vertex differences, f64 reductions and vertex state",
                        "l2": "flushed between timed steps (256 MiB write, not timed)", "parallelism": "replicas",
                        "graph": "one CUDA graph replay per time step",
+                       "timed_steps": f"steps {first}..{min(first + K, cfg_steps) - 1} of the {cfg_steps}-step run "
+                                      f"(the run's last steps, the most contact candidates)"
+                                      + (f", repeated from step {first} to make {K}" if first + K > cfg_steps else "")
+                                      + f"; steps 0..{first - 1} untimed",
                        "launch": "one kernel per phase" if args.phases else "one persistent cooperative kernel per step"},
             "time_steps_per_s": round(K / (total_ms / 1e3), 2),
             "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
