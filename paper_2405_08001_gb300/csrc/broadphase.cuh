@@ -1,19 +1,23 @@
 // Contact-candidate pass (spatial hash over surface primitives; the paper uses grid spatial hashing for its
 // broad phase, Sec. 6).  Candidates are all surface point-triangle pairs (point not in the triangle) and edge-edge
-// pairs (no shared vertex) whose boxes, inflated by dhat + r, overlap at the positions of the build; pairs of one
-// object closer than the exclusion radius at rest (Sec. 5.1) are dropped.  Since d changes by at most twice the
-// largest vertex displacement, every pair with d < dhat is a candidate until some vertex has moved r/2.
+// pairs (no shared vertex) within dhat + r of each other (box test) at the positions of the build, whose distance
+// there is below (dhat + r)(1 + 1e-3); pairs of one object closer than the exclusion radius at rest (Sec. 5.1) are
+// dropped.  Since d changes by at most twice the largest vertex displacement, every pair with d < dhat is a
+// candidate until some vertex has moved r/2.
 //
-// The five kernels run only when Ctrl::rebuild is set (they return at once otherwise):
+// Three hash tables of H buckets each: triangles [0, H) and edges [H, 2H), each registered in every cell its box
+// inflated by dhat + r covers, and surface points [2H, 3H), each in its own cell.  The five kernels run only when
+// Ctrl::rebuild is set (they return at once otherwise):
 //   bp_boxes  : inflated float boxes (rounded outwards), largest extent -> cell size, zero bucket counts, x_b = x
-//   bp_count  : entries per hash bucket (each primitive covers at most 2 cells per axis); triangles and edges
-//               have separate tables (buckets [0, H) and [H, 2H)) so each query scans one kind only
-//   bp_scan   : exclusive scan of the counts (block-local scans + the last block scans the block sums)
-//   bp_fill   : entries (cell key, a copy of the primitive's box with the primitive and its scene, the primitive's
-//               vertices relative to the cell's corner) in bucket order, and each bucket's global first entry
-//   bp_query  : batches of surface vertices (PT) or edges (EE), one warp each: exact cell-key match, box, order and
-//               scene tests on every entry of the batch's buckets, then the distance at the build positions for
-//               the entries that pass: only pairs with d < (dhat + r)(1 + 1e-3) become candidates
+//   bp_count  : entries per bucket (a box covers at most 2 cells per axis)
+//   bp_scan   : exclusive scan of the counts (block-local scans + the last block scans the block sums), and the
+//               list of work units: every 32 x 32 tile (row chunk <= column chunk) of a non-empty edge bucket, and
+//               every chunk of 32 rows of a non-empty triangle bucket
+//   bp_fill   : entries in bucket order (the two records of the cheap tests, the vertices relative to the cell's
+//               corner) and each bucket's global first entry
+//   bp_query  : one warp per work unit: its 32 rows (triangles, or edges) against its columns (the points of the
+//               same cells, or a chunk of 32 edges of the bucket) staged in shared memory; the pairs that pass the
+//               cheap tests get the distance at the build positions, 32 at a time
 #pragma once
 
 #include <cuda_fp16.h>
@@ -28,6 +32,7 @@ constexpr int BP_SCAN_T = 256;                 // threads per scan block
 constexpr int BP_SCAN_N = 4 * BP_SCAN_T;       // buckets per scan block
 constexpr int BP_B = 256;                      // threads per block, other broad-phase kernels
 constexpr int BP_MAX_CHUNKS = 4096;            // scan chunks of the persistent form (chunk totals in shared memory)
+constexpr int BP_ROWS = 32;                    // rows of a work unit (one per lane)
 constexpr int CELL_BIAS = 1 << 20;
 
 struct BPDev {
@@ -42,20 +47,25 @@ struct BPDev {
     const int *obj;         // [nv]
     float4 *blo, *bhi;      // [nf + ne] inflated boxes, triangles first
     unsigned int *cnt, *off, *boff;
-    unsigned int *goff;     // [2H] global first entry of each bucket (written with the entries, read by queries)
-    unsigned int *ctot;     // persistent form: [2H >> cshift_p] entries per scan chunk
+    unsigned int *goff;     // [3H] global first entry of each bucket (written with the entries, read by queries)
+    unsigned int *ctot;     // persistent form: [3H >> cshift_p] entries per scan chunk
     int cshift_p;           // persistent form: log2 of the buckets per scan chunk
     const int *vscene;      // batching: scene of each vertex (pairs of two scenes are never candidates); or null
-    // entries, one per (primitive, cell of its box), in bucket order: everything the cheap tests of a query read
-    // sits in two 16-byte records, the positions for the distance in the ev rows
-    uint4 *erA;             // (cell key low, cell key high, v0, v1)
-    uint4 *erB;             // (box (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z) as half pairs, w) with the box relative
-                            // to the cell's corner in units of s, rounded outwards; w is v2 for a triangle, and for
-                            // an edge the bits of the cell's offset from its box's lowest cell (x | y << 1 | z << 2)
-    float4 *ev;             // [3][ecap] the primitive's vertices relative to the entry's cell corner; edges use
-                            // the first two rows
-    int *eprim;             // triangle f or edge index (read only where rest-pose exclusions exist)
-    int ecap;               // entry capacity (8 per primitive)
+    // entries in bucket order: everything the cheap tests read sits in two 16-byte records, the positions for the
+    // distance in the ev rows
+    uint4 *erA;             // (cell key low, cell key high, v0, v1); a point: (key, v, v)
+    uint4 *erB;             // (box (lo.x, lo.y), (hi.x, hi.y), (lo.z, hi.z) as half pairs, w): the primitive's box
+                            // inflated by (dhat + r)/2, so that two such boxes meet exactly when the primitives' own
+                            // boxes are within dhat + r, relative to the cell's corner in units of s, rounded
+                            // outwards; w is v2 for a triangle, 0 for a point, and for an edge the bits of the
+                            // cell's offset from its registration box's lowest cell (x | y << 1 | z << 2)
+    float4 *ev;             // [3][ecap] the primitive's vertices relative to the entry's cell corner (edges use two
+                            // rows, points one)
+    int *eprim;             // triangle f, edge index or surface point index (read where rest-pose exclusions exist)
+    int ecap;               // entry capacity (8 per triangle or edge, 1 per point)
+    uint2 *units;           // work units, listed by the scan: (bucket, row chunk | column chunk << 16) for edges,
+                            // (bucket, row chunk | 0xffff << 16) for triangles
+    int ucap;
     int4 *cand;
     int cap;
     const unsigned long long *excl;
@@ -74,11 +84,16 @@ __device__ inline unsigned int prim_bucket(const BPDev &B, int j, int ix, int iy
 {
     return cell_hash(ix, iy, iz, B.H) + (j < B.nf ? 0u : (unsigned int)B.H);
 }
+__device__ inline unsigned int point_bucket(const BPDev &B, int ix, int iy, int iz)
+{
+    return cell_hash(ix, iy, iz, B.H) + 2u * (unsigned int)B.H;
+}
 __device__ inline unsigned long long cell_key(int ix, int iy, int iz)
 {
     return ((unsigned long long)(ix + CELL_BIAS) << 42) | ((unsigned long long)(iy + CELL_BIAS) << 21) |
            (unsigned long long)(iz + CELL_BIAS);
 }
+
 // the hash grid: cell size s and its reciprocal; every cell index of a build comes from floor(q * inv), which is
 // monotone in q, so a point inside a box lies in one of the box's cells
 struct CellGrid { float s, inv; };
@@ -149,9 +164,31 @@ __device__ inline bool box_cells(float4 lo, float4 hi, const CellGrid &g, int l[
            cell_of(hi.y, g, h[1]) && cell_of(hi.z, g, h[2]);
 }
 
-// Writes primitive j's entries, one per cell of its box: the records of the cheap tests and the vertices relative
-// to the entry's cell corner (formed once in double against the box's lowest cell, then shifted by whole cells in
-// float).  slot_of(b) reserves a slot of bucket b; the slots of all cells are reserved before any entry is written.
+// visits the cells covered by [lo, hi]; flags a coordinate out of the grid's range
+template <typename F>
+__device__ inline void for_cells(const BPDev &B, float4 lo, float4 hi, const CellGrid &g, F f)
+{
+    int l[3], h[3];
+    if (!box_cells(lo, hi, g, l, h)) {
+        atomicOr(&B.ctrl->err, ERR_RANGE);
+        return;
+    }
+    for (int i = l[0]; i <= h[0]; ++i)
+        for (int j = l[1]; j <= h[1]; ++j)
+            for (int k = l[2]; k <= h[2]; ++k) f(i, j, k);
+}
+
+// the cell of surface point j (false: out of the grid's range)
+__device__ inline bool point_cell(const BPDev &B, int j, const CellGrid &g, int &v, double4_32a &X, int c[3])
+{
+    v = B.svert[j];
+    X = ldcg4(B.x + v);
+    return cell_of((float)X.x, g, c[0]) && cell_of((float)X.y, g, c[1]) && cell_of((float)X.z, g, c[2]);
+}
+
+// Writes primitive j's entries, one per cell of its registration box: the records of the cheap tests and the
+// vertices relative to the entry's cell corner (formed once in double against the box's lowest cell, then shifted
+// by whole cells in float).  slot_of(b) reserves a slot of bucket b; all slots are reserved before any is written.
 template <typename F> __device__ inline void fill_prim(const BPDev &B, int j, const CellGrid &g, F slot_of)
 {
     const float s = g.s;
@@ -163,8 +200,8 @@ template <typename F> __device__ inline void fill_prim(const BPDev &B, int j, co
     float4 r[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) r[q] = rel_corner(ldcg4(B.x + v[q]), l[0], l[1], l[2], s, v[q]);
-    // the inflated box relative to the lowest cell's corner (a pre-filter only: the 16-bit form rounds outwards)
-    const float inf = (float)B.infl;
+    // the primitive's box inflated by half of dhat + r, relative to the lowest cell's corner
+    const float inf = 0.5f * (float)B.infl;
     const float mnx = fminf(fminf(r[0].x, r[1].x), r[2].x) - inf, mxx = fmaxf(fmaxf(r[0].x, r[1].x), r[2].x) + inf;
     const float mny = fminf(fminf(r[0].y, r[1].y), r[2].y) - inf, mxy = fmaxf(fmaxf(r[0].y, r[1].y), r[2].y) + inf;
     const float mnz = fminf(fminf(r[0].z, r[1].z), r[2].z) - inf, mxz = fmaxf(fmaxf(r[0].z, r[1].z), r[2].z) + inf;
@@ -203,14 +240,71 @@ template <typename F> __device__ inline void fill_prim(const BPDev &B, int j, co
     }
 }
 
+// Writes surface point j's entry in its own cell: (key, v, v), its box of half of dhat + r around it, its position
+// relative to the cell's corner, and j.
+template <typename F> __device__ inline void fill_point(const BPDev &B, int j, const CellGrid &g, F slot_of)
+{
+    int v, c[3];
+    double4_32a X;
+    if (!point_cell(B, j, g, v, X, c)) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
+    const unsigned int slot = slot_of(point_bucket(B, c[0], c[1], c[2]));
+    if (slot >= (unsigned int)B.ecap) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
+    const float4 p = rel_corner(X, c[0], c[1], c[2], g.s, v);
+    const float inf = 0.5f * (float)B.infl;
+    const uint3 bx = qbox(p.x - inf, p.y - inf, p.z - inf, p.x + inf, p.y + inf, p.z + inf, g);
+    const unsigned long long key = cell_key(c[0], c[1], c[2]);
+    B.erA[slot] = make_uint4((unsigned int)key, (unsigned int)(key >> 32), (unsigned int)v, (unsigned int)v);
+    B.erB[slot] = make_uint4(bx.x, bx.y, bx.z, 0u);
+    B.eprim[slot] = j;
+    B.ev[slot] = make_float4(p.x, p.y, p.z, 0.0f);
+}
+
+// Appends the work units of the lanes' buckets (all lanes call, each with up to four buckets (b, n)): an edge
+// bucket (H <= b < 2H) with n entries in t = ceil(n / 32) chunks gives its t (t + 1) / 2 tiles (r <= c), so that no
+// unit is larger than 32 x 32 pairs; a triangle bucket gives its t row chunks (the points of a cell are few).
+__device__ inline void list_units(const BPDev &B, const unsigned int (&b)[4], const unsigned int (&n)[4])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned int H = (unsigned int)B.H;
+    unsigned int u[4], t[4], tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        t[q] = b[q] < 2u * H ? (n[q] + BP_ROWS - 1) / BP_ROWS : 0u;
+        u[q] = b[q] >= H ? t[q] * (t[q] + 1u) / 2u : t[q];
+        tot += u[q];
+    }
+    unsigned int inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += x;
+    }
+    const unsigned int wtot = __shfl_sync(0xffffffffu, inc, 31);
+    if (wtot == 0u) return;
+    unsigned int base = 0;
+    if (lane == 31) base = atomicAdd((unsigned int *)&B.ctrl->n_units, wtot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned int k = base + inc - tot;
+    if (k + tot > (unsigned int)B.ucap) { if (tot) atomicOr(&B.ctrl->err, ERR_RANGE); return; }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (b[q] >= H) {
+            for (unsigned int r = 0; r < t[q]; ++r)
+                for (unsigned int c = r; c < t[q]; ++c) B.units[k++] = make_uint2(b[q], r | c << 16);
+        } else {
+            for (unsigned int r = 0; r < t[q]; ++r) B.units[k++] = make_uint2(b[q], r | 0xffffu << 16);
+        }
+    }
+}
+
 static __global__ void __launch_bounds__(BP_B) bp_boxes(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
-    const int n = max(max(B.nf + B.ne, B.nv), 2 * B.H);
+    const int n = max(max(B.nf + B.ne, B.nv), 3 * B.H);
     const int stride = gridDim.x * blockDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) { B.ctrl->n_cand = 0; B.ctrl->n_rebuilds += 1; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { B.ctrl->n_cand = 0; B.ctrl->n_units = 0; B.ctrl->n_rebuilds += 1; }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        if (j < 2 * B.H) B.cnt[j] = 0u;
+        if (j < 3 * B.H) B.cnt[j] = 0u;
         if (j < B.nv) {
             B.xb[j] = B.x[j];
             if (B.xbh) B.xbh[j] = B.xh[j];
@@ -230,27 +324,20 @@ static __global__ void __launch_bounds__(BP_B) bp_boxes(BPDev B)
     }
 }
 
-// visits the (at most 8) cells covered by [lo, hi]; returns false (and flags) on a coordinate out of range
-template <typename F>
-__device__ inline void for_cells(const BPDev &B, float4 lo, float4 hi, const CellGrid &g, F f)
-{
-    int l[3], h[3];
-    if (!box_cells(lo, hi, g, l, h)) {
-        atomicOr(&B.ctrl->err, ERR_RANGE);
-        return;
-    }
-    for (int i = l[0]; i <= h[0]; ++i)
-        for (int j = l[1]; j <= h[1]; ++j)
-            for (int k = l[2]; k <= h[2]; ++k) f(i, j, k);
-}
-
+// one thread per triangle or edge (j < nf + ne) and per surface point (j < ns)
 static __global__ void __launch_bounds__(BP_B) bp_count(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
     const CellGrid g = grid_of(cell_size(B));
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B.nf + B.ne) return;
-    for_cells(B, B.blo[j], B.bhi[j], g, [&](int i, int jj, int k) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, k)], 1u); });
+    if (j < B.nf + B.ne)
+        for_cells(B, B.blo[j], B.bhi[j], g, [&](int i, int jj, int k) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, k)], 1u); });
+    if (j < B.ns) {
+        int v, c[3];
+        double4_32a X;
+        if (point_cell(B, j, g, v, X, c)) atomicAdd(&B.cnt[point_bucket(B, c[0], c[1], c[2])], 1u);
+        else atomicOr(&B.ctrl->err, ERR_RANGE);
+    }
 }
 
 static __global__ void __launch_bounds__(BP_SCAN_T) bp_scan(BPDev B)
@@ -260,6 +347,11 @@ static __global__ void __launch_bounds__(BP_SCAN_T) bp_scan(BPDev B)
     __shared__ bool last;
     const int base = blockIdx.x * BP_SCAN_N + 4 * threadIdx.x;
     uint4 c = reinterpret_cast<const uint4 *>(B.cnt)[base / 4];
+    {
+        const unsigned int bb[4] = {(unsigned int)base, (unsigned int)base + 1u, (unsigned int)base + 2u, (unsigned int)base + 3u};
+        const unsigned int nn[4] = {c.x, c.y, c.z, c.w};
+        list_units(B, bb, nn);
+    }
     unsigned int tot = c.x + c.y + c.z + c.w;
     // inclusive warp scan of per-thread totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -295,15 +387,17 @@ static __global__ void __launch_bounds__(BP_SCAN_T) bp_scan(BPDev B)
     }
 }
 
+// one thread per triangle or edge (j < nf + ne) and per surface point (j < ns)
 static __global__ void __launch_bounds__(BP_B) bp_fill(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
     const CellGrid g = grid_of(cell_size(B));
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 2 * B.H; b += gridDim.x * blockDim.x)
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < 3 * B.H; b += gridDim.x * blockDim.x)
         B.goff[b] = B.boff[b / BP_SCAN_N] + B.off[b];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B.nf + B.ne) return;
-    fill_prim(B, j, g, [&](unsigned int b) { return B.boff[b / BP_SCAN_N] + B.off[b] + atomicAdd(&B.cnt[b], 1u); });
+    auto slot_of = [&](unsigned int b) { return B.boff[b / BP_SCAN_N] + B.off[b] + atomicAdd(&B.cnt[b], 1u); };
+    if (j < B.nf + B.ne) fill_prim(B, j, g, slot_of);
+    if (j < B.ns) fill_point(B, j, g, slot_of);
 }
 
 __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
@@ -317,42 +411,28 @@ __device__ inline bool is_excluded(const BPDev &B, unsigned long long key)
 }
 
 // ---------------------------------------------------------------------------------------------------- queries
-// A warp takes a batch of queries of one kind (points, or edges).  Its header lists the batch's non-empty
-// (query, cell) segments in shared memory: the bucket's first entry, the segment's first item in the batch, the
-// cell's key and the query's box relative to the cell's corner.  The warp then scans all the segments' entries as
-// one list, 64 per round (two windows of 32, one item per lane each, loaded together); a lane finds its segment
-// from the window's segment starts, gathered into one bit mask by a warp OR.  A round reads the two 16-byte records
-// of each entry and applies the cheap tests: cell key, shared vertex, edge order, the cell rule of edge pairs and
-// the overlap of the half-precision boxes.  The entries that pass queue up in shared memory and get the exact
-// distance 32 at a time, with every lane busy.  Found pairs collect in shared memory and are appended with one
-// atomic per 32.
+// A work unit is (bucket b, row chunk r) of the triangle or edge table.  Its warp holds 32 rows, one per lane: the
+// bucket's entries 32 r .. 32 r + 31.  The columns are staged in shared memory 32 at a time: for a triangle bucket
+// the entries of point bucket b + 2H (the same cells), for an edge bucket the bucket's own entries after the row's.
+// Every lane tests its row against each staged column (two broadcast reads): same cell key, boxes within
+// dhat + r, no shared vertex, and for edge pairs the cell rule below.  The pairs that pass queue up in shared memory
+// and get the exact distance 32 at a time, with every lane busy; found pairs collect in shared memory and are
+// appended with one atomic per 32.
 //
-// Edge pairs: each unordered pair is tested from one side only, the edge whose lower vertex index is smaller (two
-// edges without a shared vertex have different lower vertices), and in one cell only, the cell of the lower corner
-// of the intersection of the two inflated boxes.  The cell index is monotone in the coordinate, so that cell is,
-// per axis, the larger of the two boxes' lowest cells; in a cell the pair shares, it is this cell exactly when on
-// no axis both edges sit in their box's second cell (offset bits of the query's cell AND the entry's = 0).
-constexpr int BPQ_QE = 6;       // edges per batch (an edge's box covers about twice the cells of a point)
-constexpr int BPQ_QP = 8;       // points per batch
-constexpr int BPQ_SEG = 48;     // (query, cell) segments of a batch: 6 edges x 8 cells, or 8 points
-constexpr int BPQ_PEND = 64;    // entries past the cheap tests, awaiting the distance
+// Edge pairs: two edges within dhat + r of each other are registered together in the cells from the larger of
+// their registration boxes' lowest cells (per axis) to the smaller of the highest; the pair is tested in the
+// lowest of those only.  In a cell the pair shares, that is this cell exactly when on no axis both edges sit past
+// their box's lowest cell (offset bits of the two entries AND = 0); the cell index is monotone in the coordinate.
+// A point lies in one cell, and a triangle within dhat + r of it is registered there.
+constexpr int BPQ_PEND = 64;    // pairs past the cheap tests, awaiting the distance
 constexpr int BPQ_OUT = 64;     // found pairs held before an append
+constexpr unsigned int BPQ_PT = 0x80000000u;   // marks a point-triangle pair in the queue
 
 struct BPQWarp {
-    uint4 sa[BPQ_SEG];              // (first entry, first item, query's lower vertex, higher vertex; a point: v, v)
-    unsigned long long sk[BPQ_SEG]; // the cell's key
-    uint4 sb[BPQ_SEG];              // the query's box relative to the cell's corner (as the entries'), w: the cell's
-                                    // offset bits (edge) | query << 8 | cell << 11
-    float4 qa[BPQ_QP];              // point: relative to its cell's corner (w: vertex); edge: first end relative to
-                                    // the corner of its box's lowest cell (w: its vertex)
-    float4 qb[BPQ_QE];              // edge: second end as qa
-    int4 aux[BPQ_QP];               // x: point index j or edge index a; y: scene; z: object; w: edge nx | ny << 2
-    uint2 pend[BPQ_PEND];           // (entry, query | cell << 3)
+    uint4 ca[32], cb[32];           // the staged columns' records
+    uint2 pend[BPQ_PEND];           // (row entry, column entry | BPQ_PT for a point column)
     int4 out[BPQ_OUT];
 };
-
-__device__ inline int bpq_edge_batches(const BPDev &B) { return (B.ne + BPQ_QE - 1) / BPQ_QE; }
-__device__ inline int bpq_batches(const BPDev &B) { return bpq_edge_batches(B) + (B.ns + BPQ_QP - 1) / BPQ_QP; }
 
 __device__ inline unsigned int lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
@@ -381,340 +461,146 @@ __device__ inline void bpq_emit(const BPDev &B, BPQWarp &W, int &n, bool found, 
     if (n > BPQ_OUT - 32) bpq_flush(B, W, n);
 }
 
-// queues the lanes' entries that passed the cheap tests (all lanes call)
-__device__ inline void bpq_push(BPQWarp &W, int &np, bool pass, unsigned int q, unsigned int tc)
-{
-    const unsigned int m = __ballot_sync(0xffffffffu, pass);
-    if (pass) W.pend[np + __popc(m & lanemask_lt())] = make_uint2(q, tc);
-    np += __popc(m);
-}
-
-// drops the first 32 queued entries after their distances (np >= 32 on entry)
-__device__ inline void bpq_shift(BPQWarp &W, int &np)
-{
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    uint2 v = make_uint2(0u, 0u);
-    if (lane < np - 32) v = W.pend[32 + lane];
-    __syncwarp();
-    if (lane < np - 32) W.pend[lane] = v;
-    __syncwarp();
-    np -= 32;
-}
-
 __device__ inline v3<float> f3sub(const float4 &a, const float4 &b) { return mkv(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ inline unsigned long long key_of(const uint4 &A) { return (unsigned long long)A.y << 32 | A.x; }
 
-// Appends the lanes' segments to the batch's list (all lanes call; ln = 0 for none): returns the segment slot of
-// a lane with a segment; nseg and nitem (warp-uniform) grow by the segments and their entries.
-__device__ inline int bpq_add_segments(unsigned int ln, int &nseg, unsigned int &nitem, unsigned int &first)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned int m = __ballot_sync(0xffffffffu, ln > 0u);
-    unsigned int inc = ln;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += n;
-    }
-    first = nitem + inc - ln;
-    const int slot = nseg + __popc(m & lanemask_lt());
-    nseg += __popc(m);
-    nitem += __shfl_sync(0xffffffffu, inc, 31);
-    return slot;
-}
-
-// The segment of item it of the window [base, base + 32) that starts in segment k0 (all lanes call): the lanes
-// bring the starts of segments k0 + 1 .. k0 + 32 (at most 32 start inside a window of 32 items, all segments being
-// non-empty), one warp OR gathers them into a mask of window offsets.  Returns the lane's segment; k_next is the
-// segment of the window's last item.
-__device__ inline int bpq_window(const BPQWarp &W, int nseg, unsigned int base, int k0, int &k_next)
-{
-    const int lane = threadIdx.x & 31;
-    const int k = k0 + 1 + lane;
-    unsigned int bit = 0u;
-    if (k < nseg) {
-        const unsigned int off = W.sa[k].y - base;   // > 0: the segment starts after base
-        if (off < 32u) bit = 1u << off;
-    }
-    const unsigned int M = __reduce_or_sync(0xffffffffu, bit);
-    k_next = k0 + __popc(M);
-    return k0 + __popc(M & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
-}
-
-// offset of cell c among the cells of an edge's box (nx, ny packed in w)
-__device__ inline void cell_offset(int w, int c, int &dx, int &dy, int &dz)
-{
-    const int nx = w & 3, ny = (w >> 2) & 3;
-    dx = nx == 2 ? (c & 1) : 0;
-    const int c1 = nx == 2 ? (c >> 1) : c;
-    dy = ny == 2 ? (c1 & 1) : 0;
-    dz = ny == 2 ? (c1 >> 1) : c1;
-}
-
-// ---- point-triangle
-
-// cheap tests of an entry q of segment k of a point batch: the entry is of the point's cell, the triangle does not
-// hold the point, and its box holds it
-__device__ inline bool pt_filter(const BPDev &B, const BPQWarp &W, bool valid, int k, unsigned int it, unsigned int &q,
-                                 unsigned int &tc)
-{
-    if (!valid) return false;
-    const uint4 S = W.sa[k];
-    q = S.x + (it - S.y);
-    const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
-    const uint4 Q = W.sb[k];
-    tc = Q.w >> 8;
-    return (key_of(A) == W.sk[k]) & (A.z != S.z) & (A.w != S.z) & (E.w != S.z) &
-           qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
-}
-
-// exact tests of the first n queued point-triangle entries (all lanes call)
-__device__ inline void pt_exact(const BPDev &B, BPQWarp &W, int n, float thr, int &nout)
+// exact tests of the first n queued pairs (all lanes call); both entries of a pair are in the same cell, so their
+// positions are relative to the same corner
+__device__ inline void bpq_exact(const BPDev &B, BPQWarp &W, int n, float thr, int &nout)
 {
     const int lane = threadIdx.x & 31;
     bool found = false;
     int4 cnd = make_int4(0, 0, 0, 0);
     if (lane < n) do {
         const uint2 pd = W.pend[lane];
-        const unsigned int q = pd.x;
-        const int t = pd.y & 7;
-        const float4 t0 = __ldcg(B.ev + q), t1 = __ldcg(B.ev + B.ecap + q), t2 = __ldcg(B.ev + 2 * (size_t)B.ecap + q);
-        const uint4 A = __ldcg(B.erA + q);
-        const int a2 = (int)__ldcg(&B.erB[q].w);
-        const float4 qa = W.qa[t];
-        const int4 ax = W.aux[t];
-        const int a0 = (int)A.z, a1 = (int)A.w;
-        if (B.vscene && B.vscene[a0] != ax.y) break;
-        if (B.nexcl) {
-            const int f = __ldcg(B.eprim + q);
-            if (B.tri[f].w == ax.z && is_excluded(B, ((unsigned long long)ax.x << 31) | (unsigned long long)f)) break;
-        }
+        const unsigned int qr = pd.x, qc = pd.y & ~BPQ_PT;
+        const uint4 Ar = __ldcg(B.erA + qr), Ac = __ldcg(B.erA + qc);
+        const float4 r0 = __ldcg(B.ev + qr), r1 = __ldcg(B.ev + B.ecap + qr), c0 = __ldcg(B.ev + qc);
         float cc[4];
         v3<float> tv;
-        const float d = pt_coeffs<float>(f3sub(qa, t0), f3sub(t1, t0), f3sub(t2, t0), cc, tv);
-        if (!(d < thr)) break;
-        found = true;
-        cnd = make_int4(__float_as_int(qa.w), a0, a1, a2);
-    } while (false);
-    bpq_emit(B, W, nout, found, cnd);
-}
-
-// Point-triangle batch b of nb: surface points b, b + nb, b + 2 nb, ... (strided, so that a batch mixes crowded
-// and sparse parts of the surface), each against the triangle table bucket of its cell.
-__device__ inline void bpq_points(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
-{
-    const int lane = threadIdx.x & 31;
-    unsigned int ln = 0u, st = 0u;
-    unsigned long long key = 0ull;
-    uint3 bx = make_uint3(0u, 0u, 0u);
-    int v = 0;
-    if (lane < BPQ_QP && b + lane * nb < B.ns) {
-        const int j = b + lane * nb;
-        v = B.svert[j];
-        const double4_32a X = ldcg4(B.x + v);
-        int ix = 0, iy = 0, iz = 0;
-        if (!cell_of((float)X.x, g, ix) || !cell_of((float)X.y, g, iy) || !cell_of((float)X.z, g, iz)) {
-            atomicOr(&B.ctrl->err, ERR_RANGE);
+        if (pd.y & BPQ_PT) {
+            // row: triangle (Ar.z, Ar.w, v2), column: point Ac.z
+            const float4 r2 = __ldcg(B.ev + 2 * (size_t)B.ecap + qr);
+            const int t2 = (int)__ldcg(&B.erB[qr].w), v = (int)Ac.z;
+            if (B.vscene && B.vscene[v] != B.vscene[(int)Ar.z]) break;
+            if (B.nexcl) {
+                const int f = __ldcg(B.eprim + qr), jp = __ldcg(B.eprim + qc);
+                if (B.tri[f].w == B.obj[v] && is_excluded(B, ((unsigned long long)jp << 31) | (unsigned long long)f)) break;
+            }
+            const float d = pt_coeffs<float>(f3sub(c0, r0), f3sub(r1, r0), f3sub(r2, r0), cc, tv);
+            if (!(d < thr)) break;
+            found = true;
+            cnd = make_int4(v, (int)Ar.z, (int)Ar.w, t2);
         } else {
-            const unsigned int bk = cell_hash(ix, iy, iz, B.H);
-            st = __ldcg(B.goff + bk);
-            const unsigned int len = __ldcg(B.cnt + bk);
-            ln = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
+            // row: edge (Ar.z, Ar.w), column: edge (Ac.z, Ac.w)
+            const float4 c1 = __ldcg(B.ev + B.ecap + qc);
+            if (B.vscene && B.vscene[(int)Ar.z] != B.vscene[(int)Ac.z]) break;
+            if (B.nexcl) {
+                const int ea = __ldcg(B.eprim + qr), eb = __ldcg(B.eprim + qc);
+                const int a = min(ea, eb), b = max(ea, eb);
+                if (B.edge[a].z == B.edge[b].z &&
+                    is_excluded(B, (1ull << 62) | ((unsigned long long)a << 31) | (unsigned long long)b))
+                    break;
+            }
+            const float d = ee_coeffs<float>(f3sub(r0, c0), f3sub(r1, c0), f3sub(c1, c0), cc, tv);
+            if (!(d < thr)) break;
+            found = true;
+            cnd = make_int4(-1 - (int)Ar.z, (int)Ar.w, (int)Ac.z, (int)Ac.w);
         }
-        const float4 p = rel_corner(X, ix, iy, iz, g.s, v);
-        bx = qbox(p.x, p.y, p.z, p.x, p.y, p.z, g);
-        key = cell_key(ix, iy, iz);
-        W.qa[lane] = p;
-        W.aux[lane] = make_int4(j, B.vscene ? B.vscene[v] : 0, B.obj[v], 0);
-    }
-    int nseg = 0;
-    unsigned int total = 0u, first;
-    const int slot = bpq_add_segments(ln, nseg, total, first);
-    if (ln > 0u) {
-        W.sa[slot] = make_uint4(st, first, (unsigned int)v, (unsigned int)v);
-        W.sk[slot] = key;
-        W.sb[slot] = make_uint4(bx.x, bx.y, bx.z, (unsigned int)lane << 8);
-    }
-    __syncwarp();
-    int np = 0, nout = 0, k0 = 0;
-    for (unsigned int base = 0; base < total; base += 64) {
-        int k1, k2;
-        const int ka = bpq_window(W, nseg, base, k0, k1);
-        const int kb = bpq_window(W, nseg, base + 32, k1, k2);
-        k0 = k2;
-        unsigned int q0 = 0, t0 = 0, q1 = 0, t1 = 0;
-        const bool p0 = pt_filter(B, W, base + lane < total, ka, base + lane, q0, t0);
-        const bool p1 = pt_filter(B, W, base + 32 + lane < total, kb, base + 32 + lane, q1, t1);
-        bpq_push(W, np, p0, q0, t0);
-        if (np >= 32) { __syncwarp(); pt_exact(B, W, 32, thr, nout); bpq_shift(W, np); }
-        bpq_push(W, np, p1, q1, t1);
-        if (np >= 32) { __syncwarp(); pt_exact(B, W, 32, thr, nout); bpq_shift(W, np); }
-    }
-    __syncwarp();
-    if (np) pt_exact(B, W, np, thr, nout);
-    bpq_flush(B, W, nout);
-}
-
-// ---- edge-edge
-
-// cheap tests of an entry of segment k of an edge batch: the entry is of its cell, shares no vertex with the query
-// edge and has the larger lower vertex, the cell is the pair's cell, and the boxes meet
-__device__ inline bool ee_filter(const BPDev &B, const BPQWarp &W, bool valid, int k, unsigned int it, unsigned int &q,
-                                 unsigned int &tc)
-{
-    if (!valid) return false;
-    const uint4 S = W.sa[k];
-    q = S.x + (it - S.y);
-    const uint4 A = __ldcg(B.erA + q), E = __ldcg(B.erB + q);
-    const uint4 Q = W.sb[k];
-    tc = Q.w >> 8;
-    const int fmn = min((int)A.z, (int)A.w), fmx = max((int)A.z, (int)A.w);
-    return (key_of(A) == W.sk[k]) & (fmn > (int)S.z) & (fmn != (int)S.w) & (fmx != (int)S.w) & ((Q.w & E.w & 7u) == 0u) &
-           qbox_meet(make_uint3(Q.x, Q.y, Q.z), make_uint3(E.x, E.y, E.z));
-}
-
-// exact tests of the first n queued edge-edge entries (all lanes call)
-__device__ inline void ee_exact(const BPDev &B, BPQWarp &W, int n, float s, float thr, int &nout)
-{
-    const int lane = threadIdx.x & 31;
-    bool found = false;
-    int4 cnd = make_int4(0, 0, 0, 0);
-    if (lane < n) do {
-        const uint2 pd = W.pend[lane];
-        const unsigned int q = pd.x;
-        const int t = pd.y & 7, c = pd.y >> 3;
-        const float4 v0 = __ldcg(B.ev + q), v1 = __ldcg(B.ev + B.ecap + q);
-        const uint4 A = __ldcg(B.erA + q);
-        const float4 pa = W.qa[t], pb = W.qb[t];
-        const int4 ax = W.aux[t];
-        const int f0 = (int)A.z, f1 = (int)A.w;
-        if (B.vscene && B.vscene[f0] != ax.y) break;
-        if (B.nexcl) {
-            const int bi = __ldcg(B.eprim + q);
-            if (B.edge[bi].z == ax.z &&
-                is_excluded(B, (1ull << 62) | ((unsigned long long)ax.x << 31) | (unsigned long long)bi))
-                break;
-        }
-        // the query edge's ends relative to this entry's cell corner
-        int dx, dy, dz;
-        cell_offset(ax.w, c, dx, dy, dz);
-        const float ox = (float)dx * s, oy = (float)dy * s, oz = (float)dz * s;
-        const float4 ra = make_float4(pa.x - ox, pa.y - oy, pa.z - oz, 0.f), rb = make_float4(pb.x - ox, pb.y - oy, pb.z - oz, 0.f);
-        float cc[4];
-        v3<float> tv;
-        const float d = ee_coeffs<float>(f3sub(ra, v0), f3sub(rb, v0), f3sub(v1, v0), cc, tv);
-        if (!(d < thr)) break;
-        found = true;
-        cnd = make_int4(-1 - __float_as_int(pa.w), __float_as_int(pb.w), f0, f1);
     } while (false);
     bpq_emit(B, W, nout, found, cnd);
 }
 
-// Edge-edge batch b of nb: edges b, b + nb, b + 2 nb, ... (strided), each against the edge table buckets of the
-// cells of its own box (at most 2 per axis: a box is no wider than a cell).  The headers take two passes of four
-// edges, eight lanes per edge (one per cell), each lane forming its edge's box and cells itself.
-__device__ inline void bpq_edges(const BPDev &B, int b, int nb, const CellGrid &g, float thr, BPQWarp &W)
+// queues the lanes' passing pairs (all lanes call); runs the exact tests once 32 are queued
+__device__ inline void bpq_push(const BPDev &B, BPQWarp &W, int &np, int &nout, float thr, bool pass, unsigned int qr,
+                                unsigned int qc)
 {
-    const int lane = threadIdx.x & 31, c = lane & 7;
-    int nseg = 0;
-    unsigned int total = 0u;
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        const int t = pass * 4 + (lane >> 3);
-        const int a = b + t * nb;
-        unsigned int st = 0u, ln = 0u;
-        unsigned long long key = 0ull;
-        uint4 sb = make_uint4(0u, 0u, 0u, 0u);
-        int vlo = 0, vhi = 0;
-        if (t < BPQ_QE && a < B.ne) {
-            const int4 e = B.edge[a];
-            vlo = min(e.x, e.y);
-            vhi = max(e.x, e.y);
-            const double4_32a XA = ldcg4(B.x + e.x), XB = ldcg4(B.x + e.y);
-            const float4 lo = make_float4(__double2float_rd(fmin(XA.x, XB.x)), __double2float_rd(fmin(XA.y, XB.y)),
-                                          __double2float_rd(fmin(XA.z, XB.z)), 0.f);
-            const float4 hi = make_float4(__double2float_ru(fmax(XA.x, XB.x)), __double2float_ru(fmax(XA.y, XB.y)),
-                                          __double2float_ru(fmax(XA.z, XB.z)), 0.f);
-            int l[3] = {0, 0, 0}, h[3] = {0, 0, 0};
-            int nx = 1, ny = 1, ncell = 0;
-            if (!box_cells(lo, hi, g, l, h)) {
-                if (c == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
-            } else {
-                nx = h[0] - l[0] + 1;
-                ny = h[1] - l[1] + 1;
-                ncell = nx * ny * (h[2] - l[2] + 1);
-                if (nx > 2 || ny > 2 || ncell > 8) {
-                    if (c == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
-                    ncell = 0; nx = ny = 1;
-                }
-            }
-            const int w = nx | ny << 2;
-            const float4 pa = rel_corner(XA, l[0], l[1], l[2], g.s, e.x), pb = rel_corner(XB, l[0], l[1], l[2], g.s, e.y);
-            if (c < ncell) {
-                int dx, dy, dz;
-                cell_offset(w, c, dx, dy, dz);
-                const unsigned int bk = cell_hash(l[0] + dx, l[1] + dy, l[2] + dz, B.H) + (unsigned int)B.H;
-                st = __ldcg(B.goff + bk);
-                const unsigned int len = __ldcg(B.cnt + bk);
-                ln = st < (unsigned int)B.ecap ? min(len, (unsigned int)B.ecap - st) : 0u;   // a fill overflow is flagged
-                const float ox = (float)dx * g.s, oy = (float)dy * g.s, oz = (float)dz * g.s;
-                const uint3 bx = qbox(fminf(pa.x, pb.x) - ox, fminf(pa.y, pb.y) - oy, fminf(pa.z, pb.z) - oz,
-                                      fmaxf(pa.x, pb.x) - ox, fmaxf(pa.y, pb.y) - oy, fmaxf(pa.z, pb.z) - oz, g);
-                key = cell_key(l[0] + dx, l[1] + dy, l[2] + dz);
-                sb = make_uint4(bx.x, bx.y, bx.z, (unsigned int)(dx | dy << 1 | dz << 2) | (unsigned int)t << 8 | (unsigned int)c << 11);
-            }
-            if (c == 0) {
-                W.qa[t] = pa;
-                W.qb[t] = pb;
-                W.aux[t] = make_int4(a, B.vscene ? B.vscene[e.x] : 0, e.z, w);
-            }
-        }
-        unsigned int first;
-        const int slot = bpq_add_segments(ln, nseg, total, first);
-        if (ln > 0u) {
-            W.sa[slot] = make_uint4(st, first, (unsigned int)vlo, (unsigned int)vhi);
-            W.sk[slot] = key;
-            W.sb[slot] = sb;
-        }
+    const unsigned int m = __ballot_sync(0xffffffffu, pass);
+    if (!m) return;
+    if (pass) W.pend[np + __popc(m & lanemask_lt())] = make_uint2(qr, qc);
+    np += __popc(m);
+    if (np >= 32) {
+        __syncwarp();
+        bpq_exact(B, W, 32, thr, nout);
+        // drop the 32 done
+        const int lane = threadIdx.x & 31;
+        uint2 v = make_uint2(0u, 0u);
+        if (lane < np - 32) v = W.pend[32 + lane];
+        __syncwarp();
+        if (lane < np - 32) W.pend[lane] = v;
+        __syncwarp();
+        np -= 32;
     }
-    __syncwarp();
-    int np = 0, nout = 0, k0 = 0;
-    for (unsigned int base = 0; base < total; base += 64) {
-        int k1, k2;
-        const int ka = bpq_window(W, nseg, base, k0, k1);
-        const int kb = bpq_window(W, nseg, base + 32, k1, k2);
-        k0 = k2;
-        unsigned int q0 = 0, c0 = 0, q1 = 0, c1 = 0;
-        const bool p0 = ee_filter(B, W, base + lane < total, ka, base + lane, q0, c0);
-        const bool p1 = ee_filter(B, W, base + 32 + lane < total, kb, base + 32 + lane, q1, c1);
-        bpq_push(W, np, p0, q0, c0);
-        if (np >= 32) { __syncwarp(); ee_exact(B, W, 32, g.s, thr, nout); bpq_shift(W, np); }
-        bpq_push(W, np, p1, q1, c1);
-        if (np >= 32) { __syncwarp(); ee_exact(B, W, 32, g.s, thr, nout); bpq_shift(W, np); }
-    }
-    __syncwarp();
-    if (np) ee_exact(B, W, np, g.s, thr, nout);
-    bpq_flush(B, W, nout);
 }
 
-// Query batch w: edge batches first (they scan more entries), then point batches.  The candidate threshold adds
-// 4e-6 s to the exact-distance one: positions within a cell or two of a corner keep ~1e-7 s each in float, and
-// the differences and the distance formed from them stay well inside that.
-__device__ inline void bpq_batch(const BPDev &B, int w, const CellGrid &g, BPQWarp &W)
+// Work unit (b, r | c << 16) (all lanes call): rows 32 r .. 32 r + 31 of bucket b; columns 32 c .. 32 c + 31 of the
+// same bucket (edges, the pairs with the row before the column), or all entries of point bucket b + 2H (c = 0xffff).
+__device__ inline void bpq_unit(const BPDev &B, uint2 unit, float thr, BPQWarp &W, int &np, int &nout)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned int b = unit.x, r = unit.y & 0xffffu, cc = unit.y >> 16;
+    const bool ee = b >= (unsigned int)B.H;
+    const unsigned int E = (unsigned int)B.ecap;
+    const unsigned int rst = __ldcg(B.goff + b), rn = min(__ldcg(B.cnt + b), E - min(rst, E));
+    unsigned int cst, c0, c1;
+    if (ee) {
+        cst = rst;
+        c0 = cc * BP_ROWS;
+        c1 = min(c0 + BP_ROWS, rn);
+    } else {
+        const unsigned int pb = b + 2u * (unsigned int)B.H;
+        cst = __ldcg(B.goff + pb);
+        c0 = 0u;
+        c1 = min(__ldcg(B.cnt + pb), E - min(cst, E));
+    }
+    // the lane's row
+    const unsigned int i = r * BP_ROWS + lane;
+    const bool rv = i < rn;
+    uint4 Ar = make_uint4(0u, 0u, 0u, 0u), Br = make_uint4(0u, 0u, 0u, 0u);
+    if (rv) { Ar = __ldcg(B.erA + rst + i); Br = __ldcg(B.erB + rst + i); }
+    const unsigned long long kr = key_of(Ar);
+    const uint3 bxr = make_uint3(Br.x, Br.y, Br.z);
+    const unsigned int qr = rst + i, tag = ee ? 0u : BPQ_PT;
+    for (unsigned int j0 = c0; j0 < c1; j0 += 32u) {
+        __syncwarp();
+        if (j0 + lane < c1) { W.ca[lane] = __ldcg(B.erA + cst + j0 + lane); W.cb[lane] = __ldcg(B.erB + cst + j0 + lane); }
+        __syncwarp();
+        const unsigned int kn = min(32u, c1 - j0);
+        for (unsigned int k = 0; k < kn; ++k) {
+            const uint4 Ac = W.ca[k], Bc = W.cb[k];
+            bool pass = rv & (key_of(Ac) == kr) & qbox_meet(bxr, make_uint3(Bc.x, Bc.y, Bc.z));
+            if (ee) {
+                pass &= (j0 + k > i) & (Ac.z != Ar.z) & (Ac.z != Ar.w) & (Ac.w != Ar.z) & (Ac.w != Ar.w) &
+                        ((Br.w & Bc.w) == 0u);
+            } else {
+                pass &= (Ac.z != Ar.z) & (Ac.z != Ar.w) & (Ac.z != Br.w);
+            }
+            bpq_push(B, W, np, nout, thr, pass, qr, (cst + j0 + k) | tag);
+        }
+    }
+}
+
+// Work units u = first, first + stride, ... (all lanes of the warp call; its batch area in W).  The candidate
+// threshold adds 4e-6 s to the exact-distance one: positions within a cell or two of a corner keep ~1e-7 s each
+// in float, and the differences and the distance formed from them stay well inside that.
+template <typename Next> __device__ inline void bpq_units(const BPDev &B, const CellGrid &g, BPQWarp &W, int first, Next next)
 {
     const float thr = B.thr + 4e-6f * g.s;
-    const int nbe = bpq_edge_batches(B);
-    if (w < nbe) bpq_edges(B, w, nbe, g, thr, W);
-    else bpq_points(B, w - nbe, bpq_batches(B) - nbe, g, thr, W);
+    const int nu = min((int)((volatile Ctrl *)B.ctrl)->n_units, B.ucap);
+    int np = 0, nout = 0;
+    for (int u = first; u < nu; u = next()) bpq_unit(B, __ldcg(B.units + u), thr, W, np, nout);
+    __syncwarp();
+    if (np) bpq_exact(B, W, np, thr, nout);
+    bpq_flush(B, W, nout);
 }
 
 static __global__ void __launch_bounds__(BP_B) bp_query(BPDev B)
 {
     if (!B.ctrl->rebuild) return;
     __shared__ BPQWarp W[BP_B / 32];
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w < bpq_batches(B)) bpq_batch(B, w, grid_of(cell_size(B)), W[threadIdx.x >> 5]);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    int u = w;
+    bpq_units(B, grid_of(cell_size(B)), W[threadIdx.x >> 5], w, [&]() { return u += nw; });
 }
 
 } // namespace pncg

@@ -462,10 +462,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         if (rebuild) {
             br.phase = 1;   // K_BP_BOXES
             // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
-            if (lead) { c->n_cand = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
+            if (lead) { c->n_cand = 0; c->n_units = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
             const int nprim = B.nf + B.ne;
             float ext_max = 0.0f;
-            for (int j = tid; j < 2 * B.H; j += nthr) B.cnt[j] = 0u;
+            for (int j = tid; j < 3 * B.H; j += nthr) B.cnt[j] = 0u;
             for (int j = ov; j < vs.b1; j += PB) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
             const Share ps = share_of(nprim);
             for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) {
@@ -486,18 +486,31 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             br.phase = 2;   // K_BP_COUNT
             for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
                 for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
+            const Share ss = share_of(B.ns);
+            for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) {
+                int v, cc[3];
+                double4_32a X;
+                if (point_cell(B, j, cg, v, X, cc)) atomicAdd(&B.cnt[point_bucket(B, cc[0], cc[1], cc[2])], 1u);
+                else atomicOr(&c->err, ERR_RANGE);
+            }
             grid_barrier(br, c);
             st.mark(2);   // K_BP_COUNT
-            // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane
+            // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane; the work
+            // units of the triangle and edge buckets are listed on the way
             br.phase = 3;   // K_BP_SCAN
             const int cs = B.cshift_p;
-            const int nchunk = (2 * B.H) >> cs;
+            const int nchunk = (3 * B.H) >> cs;
             {
                 const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
                 for (int ch = gw; ch < nchunk; ch += nwarps) {
                     unsigned int run = 0;
                     for (int base = ch << cs; base < (ch + 1) << cs; base += 128) {
                         const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(B.cnt + base) + lane);
+                        {
+                            const unsigned int b4 = (unsigned int)base + 4u * (unsigned int)lane;
+                            const unsigned int bb[4] = {b4, b4 + 1u, b4 + 2u, b4 + 3u}, nn[4] = {v.x, v.y, v.z, v.w};
+                            list_units(B, bb, nn);
+                        }
                         const unsigned int tot = v.x + v.y + v.z + v.w;
                         unsigned int inc = tot;
                         for (int o = 1; o < 32; o <<= 1) {
@@ -546,24 +559,25 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 }
                 __syncthreads();
             }
-            for (int b = tid; b < 2 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
-            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
-                fill_prim(B, j, cg, [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); });
+            for (int b = tid; b < 3 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
+            {
+                auto slot_of = [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); };
+                for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) fill_prim(B, j, cg, slot_of);
+                for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) fill_point(B, j, cg, slot_of);
+            }
             grid_barrier(br, c);
             st.mark(4);   // K_BP_FILL
-            // queries: batches of query primitives, the warp's batch data in sbuf; a warp takes its own batch, then
-            // whichever batches are left (edge batches come first and scan about twice the entries of point batches)
+            // queries: the listed work units, the warp's staging area in sbuf; a warp takes its own unit, then
+            // whichever units are left
             br.phase = 5;   // K_BP_QUERY
             {
                 BPQWarp &W = reinterpret_cast<BPQWarp *>(sbuf)[threadIdx.x >> 5];
-                const int nb = bpq_batches(B), nw = nthr >> 5;
-                int w = tid >> 5;
-                while (w < nb) {
-                    bpq_batch(B, w, cg, W);
+                const int nw = nthr >> 5;
+                bpq_units(B, cg, W, tid >> 5, [&]() {
                     int nx = 0;
                     if ((threadIdx.x & 31) == 0) nx = nw + (int)atomicAdd(&c->ticket[TK_QUERY], 1u);
-                    w = __shfl_sync(0xffffffffu, nx, 0);
-                }
+                    return __shfl_sync(0xffffffffu, nx, 0);
+                });
             }
             grid_barrier(br, c);
             st.mark(5);   // K_BP_QUERY

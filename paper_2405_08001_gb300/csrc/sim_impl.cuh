@@ -488,7 +488,7 @@ public:
             const int par = k & 1;
             mark(K_BP_BOXES); bp_boxes<<<bpb_boxes, BP_B, 0, s>>>(B);
             mark(K_BP_COUNT); bp_count<<<bpb_prims, BP_B, 0, s>>>(B);
-            mark(K_BP_SCAN); bp_scan<<<2 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
+            mark(K_BP_SCAN); bp_scan<<<3 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
             mark(K_BP_FILL); bp_fill<<<bpb_prims, BP_B, 0, s>>>(B);
             mark(K_BP_QUERY); bp_query<<<bpb_query, BP_B, 0, s>>>(B);
             mark(K_GRAD); k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
@@ -780,7 +780,7 @@ private:
     {
         persist = false;
         if (!M.opt.persistent) return SIM_OK;
-        if (((2 * B.H) >> B.cshift_p) > BP_MAX_CHUNKS) return SIM_OK;   // chunk offsets live in shared memory
+        if (((3 * B.H) >> B.cshift_p) > BP_MAX_CHUNKS) return SIM_OK;   // chunk offsets live in shared memory
         int coop = 0;
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (!coop) return SIM_OK;
@@ -906,18 +906,27 @@ private:
         int4 *ed; AL(ed, M.ne); B.edge = ed;
         int *ob; AL(ob, nv); B.obj = ob;
         AL(B.blo, (size_t)(M.nf + M.ne)); AL(B.bhi, (size_t)(M.nf + M.ne));
-        AL(B.cnt, 2 * (size_t)H); AL(B.off, 2 * (size_t)H); AL(B.boff, 2 * (size_t)H / BP_SCAN_N);
-        AL(B.goff, 2 * (size_t)H);
+        // triangle, edge and point tables of H buckets each
+        AL(B.cnt, 3 * (size_t)H); AL(B.off, 3 * (size_t)H); AL(B.boff, 3 * (size_t)H / BP_SCAN_N);
+        AL(B.goff, 3 * (size_t)H);
         {
             // persistent scan chunks: 128 buckets (one warp, four per lane) or more, at most BP_MAX_CHUNKS chunks
             int cs = 7;
-            while (((2 * (size_t)H) >> cs) > (size_t)BP_MAX_CHUNKS) ++cs;
+            while (((3 * (size_t)H) >> cs) > (size_t)BP_MAX_CHUNKS) ++cs;
             B.cshift_p = cs;
-            AL(B.ctot, (2 * (size_t)H) >> cs);
+            AL(B.ctot, (3 * (size_t)H) >> cs);
         }
-        AL(B.erA, 8 * (size_t)(M.nf + M.ne)); AL(B.erB, 8 * (size_t)(M.nf + M.ne));
-        AL(B.ev, 3 * 8 * (size_t)(M.nf + M.ne)); AL(B.eprim, 8 * (size_t)(M.nf + M.ne));
-        B.ecap = 8 * (M.nf + M.ne);
+        {
+            // entries: at most 8 per triangle or edge (a box spans at most 2 cells per axis), 1 per surface point;
+            // work units: an edge bucket of n entries lists t (t + 1) / 2 tiles, t = ceil(n / 32), which is at most
+            // n for n <= 2016; a triangle bucket one per 32 entries
+            const size_t ecap = 8 * (size_t)(M.nf + M.ne) + (size_t)M.ns;
+            AL(B.erA, ecap); AL(B.erB, ecap); AL(B.ev, 3 * ecap); AL(B.eprim, ecap);
+            B.ecap = (int)ecap;
+            const size_t ucap = ecap + std::min(2 * (size_t)H, 8 * (size_t)(M.nf + M.ne)) + 64;
+            AL(B.units, ucap);
+            B.ucap = (int)ucap;
+        }
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
         B.excl = ex; B.nexcl = (int)M.excl.size();
@@ -925,9 +934,9 @@ private:
         B.infl = M.dhat + D.pad_r;
         B.thr = (float)(B.infl * 1.001);
         B.ctrl = c;
-        bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), 2 * H) + BP_B - 1) / BP_B));
-        bpb_prims = std::max(1, (M.nf + M.ne + BP_B - 1) / BP_B);
-        bpb_query = std::max(1, (32 * ((M.ne + BPQ_QE - 1) / BPQ_QE + (M.ns + BPQ_QP - 1) / BPQ_QP) + BP_B - 1) / BP_B);   // one warp per query batch
+        bpb_boxes = std::max(1, std::min(4 * nsm, (std::max(std::max(M.nf + M.ne, nv), 3 * H) + BP_B - 1) / BP_B));
+        bpb_prims = std::max(1, (std::max(M.nf + M.ne, M.ns) + BP_B - 1) / BP_B);
+        bpb_query = 4 * nsm;   // warps stride over the work units the scan listed
         {
             sim_status st = setup_persistent();
             if (st != SIM_OK) return st;
@@ -1099,7 +1108,7 @@ private:
     {
         bp_boxes<<<bpb_boxes, BP_B, 0, s>>>(B);
         bp_count<<<bpb_prims, BP_B, 0, s>>>(B);
-        bp_scan<<<2 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
+        bp_scan<<<3 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
         bp_fill<<<bpb_prims, BP_B, 0, s>>>(B);
         bp_query<<<bpb_query, BP_B, 0, s>>>(B);
     }
