@@ -86,7 +86,8 @@ typedef struct {
     double plane_n[3];    /* plane normal (normalised by the library) */
     double plane_o;       /* plane offset */
     double pad_r;         /* contact-candidate padding r: candidates are rebuilt when some vertex has moved r/2
-                             since the last build; <= 0 = default 4 dhat */
+                             since the last build; <= 0 = default: half the mean surface edge length at rest
+                             minus dhat, clamped to [2, 6] dhat */
     int32_t pnorm;        /* norm of p in alpha_upper = dhat / (2 ||p||): SIM_PNORM_VERTEX2 (largest per-vertex
                              Euclidean length, default) or SIM_PNORM_COMPONENT_INF (largest component) */
     int32_t scatter;      /* gradient / diagonal scatter of the tets: SIM_SCATTER_ATOMIC (default: one global

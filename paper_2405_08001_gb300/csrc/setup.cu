@@ -223,6 +223,14 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         for (int i = 0; i < nv; ++i) if (mesh->fixed[i]) m.fix_slot[i] = m.nfix++;
     // rest-pose exclusion of same-object pairs
     rest_exclusions(std::vector<double>(X, X + 3 * (size_t)nv), m, opt.excl_factor * dhat);
+    {
+        double Ls = 0;
+        for (int e = 0; e < m.ne; ++e) {
+            const double *a = &X[3 * (size_t)m.edge[4 * e]], *b = &X[3 * (size_t)m.edge[4 * e + 1]];
+            Ls += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+        }
+        m.edge_mean = m.ne > 0 ? Ls / m.ne : 0.0;
+    }
     // vertex -> (tet, corner) CSR in tet order
     m.v2c_off.assign(nv + 1, 0);
     for (int q = 0; q < 4 * nt; ++q) m.v2c_off[m.tet[q] + 1]++;

@@ -30,6 +30,7 @@ struct HostMesh {
     std::vector<int> obj;                  // [nv]
     std::vector<int> fix_slot;             // [nv] slot in the targets array or -1
     std::vector<unsigned long long> excl;  // sorted keys (type << 62 | a << 31 | b) of excluded pairs
+    double edge_mean = 0;                  // mean surface edge length at rest
     std::vector<int> v2c_off, v2c;         // vertex -> 4 * tet + corner CSR
     // block scatter: per chunk of SCATTER_CHUNK consecutive tets, its distinct vertices (sorted) and, per tet,
     // the chunk-local index of each corner

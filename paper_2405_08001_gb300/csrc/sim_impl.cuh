@@ -850,7 +850,11 @@ private:
         D.escale = es;
         D.mu = R(M.mu); D.lam = R(M.lam);
         D.h = M.h; D.dhat = M.dhat; D.kappa = M.kappa; D.eps = M.opt.eps;
-        D.pad_r = M.opt.pad_r > 0 ? M.opt.pad_r : 4.0 * M.dhat;
+        // default candidate slack: r = 0.5 L - dhat (L the mean surface edge at rest) within [2, 6] dhat, so that
+        // dhat + r stays below about half an edge and the candidates stay near neighbours; 6 dhat measured the
+        // fewest ms per step on the twisted bar (2 to 8 dhat tried)
+        D.pad_r = M.opt.pad_r > 0 ? M.opt.pad_r
+                                  : M.dhat * std::min(6.0, std::max(2.0, (0.5 * M.edge_mean - M.dhat) / M.dhat));
         for (int a = 0; a < 3; ++a) D.grav[a] = M.opt.gravity[a];
         D.has_plane = M.opt.has_plane;
         if (D.has_plane) {
