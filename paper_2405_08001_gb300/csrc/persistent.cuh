@@ -590,20 +590,26 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             c->rebuild = 0;
             if (ncand > D.cand_cap) flag_error(c, ERR_CAPACITY);
         }
-        if (D.scatter_block) {
-            const int nch = (D.nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
-            for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
-                tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
-        } else {
-            for (int e = ts.b0 + (int)threadIdx.x; e < ts.b1; e += PB) {
-                TetIn<R> in;
-                load_tet_in<R>(D, e, in);
-                tet_grad<R>(D, e, par, in);
-            }
-        }
         {
             const Share cs = share_of(min(ncand, D.cand_cap));
-            for (int ci = cs.b0 + (int)threadIdx.x; ci < cs.b1; ci += PB) pair_grad<R>(D, ci, par);
+            if (D.scatter_block) {
+                const int nch = (D.nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
+                for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+                    tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
+                for (int ci = cs.b0 + (int)threadIdx.x; ci < cs.b1; ci += PB) pair_grad<R>(D, ci, par);
+            } else {
+                // the block's tets and candidates as one list, so that no thread takes more than its share of both
+                const int nts = ts.b1 - ts.b0, nit = nts + (cs.b1 - cs.b0);
+                for (int q = threadIdx.x; q < nit; q += PB) {
+                    if (q < nts) {
+                        TetIn<R> in;
+                        load_tet_in<R>(D, ts.b0 + q, in);
+                        tet_grad<R>(D, ts.b0 + q, par, in);
+                    } else {
+                        pair_grad<R>(D, cs.b0 + q - nts, par);
+                    }
+                }
+            }
         }
         grid_barrier(br, c);
         st.mark(6);   // K_GRAD
@@ -727,17 +733,22 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 }
                 D.pnext[i] = Pn;
             }
-            for (int e = ts.b0 + (int)threadIdx.x; e < ts.b1; e += PB) {
-                const int4 tv = D.tet[e];
-                s3[2].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
-                                         dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
-            }
+            // the block's tets and active pairs as one list, so that no thread takes more than its share of both (the
+            // vertex pass above is short)
             const Share as = share_of(na);
-            for (int kk = as.b0 + (int)threadIdx.x; kk < as.b1; kk += PB) {
-                Active<R> ap;
-                load_active<R>(D, kk, ap);
-                s3[2].add_d(pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
-                                            dir_of<R>(D, ap.v.z, b, nzb), dir_of<R>(D, ap.v.w, b, nzb)));
+            const int nts = ts.b1 - ts.b0, nit = nts + (as.b1 - as.b0);
+            for (int q = threadIdx.x; q < nit; q += PB) {
+                if (q < nts) {
+                    const int e = ts.b0 + q;
+                    const int4 tv = D.tet[e];
+                    s3[2].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
+                                             dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
+                } else {
+                    Active<R> ap;
+                    load_active<R>(D, as.b0 + q - nts, ap);
+                    s3[2].add_d(pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
+                                                dir_of<R>(D, ap.v.z, b, nzb), dir_of<R>(D, ap.v.w, b, nzb)));
+                }
             }
             Fetch f;
             f.pe = &c->err;
