@@ -81,14 +81,18 @@ template <> __device__ inline void atomic_add4<double>(double4_32a *p, double a,
 
 __device__ inline void flag_error(Ctrl *c, uint32_t bits) { atomicOr(&c->err, bits); }
 
-// Writes vertex i's position (and, in the FP32 form, its float-float copy).
-template <typename R> __device__ inline void put_x(const Dev<R> &D, int i, const double4_32a &X)
+// Writes vertex i's position (and, in the FP32 form, its float-float copy, whose head it returns).
+template <typename R> __device__ inline float4 put_x(const Dev<R> &D, int i, const double4_32a &X)
 {
     D.x[i] = X;
     if constexpr (sizeof(R) == 4) {
         const ffl a = ff_split(X.x), b = ff_split(X.y), c = ff_split(X.z);
-        D.xh[i] = make_float4(a.h, b.h, c.h, 0.0f);
+        const float4 h = make_float4(a.h, b.h, c.h, 0.0f);
+        D.xh[i] = h;
         D.xl[i] = make_float4(a.l, b.l, c.l, 0.0f);
+        return h;
+    } else {
+        return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -100,13 +104,34 @@ template <typename R>
 __device__ inline void init_vertex(const Dev<R> &D, int i, const double4_32a &X, const double4_32a &XT, int par)
 {
     const double m = XT.w;
-    const double mm = m > 0.0 ? m : 0.0;
-    double gx, gy, gz;
-    if constexpr (sizeof(R) == 4) {   // the difference in double, the product in float (the value is rounded anyway)
-        gx = float(mm) * float(X.x - XT.x); gy = float(mm) * float(X.y - XT.y); gz = float(mm) * float(X.z - XT.z);
-    } else {
-        gx = mm * (X.x - XT.x); gy = mm * (X.y - XT.y); gz = mm * (X.z - XT.z);
+    if constexpr (sizeof(R) == 4) {
+        // the differences and the half-space distance and barrier in double, the rest in float (the values are
+        // stored as floats): this runs for every vertex every iteration, and the FP64 pipes are scarce
+        const float mm = m > 0.0 ? (float)m : 0.0f;
+        float gx = mm * (float)(X.x - XT.x), gy = mm * (float)(X.y - XT.y), gz = mm * (float)(X.z - XT.z);
+        float dx = mm, dy = mm, dz = mm, curv = 0.0f;
+        if (D.has_plane) {
+            const double d = D.pn[0] * X.x + D.pn[1] * X.y + D.pn[2] * X.z - D.po;
+            if (d < D.dhat) {
+                if (!(d > 0.0)) {
+                    flag_error(D.ctrl, ERR_PENETRATION);
+                } else {
+                    double b1, b2;
+                    barrier_d12<double>(d, D.dhat, b1, b2);
+                    const float k1 = (float)(D.kappa * b1), k2 = (float)(D.kappa * b2);
+                    const float n0 = (float)D.pn[0], n1 = (float)D.pn[1], n2 = (float)D.pn[2];
+                    gx += k1 * n0; gy += k1 * n1; gz += k1 * n2;
+                    dx += k2 * n0 * n0; dy += k2 * n1 * n1; dz += k2 * n2 * n2;
+                    curv = k2;
+                }
+            }
+        }
+        D.g[par][i] = mk4<R>(gx, gy, gz, curv);
+        D.dg[par][i] = mk4<R>(dx, dy, dz, (float)m);
+        return;
     }
+    const double mm = m > 0.0 ? m : 0.0;
+    double gx = mm * (X.x - XT.x), gy = mm * (X.y - XT.y), gz = mm * (X.z - XT.z);
     double dx = mm, dy = mm, dz = mm, curv = 0.0;
     if (D.has_plane) {
         double d = D.pn[0] * X.x + D.pn[1] * X.y + D.pn[2] * X.z - D.po;

@@ -827,10 +827,15 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 if (i == ov) { X = uX; P = uP; XT = uXT; XB = uXB; }
                 else { X = ldcg4(D.x + i); P = ldcg4(D.pnext + i); XT = ldcg4(D.xtil + i); XB = disp_ref<R>(D, i); }
                 X.x += alpha * double(P.x); X.y += alpha * double(P.y); X.z += alpha * double(P.z);
-                put_x<R>(D, i, X);
+                const float4 xh = put_x<R>(D, i, X);
                 D.p[i] = P;
                 init_vertex<R>(D, i, X, XT, par ^ 1);
-                md = fmax(md, disp2_from<R>(X, XB));
+                if constexpr (sizeof(R) == 4) {   // the float head just written, as disp2 forms it
+                    const float dx = xh.x - XB.x, dy = xh.y - XB.y, dz = xh.z - XB.z;
+                    md = fmax(md, dx * dx + dy * dy + dz * dz);
+                } else {
+                    md = fmax(md, disp2_from<R>(X, XB));
+                }
             }
             if (lead) c->n_active = 0;
             const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
