@@ -14,6 +14,13 @@ __host__ __device__ inline float gsqrt(float a) { return sqrtf(a); }
 __host__ __device__ inline double gsqrt(double a) { return ::sqrt(a); }
 
 template <typename R> __host__ __device__ inline v3<R> mkv(R a, R b, R c) { v3<R> r; r.x = a; r.y = b; r.z = c; return r; }
+
+// Relative size of the 2x2 normal equations' determinant below which the interior solution is not trusted (nearly
+// parallel edges, a sliver triangle) and the clamped cases decide.  It must exceed the determinant's rounding error,
+// a few units of the number type's precision relative to a cq: 1e-12 for double and the float-float type (2^-44),
+// 1e-5 for float (2^-24), whose interior solution of two parallel edges can otherwise come out of cancellation noise.
+template <typename R> struct GeomEps { static constexpr double par = 1e-12; };
+template <> struct GeomEps<float> { static constexpr double par = 1e-5; };
 template <typename R> __host__ __device__ inline v3<R> operator-(v3<R> a, v3<R> b) { return mkv(a.x - b.x, a.y - b.y, a.z - b.z); }
 template <typename R> __host__ __device__ inline v3<R> operator+(v3<R> a, v3<R> b) { return mkv(a.x + b.x, a.y + b.y, a.z + b.z); }
 template <typename R> __host__ __device__ inline v3<R> operator*(R s, v3<R> a) { return mkv(s * a.x, s * a.y, s * a.z); }
@@ -44,7 +51,7 @@ template <typename R> __host__ __device__ inline R pt_coeffs(v3<R> r, v3<R> e1, 
 {
     R a = dot(e1, e1), b = dot(e1, e2), cq = dot(e2, e2);
     R det = a * cq - b * b;
-    if (det > R(1e-12) * a * cq) {
+    if (det > R(GeomEps<R>::par) * a * cq) {
         R p = dot(r, e1), q = dot(r, e2);
         R be = (cq * p - b * q) / det, ga = (a * q - b * p) / det;
         if (be >= R(0) && ga >= R(0) && be + ga <= R(1)) {
@@ -79,7 +86,7 @@ template <typename R> __host__ __device__ inline R ee_coeffs(v3<R> r, v3<R> a1, 
     R a = dot(e0, e0), b = dot(e0, e1), cq = dot(e1, e1), dd = dot(e0, r), ee = dot(e1, r);
     R det = a * cq - b * b;
     bool done = false;
-    if (det > R(1e-12) * a * cq) {
+    if (det > R(GeomEps<R>::par) * a * cq) {
         R s = (b * ee - cq * dd) / det, u = (a * ee - b * dd) / det;
         if (s >= R(0) && s <= R(1) && u >= R(0) && u <= R(1)) {
             c[0] = R(1) - s; c[1] = s; c[2] = -(R(1) - u); c[3] = -u;
