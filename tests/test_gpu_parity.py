@@ -42,9 +42,22 @@ def lowered_cube(cells=(7, 5, 9)):
     return sc
 
 
+def stacked_blocks(n=3, side=0.03, dhat=2e-3, gap=0.5):
+    """Two axis-aligned blocks, the upper one gap*dhat above the lower one and shifted by a third and a quarter of
+    a cell: face-to-face proximity, so that many active edge pairs are (nearly) parallel."""
+    h = side / n
+    Xa, Ta = S.kuhn_grid(n, n, n, size=(side, side, side), origin=(0.0, 0.0, 0.004))
+    Xb, Tb = S.kuhn_grid(n, n, n, size=(side, side, side), origin=(h / 3, h / 4, 0.004 + side + gap * dhat))
+    X = np.concatenate([Xa, Xb])
+    T = np.concatenate([Ta, Tb + Xa.shape[0]]).astype(np.int32)
+    return S.Scene(name="stacked_blocks", rest_x=X, tets=T, x0=X.copy(), v0=np.zeros_like(X), youngs=1e5,
+                   poisson=0.4, density=1000.0, dt=1.0 / 60.0, dhat=dhat, kappa=1e4, gravity=(0.0, 0.0, -9.8),
+                   plane=((0.0, 0.0, 1.0), 0.0), iters=20, steps=3)
+
+
 def grad_cases():
     return [("ragged_plane", lowered_cube), ("blocks0", lambda: S.two_blocks(0)), ("blocks1", lambda: S.two_blocks(1)),
-            ("blocks3", lambda: S.two_blocks(3))]
+            ("blocks3", lambda: S.two_blocks(3)), ("blocks_stacked", stacked_blocks)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
