@@ -261,38 +261,55 @@ template <typename F> __device__ inline void fill_point(const BPDev &B, int j, c
 
 // Appends the work units of the lanes' buckets (all lanes call, each with up to four buckets (b, n)): an edge
 // bucket (H <= b < 2H) with n entries in t = ceil(n / 32) chunks gives its t (t + 1) / 2 tiles (r <= c), so that no
-// unit is larger than 32 x 32 pairs; a triangle bucket gives its t row chunks (the points of a cell are few).
-__device__ inline void list_units(const BPDev &B, const unsigned int (&b)[4], const unsigned int (&n)[4])
+// unit is larger than 32 x 32 pairs; a triangle bucket gives its t row chunks (the points of a cell are few).  The
+// tiles of edge buckets of 64 or more entries (full tiles, the densest cells) are listed from the front of the list
+// and taken first by the query; the rest from the end.
+__device__ inline unsigned int warp_excl(unsigned int v, unsigned int &total)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned int H = (unsigned int)B.H;
-    unsigned int u[4], t[4], tot = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        t[q] = b[q] < 2u * H ? (n[q] + BP_ROWS - 1) / BP_ROWS : 0u;
-        u[q] = b[q] >= H ? t[q] * (t[q] + 1u) / 2u : t[q];
-        tot += u[q];
-    }
-    unsigned int inc = tot;
+    unsigned int inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned int x = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += x;
     }
-    const unsigned int wtot = __shfl_sync(0xffffffffu, inc, 31);
-    if (wtot == 0u) return;
-    unsigned int base = 0;
-    if (lane == 31) base = atomicAdd((unsigned int *)&B.ctrl->n_units, wtot);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    unsigned int k = base + inc - tot;
-    if (k + tot > (unsigned int)B.ucap) { if (tot) atomicOr(&B.ctrl->err, ERR_RANGE); return; }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+__device__ inline void list_units(const BPDev &B, const unsigned int (&b)[4], const unsigned int (&n)[4])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned int H = (unsigned int)B.H;
+    unsigned int t[4], th = 0, tl = 0;
+    bool heavy[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        t[q] = b[q] < 2u * H ? (n[q] + BP_ROWS - 1) / BP_ROWS : 0u;
+        const unsigned int u = b[q] >= H ? t[q] * (t[q] + 1u) / 2u : t[q];
+        heavy[q] = b[q] >= H && t[q] >= 2u;
+        if (heavy[q]) th += u; else tl += u;
+    }
+    unsigned int wh, wl;
+    const unsigned int eh = warp_excl(th, wh), el = warp_excl(tl, wl);
+    if (wh + wl == 0u) return;
+    unsigned int bh = 0, bl = 0;
+    if (lane == 31) {
+        if (wh) bh = atomicAdd((unsigned int *)&B.ctrl->n_units_h, wh);
+        if (wl) bl = atomicAdd((unsigned int *)&B.ctrl->n_units, wl);
+    }
+    unsigned int kh = __shfl_sync(0xffffffffu, bh, 31) + eh, kl = __shfl_sync(0xffffffffu, bl, 31) + el;
+    const unsigned int cap = (unsigned int)B.ucap;
+    if (kh + th > cap || kl + tl > cap) { atomicOr(&B.ctrl->err, ERR_RANGE); return; }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (b[q] >= H) {
             for (unsigned int r = 0; r < t[q]; ++r)
-                for (unsigned int c = r; c < t[q]; ++c) B.units[k++] = make_uint2(b[q], r | c << 16);
+                for (unsigned int c = r; c < t[q]; ++c) {
+                    const uint2 unit = make_uint2(b[q], r | c << 16);
+                    if (heavy[q]) B.units[kh++] = unit; else B.units[cap - 1u - kl++] = unit;
+                }
         } else {
-            for (unsigned int r = 0; r < t[q]; ++r) B.units[k++] = make_uint2(b[q], r | 0xffffu << 16);
+            for (unsigned int r = 0; r < t[q]; ++r) B.units[cap - 1u - kl++] = make_uint2(b[q], r | 0xffffu << 16);
         }
     }
 }
@@ -302,7 +319,9 @@ static __global__ void __launch_bounds__(BP_B) bp_boxes(BPDev B)
     if (!B.ctrl->rebuild) return;
     const int n = max(max(B.nf + B.ne, B.nv), 3 * B.H);
     const int stride = gridDim.x * blockDim.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) { B.ctrl->n_cand = 0; B.ctrl->n_units = 0; B.ctrl->n_rebuilds += 1; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B.ctrl->n_cand = 0; B.ctrl->n_units = 0; B.ctrl->n_units_h = 0; B.ctrl->n_rebuilds += 1;
+    }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         if (j < 3 * B.H) B.cnt[j] = 0u;
         if (j < B.nv) {
@@ -586,9 +605,15 @@ __device__ inline void bpq_unit(const BPDev &B, uint2 unit, float thr, BPQWarp &
 template <typename Next> __device__ inline void bpq_units(const BPDev &B, const CellGrid &g, BPQWarp &W, int first, Next next)
 {
     const float thr = B.thr + 4e-6f * g.s;
-    const int nu = min((int)((volatile Ctrl *)B.ctrl)->n_units, B.ucap);
+    const int nh = ((volatile Ctrl *)B.ctrl)->n_units_h, nl = ((volatile Ctrl *)B.ctrl)->n_units;
+    const int nu = nh + nl;
+    if (nu > B.ucap) {   // the two ends of the list met: the build cannot be trusted
+        if ((threadIdx.x & 31) == 0) atomicOr(&B.ctrl->err, ERR_RANGE);
+        return;
+    }
     int np = 0, nout = 0;
-    for (int u = first; u < nu; u = next()) bpq_unit(B, __ldcg(B.units + u), thr, W, np, nout);
+    for (int u = first; u < nu; u = next())
+        bpq_unit(B, __ldcg(B.units + (u < nh ? u : B.ucap - 1 - (u - nh))), thr, W, np, nout);
     __syncwarp();
     if (np) bpq_exact(B, W, np, thr, nout);
     bpq_flush(B, W, nout);

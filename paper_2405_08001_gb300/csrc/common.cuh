@@ -36,7 +36,9 @@ struct Ctrl {
     uint32_t err;          // sticky error bits
     int32_t err_step;      // time step index of the first error (-1 = none)
     int32_t n_cand;        // candidates emitted by the last build (may exceed capacity)
-    int32_t n_units;       // work units listed by the last build's scan (may exceed capacity)
+    int32_t n_units;       // work units listed by the last build's scan, from the end of the list (may exceed
+                           // capacity)
+    int32_t n_units_h;     // the heavy ones (tiles of buckets of 64+ entries), from the front
     int32_t n_active;      // active pairs appended by the current gradient pass
     int32_t n_active_last; // active pairs of the last completed iteration
     int32_t rebuild;       // 1 = candidate build needed before the next gradient pass

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         if (rebuild) {
             br.phase = 1;   // K_BP_BOXES
             // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
-            if (lead) { c->n_cand = 0; c->n_units = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
+            if (lead) { c->n_cand = 0; c->n_units = 0; c->n_units_h = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
             const int nprim = B.nf + B.ne;
             float ext_max = 0.0f;
             for (int j = tid; j < 3 * B.H; j += nthr) B.cnt[j] = 0u;
