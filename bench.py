@@ -296,6 +296,52 @@ def run_ours(args):
     ms64 = sum(t64) / K64
     v64 = K64 * iters / (sum(t64) / 1e3)
 
+    # IterMax = 150 (the iteration cap of the twist scenes in Sec. 5), on steps 80..89 of the run: with 75 or more
+    # iterations per step the twisted bar ends between steps 100 and 115 with an inverted tet next to a cap (the
+    # cap layer is compressed to under 1 % of its rest volume by then, and moving the caps to their next targets
+    # at the start of a step flips it before the first iteration; the FP64 oracle does the same)
+    K150, f150 = min(K, 10), 80
+    sim150 = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
+                   persistent=0 if args.phases else 1, iters=150)
+    try:
+        for s in range(f150):
+            B.sim_step_async(sim150.h, 1, targets[s])
+        torch.cuda.synchronize()
+        B.sim_get_state(sim150.h, want_x=False, want_v=False)
+        t150 = time_steps(B, torch, sim150, targets, f150, K150, flush, f150 + K150)
+        _, _, st150 = B.sim_get_state(sim150.h, want_x=False, want_v=False)
+        ms150 = sum(t150) / K150
+        iter150 = {"iters_per_step": 150, "value": round(K150 * 150 / (sum(t150) / 1e3), 2), "unit": UNIT,
+                   "ms_per_step": round(ms150, 4), "time_steps_per_s": round(1e3 / ms150, 2), "steps": K150,
+                   "timed_steps": f"{f150}..{f150 + K150 - 1}", "dE_last_over_dE0_last_step":
+                   st150["dE_last"] / st150["dE0"] if st150["dE0"] else None}
+    except B.SimError as e:
+        iter150 = {"iters_per_step": 150, "error": str(e)}
+    sim150.close()
+
+    # PR+ against DK (Sec. 4.1): the whole run step by step, untimed; per step the last iteration's energy
+    # decrease relative to the first (the convergence measure of the stopping rule in Sec. 4.4)
+    conv = {}
+    for name, beta in (("pr_plus", B.SIM_BETA_PR_PLUS), ("dk", B.SIM_BETA_DK)):
+        simc = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
+                     persistent=0 if args.phases else 1, beta=beta)
+        ratios, err = [], None
+        for s in range(cfg_steps):
+            try:
+                B.sim_step_async(simc.h, 1, targets[s])
+                _, _, stc = B.sim_get_state(simc.h, want_x=False, want_v=False)
+            except B.SimError as e:
+                err = str(e)
+                break
+            if stc["dE0"] > 0:
+                ratios.append(max(stc["dE_last"], 1e-300) / stc["dE0"])
+        simc.close()
+        lr = np.log10(np.asarray(ratios))
+        conv[name] = {"median_dE_last_over_dE0": float(10 ** np.median(lr)),
+                      "geomean_dE_last_over_dE0": float(10 ** lr.mean()),
+                      "worst_dE_last_over_dE0": float(10 ** lr.max()), "steps": len(ratios),
+                      **({"error": err} if err else {})}
+
     # end to end through the C ABI with host buffers: pinned targets in, positions out, every step
     e2e = None
     if True:
@@ -421,6 +467,8 @@ def run_ours(args):
                            "launch": "persistent" if st64["launch_form"] == 1 else "one kernel per phase",
                            "launch_choice": "autotuned (options.persistent = 2)" if not args.phases else "per phase",
                            "speedup_fp32_over_fp64": round(value / ws / v64, 3)},
+            "iter_max_150": iter150,
+            "beta_convergence": {"note": "whole 120-step run, FP32-mixed, 50 iterations per step, untimed", **conv},
             "roofline": {"bound": "hbm", "kernel": dom, "largest_phase": dom_all, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes_per_launch": int(abytes),
