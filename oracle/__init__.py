@@ -79,6 +79,7 @@ def _load():
             "or_pmax": (D, [I32, P, I32]),
             "or_ncg_alpha": (None, [D, D, D, D, P]),
             "or_iteration": (C.c_int, [P, P, P, P, P, P, P]),
+            "or_iteration_split": (C.c_int, [P, I32, P, P, P, P, P, P, P, P]),
             "or_step": (C.c_int, [P, P, P, P, I32, D, P, P]),
             "or_predict": (None, [P, P, P, P, P]),
             "or_intersections": (I32, [P, P]),
@@ -262,6 +263,49 @@ class Oracle:
         s.k, s.dE0 = int(k), float(dE0)
         _check(_load().or_iteration(self._m, _ptr(x), _ptr(xt), _ptr(g), _ptr(P), _ptr(p), C.byref(s)))
         return {f: getattr(s, f) for f, _ in _Scalars._fields_}
+
+    def iteration_split(self, x, xtilde, g, P, p, off, state, moving=None):
+        """One PNCG iteration with per-object splitting (Sec. 5.2) in place on x, g, P, p.  off: object boundaries
+        [nobj + 1] (object o = vertices off[o] .. off[o+1]-1); state: a list of nobj dicts carrying each object's
+        "k" and "dE0" between calls (start with [{}] * nobj, or None entries); moving: nobj flags (None = all move).
+        Returns the per-object scalars (and updates state)."""
+        for a in (x, g, P, p):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        off = np.ascontiguousarray(off, dtype=np.int32)
+        nobj = len(off) - 1
+        ss = (_Scalars * nobj)()
+        for o in range(nobj):
+            st = state[o] or {}
+            ss[o].k, ss[o].dE0 = int(st.get("k", 0)), float(st.get("dE0", 0.0))
+        mv = None if moving is None else np.ascontiguousarray(moving, dtype=np.int32)
+        _check(_load().or_iteration_split(self._m, nobj, _ptr(off), _ptr(mv), _ptr(x), _ptr(_f64(xtilde)), _ptr(g),
+                                          _ptr(P), _ptr(p), ss))
+        out = [{f: getattr(ss[o], f) for f, _ in _Scalars._fields_} for o in range(nobj)]
+        for o in range(nobj):
+            state[o] = {"k": out[o]["k"], "dE0": out[o]["dE0"]}
+        return out
+
+    def step_split(self, x, v, off, targets=None, iters=50, eps=0.0):
+        """One time step with per-object splitting, in place on x and v: the prediction and kinematic targets of
+        `step`, then iterations of `iteration_split`; under the eps rule (Sec. 4.4) an object stops moving once its
+        Delta E < eps Delta E_0 and the step ends when every object has stopped.  Returns the iterations done."""
+        xt = self.predict(x, v, targets)
+        x0 = x.copy()
+        if targets is not None and self.fixed is not None:
+            x[self.fixed.astype(bool)] = _f64(targets).reshape(-1, 3)
+        g, P, p = np.zeros_like(x), np.zeros_like(x), np.zeros_like(x)
+        nobj = len(off) - 1
+        state, moving = [None] * nobj, np.ones(nobj, dtype=np.int32)
+        k = 0
+        while k < iters and moving.any():
+            sc = self.iteration_split(x, xt, g, P, p, off, state, moving)
+            k += 1
+            if eps > 0.0:
+                for o in range(nobj):
+                    if moving[o] and sc[o]["dE"] < eps * sc[o]["dE0"]:
+                        moving[o] = 0
+        v[:] = (x - x0) / self.dt
+        return k
 
     def step(self, x, v, targets=None, iters=50, eps=0.0):
         """One time step in place on x and v; returns (iterations done, trace [iters, 8])."""

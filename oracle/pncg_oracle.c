@@ -18,6 +18,7 @@
  *   - preconditioned Polak-Ribiere+ (default) or Dai-Kou beta                                    (Sec. 4.1-4.2)
  *   - the single-pass step alpha = min(dhat / (2 ||p||_inf), -g^T p / p^T H p)                   (Sec. 4.3, Eqs. upper, alpha)
  *   - the rest-pose exclusion of self-collision pairs closer than 1.5 dhat                        (Sec. 5.1)
+ *   - per-object splitting: each object its own beta, direction and step                         (Sec. 5.2)
  *
  * Readings where the paper is silent (each one is also taken by the CUDA library):
  *   - Psi(x) = sum_e V_e Psi_NH(F_e), F = Ds Dm^-1 with D = [x1-x0, x2-x0, x3-x0]; mu = E/(2(1+nu)),
@@ -977,6 +978,26 @@ void or_ncg_alpha(double gp, double pHp, double pmax, double dhat, double *out)
     out[4] = capped;
 }
 
+/* Jacobi preconditioner P = 1 / max(diag, m_v) (Sec. 4.2); kinematic vertices get g = 0 and P = 0 */
+static void jacobi(const or_model *m, double *g1, const double *d1, double *P1)
+{
+    for (int32_t i = 0; i < m->p.nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            size_t q = 3 * (size_t)i + a;
+            if (m->fixed[i]) { g1[q] = 0.0; P1[q] = 0.0; continue; }
+            P1[q] = 1.0 / (d1[q] > m->mass[i] ? d1[q] : m->mass[i]);
+        }
+}
+
+/* vertices within dhat of the plane (reported, like the pair count) */
+static int32_t count_plane(const or_model *m, const double *x)
+{
+    int32_t nplane = 0;
+    if (m->p.has_plane)
+        for (int32_t i = 0; i < m->p.nv; ++i) if (dot3(m->plane_n, x + 3 * (size_t)i) - m->p.plane_o < m->p.dhat) ++nplane;
+    return nplane;
+}
+
 /*
  * One iteration of Algorithm 1 at x = x_k.  In: g = g_k, P = P_k, p = p_k (ignored at k = 0).
  * Out: x = x_{k+1}, g = g_{k+1} (at x_k, kinematic entries zero), P = P_{k+1}, p = p_{k+1}; scalars in *s.
@@ -990,15 +1011,8 @@ int or_iteration(const or_model *m, double *x, const double *xtilde, double *g, 
     int32_t nact = 0;
     int st = or_grad_diag(m, x, xtilde, g1, d1, &nact);   /* C <- ComputeConstraintSet; g, diag */
     if (st) { free(g1); free(d1); free(P1); return st; }
-    for (int32_t i = 0; i < nv; ++i)
-        for (int a = 0; a < 3; ++a) {
-            size_t q = 3 * (size_t)i + a;
-            if (m->fixed[i]) { g1[q] = 0.0; P1[q] = 0.0; continue; }
-            P1[q] = 1.0 / (d1[q] > m->mass[i] ? d1[q] : m->mass[i]);
-        }
-    int32_t nplane = 0;
-    if (m->p.has_plane)
-        for (int32_t i = 0; i < nv; ++i) if (dot3(m->plane_n, x + 3 * (size_t)i) - m->p.plane_o < m->p.dhat) ++nplane;
+    jacobi(m, g1, d1, P1);
+    int32_t nplane = count_plane(m, x);
     double beta, gp;
     int32_t rs;
     or_ncg_direction((int32_t)n, g1, P1, g, P, p, s->k, m->p.beta_rule, &beta, &gp, &rs);
@@ -1018,6 +1032,63 @@ int or_iteration(const or_model *m, double *x, const double *xtilde, double *g, 
     if (s->k == 0) s->dE0 = s->dE;
     s->k += 1;
     return OR_OK;
+}
+
+/*
+ * One iteration with per-object splitting (Sec. 5.2): the vertices form nobj objects, object o the contiguous range
+ * off[o] .. off[o+1]-1.  Gradient and preconditioner are those of the whole scene (pairs between two objects
+ * included).  Each object then takes its own beta and direction over its own entries (Sec. 4.1-4.2), its own max
+ * |p_v|, and its own step along p_o, which is p with every other object's entries zero: alpha_o = min(dhat /
+ * (2 max |p_v|), -g^T p_o / p_o^T H p_o) (Sec. 4.3), i.e. the step of the quadratic model of E along p_o with the
+ * other objects held still.  All p_o^T H p_o are taken at x_k before any object moves.  moving (nullable): objects
+ * with moving[o] = 0 (converged under the eps rule) keep their direction but take no step.  s: nobj scalars, each
+ * with its own k and dE0.
+ */
+int or_iteration_split(const or_model *m, int32_t nobj, const int32_t *off, const int32_t *moving, double *x,
+                       const double *xtilde, double *g, double *P, double *p, or_ncg_scalars *s)
+{
+    int32_t nv = m->p.nv;
+    size_t n = 3 * (size_t)nv;
+    if (nobj < 1 || off[0] != 0 || off[nobj] != nv) { set_err("object ranges must cover the vertices"); return OR_ERR_ARG; }
+    for (int32_t o = 0; o < nobj; ++o)
+        if (off[o + 1] < off[o]) { set_err("object ranges must be non-decreasing"); return OR_ERR_ARG; }
+    double *g1 = malloc(sizeof(double) * n), *d1 = malloc(sizeof(double) * n), *P1 = malloc(sizeof(double) * n);
+    double *po = calloc(n, sizeof(double)), *al = malloc(sizeof(double) * 5 * (size_t)nobj);
+    if (!g1 || !d1 || !P1 || !po || !al) { free(g1); free(d1); free(P1); free(po); free(al); return OR_ERR_OOM; }
+    int32_t nact = 0;
+    int st = or_grad_diag(m, x, xtilde, g1, d1, &nact);
+    if (st) goto done;
+    jacobi(m, g1, d1, P1);
+    int32_t nplane = count_plane(m, x);
+    for (int32_t o = 0; o < nobj; ++o) {
+        size_t q0 = 3 * (size_t)off[o];
+        int32_t no = 3 * (off[o + 1] - off[o]);
+        or_ncg_direction(no, g1 + q0, P1 + q0, g + q0, P + q0, p + q0, s[o].k, m->p.beta_rule, &s[o].beta, &s[o].gp,
+                         &s[o].restarted);
+        s[o].pmax = or_pmax(off[o + 1] - off[o], p + q0, m->p.pnorm);
+    }
+    for (int32_t o = 0; o < nobj; ++o) {
+        size_t q0 = 3 * (size_t)off[o], q1 = 3 * (size_t)off[o + 1];
+        memset(po, 0, sizeof(double) * n);
+        memcpy(po + q0, p + q0, sizeof(double) * (q1 - q0));
+        st = or_pHp(m, x, po, &s[o].pHp);
+        if (st) goto done;
+        or_ncg_alpha(s[o].gp, s[o].pHp, s[o].pmax, m->p.dhat, al + 5 * (size_t)o);
+    }
+    for (int32_t o = 0; o < nobj; ++o) {
+        const double *a = al + 5 * (size_t)o;
+        double step = (moving && !moving[o]) ? 0.0 : a[0];
+        for (size_t q = 3 * (size_t)off[o]; q < 3 * (size_t)off[o + 1]; ++q) x[q] += step * p[q];
+        s[o].alpha = step; s[o].alpha_bar = a[1]; s[o].alpha_up = a[2]; s[o].dE = a[3]; s[o].capped = (int32_t)a[4];
+        s[o].n_active = nact; s[o].n_plane = nplane;
+        if (s[o].k == 0) s[o].dE0 = s[o].dE;
+        s[o].k += 1;
+    }
+    memcpy(g, g1, sizeof(double) * n);
+    memcpy(P, P1, sizeof(double) * n);
+done:
+    free(g1); free(d1); free(P1); free(po); free(al);
+    return st;
 }
 
 /*

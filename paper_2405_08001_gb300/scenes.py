@@ -229,6 +229,22 @@ def two_blocks(seed: int = 0, n: int = 3, side: float = 0.03, gap: float = 0.5, 
                  plane=((0.0, 0.0, 1.0), 0.0) if plane else None, iters=iters, steps=steps)
 
 
+def objects(seed: int = 0, n: int = 3, side: float = 0.03, dhat: float = 2e-3, iters: int = 20) -> Scene:
+    """Three objects of one scene for per-object splitting (Sec. 5.2): the two blocks of `two_blocks(seed)` (the
+    rotated upper block falling onto the lower one, which rests a little above the plane) and a third block
+    falling freely well away from both.  scene_of_vert holds the object of each vertex (0, 1, 2)."""
+    ab = two_blocks(seed, n=n, side=side, dhat=dhat, iters=iters)
+    Xc, Tc = kuhn_grid(n, n, n, size=(side, side, side), origin=(4.0 * side, 0.0, 0.02))
+    na = kuhn_grid(n, n, n)[0].shape[0]
+    X = np.concatenate([ab.rest_x, Xc])
+    T = np.concatenate([ab.tets, Tc + ab.n_verts]).astype(np.int32)
+    v0 = np.concatenate([ab.v0, np.zeros_like(Xc)])
+    obj = np.concatenate([np.zeros(na), np.ones(ab.n_verts - na), np.full(Xc.shape[0], 2)]).astype(np.int32)
+    return Scene(name=f"objects{seed}", rest_x=X, tets=T, x0=X.copy(), v0=v0, youngs=ab.youngs, poisson=ab.poisson,
+                 density=ab.density, dt=ab.dt, dhat=dhat, kappa=ab.kappa, gravity=ab.gravity, plane=ab.plane,
+                 scene_of_vert=obj, iters=iters, steps=3)
+
+
 def toss(n: int = 24, side: float = 0.1, dt: float = 1.0 / 60.0, steps: int = 20, seed: int = 3,
          youngs: float = 1e5, poisson: float = 0.4, dhat: float = 1e-3, kappa: float = 1e4, iters: int = 50,
          height: float = 0.02) -> Scene:
