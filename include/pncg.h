@@ -106,6 +106,14 @@ typedef struct {
                              synchronise), and the faster form runs from then on (sim_stats.launch_form).  Falls
                              back to 0 when the device cannot launch cooperative kernels; batched scenes always run
                              persistent. */
+    int32_t split_objects; /* 0 (default) = the groups of sim_mesh.scene_of_vert are independent scenes (no pair
+                             spans two of them).  1 = they are objects of ONE scene that may touch one another
+                             (pairs between two objects are contact candidates), each with its own beta, direction,
+                             max |p_v|, alpha and eps rule: the per-object splitting of Sec. 5.2.  Object o steps
+                             along p_o (p with every other object's entries zero) by alpha_o = min(dhat / (2 max_o
+                             |p_v|), -g^T p_o / p_o^T H p_o); a pair between objects a and b adds to p_a^T H p_a
+                             and to p_b^T H p_b, each with the other object's entries of p zero.  Needs the
+                             persistent form, like batched scenes. */
 } sim_options;
 
 /* Statistics of the last completed time step. */

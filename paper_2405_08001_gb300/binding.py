@@ -38,7 +38,7 @@ class sim_options(C.Structure):
                 ("gravity", C.c_double * 3), ("has_plane", C.c_int32), ("plane_n", C.c_double * 3),
                 ("plane_o", C.c_double), ("pad_r", C.c_double), ("pnorm", C.c_int32), ("scatter", C.c_int32),
                 ("excl_factor", C.c_double), ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
-                ("candidate_capacity", C.c_int32), ("persistent", C.c_int32)]
+                ("candidate_capacity", C.c_int32), ("persistent", C.c_int32), ("split_objects", C.c_int32)]
 
 
 class sim_stats(C.Structure):

@@ -1,7 +1,9 @@
 // Batched form of the persistent step: many independent scenes in one launch (the vertices and tets of each scene
 // contiguous, scene ids non-decreasing).  Each scene is its own PNCG problem -- own beta, direction scale, max |p_v|,
 // alpha and eps rule: the per-object splitting of Sec. 5.2 applied to scenes that share no contact -- while the
-// gradient pass, the candidate build and the grid barriers are shared.
+// gradient pass, the candidate build and the grid barriers are shared.  With split objects the groups are objects
+// of one scene: the candidate pass also pairs primitives of two objects, and such a pair's p^T H p term is split
+// between the two objects (each with the other's entries of p zero).
 //
 // Per-scene sums: the lanes of a warp take consecutive vertices (tets), so their scene ids are non-decreasing; a
 // segmented warp scan adds up each run of equal ids and the run's last lane adds it to the scene's accumulator
@@ -215,13 +217,31 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, uns
         for (int kk = tid; kk < na; kk += nthr) {   // active pairs come in no order: one atomic each
             Active<R> ap;
             load_active<R>(D, kk, ap);
-            const int key = D.vscene[ap.v.x];
-            const double bd = sbeta[key];
-            const R b = R(bd);
-            const bool nzb = bd != 0.0;
-            atomicAdd(acc + (size_t)key * 8 + 2,
-                      pair_pHp_vec<R>(ap, dir_of<R>(D, ap.v.x, b, nzb), dir_of<R>(D, ap.v.y, b, nzb),
-                                      dir_of<R>(D, ap.v.z, b, nzb), dir_of<R>(D, ap.v.w, b, nzb)));
+            const int vv[4] = {ap.v.x, ap.v.y, ap.v.z, ap.v.w};
+            int ks[4];
+            R4 pv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {   // each vertex takes the direction of its own scene (object)
+                ks[q] = D.vscene[vv[q]];
+                const double bd = sbeta[ks[q]];
+                pv[q] = dir_of<R>(D, vv[q], R(bd), bd != 0.0);
+            }
+            // both primitives of a pair lie in one object each: v.x in the first (the point, or edge a), v.w in the
+            // second.  A pair between two objects (split objects only) adds to each object's p^T H p with the
+            // other object's entries of p zero.
+            const int ka = ks[0], kb = ks[3];
+            if (ka == kb) {
+                atomicAdd(acc + (size_t)ka * 8 + 2, pair_pHp_vec<R>(ap, pv[0], pv[1], pv[2], pv[3]));
+            } else {
+                const R4 z = mk4<R>(R(0), R(0), R(0), R(0));
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int key = side ? kb : ka;
+                    atomicAdd(acc + (size_t)key * 8 + 2,
+                              pair_pHp_vec<R>(ap, ks[0] == key ? pv[0] : z, ks[1] == key ? pv[1] : z,
+                                              ks[2] == key ? pv[2] : z, ks[3] == key ? pv[3] : z));
+                }
+            }
         }
         grid_barrier(br, c);
         if (threadIdx.x == 0) sh.fe = (volatile const uint32_t &)c->err;

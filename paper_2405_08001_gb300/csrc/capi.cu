@@ -62,6 +62,7 @@ sim_status sim_default_options(sim_options *o)
     o->use_graph = 1;
     o->candidate_capacity = 0;
     o->persistent = 1;
+    o->split_objects = 0;
     return SIM_OK;
 }
 

@@ -115,7 +115,8 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         return SIM_ERR_INVALID_ARG;
     }
     if (opt.iters <= 0 || opt.beta < 0 || opt.beta > 1 || opt.pnorm < 0 || opt.pnorm > 1 || opt.precision < 0 ||
-        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 2 || opt.persistent < 0 || opt.persistent > 2) {
+        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 2 || opt.persistent < 0 || opt.persistent > 2 ||
+        opt.split_objects < 0 || opt.split_objects > 1) {
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }

@@ -145,8 +145,8 @@ public:
         sim_status st = alloc_all();
         if (st != SIM_OK) return st;
         if (M.nseg > 1 && !persist)
-            return fail(SIM_ERR_INVALID_ARG, "batched scenes need the persistent form (options.persistent = 1 on a "
-                                             "device with cooperative launch)");
+            return fail(SIM_ERR_INVALID_ARG, "batched scenes and split objects need the persistent form "
+                                             "(options.persistent = 1 on a device with cooperative launch)");
         return upload_initial();
     }
 
@@ -934,7 +934,7 @@ private:
         unsigned long long *ex = nullptr;
         if (!M.excl.empty()) AL(ex, M.excl.size());
         B.excl = ex; B.nexcl = (int)M.excl.size();
-        B.vscene = D.vscene;
+        B.vscene = M.opt.split_objects ? nullptr : D.vscene;   // objects of one scene touch one another
         B.infl = M.dhat + D.pad_r;
         B.thr = (float)(B.infl * 1.001);
         B.ctrl = c;
