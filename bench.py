@@ -300,29 +300,32 @@ def run_ours(args):
     # iterations per step the twisted bar ends between steps 100 and 115 with an inverted tet next to a cap (the
     # cap layer is compressed to under 1 % of its rest volume by then, and moving the caps to their next targets
     # at the start of a step flips it before the first iteration; the FP64 oracle does the same)
-    K150, f150 = min(K, 10), 80
-    sim150 = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
-                   persistent=0 if args.phases else 1, iters=150)
-    try:
-        for s in range(f150):
-            B.sim_step_async(sim150.h, 1, targets[s])
-        torch.cuda.synchronize()
-        B.sim_get_state(sim150.h, want_x=False, want_v=False)
-        t150 = time_steps(B, torch, sim150, targets, f150, K150, flush, f150 + K150)
-        _, _, st150 = B.sim_get_state(sim150.h, want_x=False, want_v=False)
+    def iter_max_150(K150=min(K, 10), f150=80):
+        sim150 = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
+                       persistent=0 if args.phases else 1, iters=150)
+        try:
+            for s in range(f150):
+                B.sim_step_async(sim150.h, 1, targets[s])
+            torch.cuda.synchronize()
+            B.sim_get_state(sim150.h, want_x=False, want_v=False)
+            t150 = time_steps(B, torch, sim150, targets, f150, K150, flush, f150 + K150)
+            _, _, st150 = B.sim_get_state(sim150.h, want_x=False, want_v=False)
+        except B.SimError as e:
+            return {"iters_per_step": 150, "error": str(e)}
+        finally:
+            sim150.close()
         ms150 = sum(t150) / K150
-        iter150 = {"iters_per_step": 150, "value": round(K150 * 150 / (sum(t150) / 1e3), 2), "unit": UNIT,
-                   "ms_per_step": round(ms150, 4), "time_steps_per_s": round(1e3 / ms150, 2), "steps": K150,
-                   "timed_steps": f"{f150}..{f150 + K150 - 1}", "dE_last_over_dE0_last_step":
-                   st150["dE_last"] / st150["dE0"] if st150["dE0"] else None}
-    except B.SimError as e:
-        iter150 = {"iters_per_step": 150, "error": str(e)}
-    sim150.close()
+        return {"iters_per_step": 150, "value": round(K150 * 150 / (sum(t150) / 1e3), 2), "unit": UNIT,
+                "ms_per_step": round(ms150, 4), "time_steps_per_s": round(1e3 / ms150, 2), "steps": K150,
+                "timed_steps": f"{f150}..{f150 + K150 - 1}",
+                "dE_last_over_dE0_last_step": st150["dE_last"] / st150["dE0"] if st150["dE0"] else None}
+
+    iter150 = None if args.no_extras else iter_max_150()
 
     # PR+ against DK (Sec. 4.1): the whole run step by step, untimed; per step the last iteration's energy
     # decrease relative to the first (the convergence measure of the stopping rule in Sec. 4.4)
-    conv = {}
-    for name, beta in (("pr_plus", B.SIM_BETA_PR_PLUS), ("dk", B.SIM_BETA_DK)):
+    conv = None if args.no_extras else {}
+    for name, beta in ((("pr_plus", B.SIM_BETA_PR_PLUS), ("dk", B.SIM_BETA_DK)) if not args.no_extras else ()):
         simc = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
                      persistent=0 if args.phases else 1, beta=beta)
         ratios, err = [], None
@@ -342,14 +345,16 @@ def run_ours(args):
                       "worst_dE_last_over_dE0": float(10 ** lr.max()), "steps": len(ratios),
                       **({"error": err} if err else {})}
 
-    # end to end through the C ABI with host buffers: pinned targets in, positions out, every step
+    # end to end through the C ABI with host buffers: pinned targets in, positions out, every step (the step is
+    # enqueued with sim_step_async; sim_get_state copies the positions out, synchronises and reports any error of
+    # the step: one synchronisation per step)
     e2e = None
     if True:
         sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
         tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
         x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
         for s in range(first):
-            B.sim_step(sim.h, 1, tg_host[s])
+            B.sim_step_async(sim.h, 1, tg_host[s])
             B.sim_get_state(sim.h, x_out=x_host, want_v=False)
         span = max(1, cfg_steps - first)
         saved = B.sim_get_state(sim.h)[:2] if K > span else None
@@ -358,7 +363,7 @@ def run_ours(args):
             if s > 0 and s % span == 0:
                 B.sim_set_state(sim.h, *saved)   # not timed, as in the device-timed window
             t0 = time.perf_counter()
-            B.sim_step(sim.h, 1, tg_host[first + s % span])
+            B.sim_step_async(sim.h, 1, tg_host[first + s % span])
             B.sim_get_state(sim.h, x_out=x_host, want_v=False)
             te += time.perf_counter() - t0
         sim.close()
@@ -468,7 +473,8 @@ def run_ours(args):
                            "launch_choice": "autotuned (options.persistent = 2)" if not args.phases else "per phase",
                            "speedup_fp32_over_fp64": round(value / ws / v64, 3)},
             "iter_max_150": iter150,
-            "beta_convergence": {"note": "whole 120-step run, FP32-mixed, 50 iterations per step, untimed", **conv},
+            "beta_convergence": None if conv is None else
+            {"note": "whole 120-step run, FP32-mixed, 50 iterations per step, untimed", **conv},
             "roofline": {"bound": "hbm", "kernel": dom, "largest_phase": dom_all, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes_per_launch": int(abytes),
@@ -564,6 +570,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="one kernel per phase instead of the persistent step")
     ap.add_argument("--no-pile", action="store_true", help="skip the large-pile and batched measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the IterMax-150 run and the PR+ / DK convergence comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -1061,11 +1061,12 @@ private:
         CK(cudaGetLastError());
         return SIM_OK;
     }
+    // enqueues the unpack and the copy out; the caller synchronises (the stream orders a following unpack into the
+    // same staging buffer after this copy)
     sim_status out3(const double4_32a *src, double *dst)
     {
         k_unpack4<<<(M.nv + 255) / 256, 256, 0, s>>>(src, stage, M.nv);
         CK(cudaMemcpyAsync(dst, stage, 24 * (size_t)M.nv, cudaMemcpyDefault, s));
-        CK(cudaStreamSynchronize(s));
         return SIM_OK;
     }
 
@@ -1073,8 +1074,9 @@ private:
 
     sim_status sync_and_check()
     {
+        // the control block comes back behind the stream's work (hctrl is pinned): one synchronisation
+        CK(cudaMemcpyAsync(hctrl, dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        CK(cudaMemcpy(hctrl, dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
         const uint32_t e = hctrl->err;
         if (e == 0u) return SIM_OK;
         // report, clear the sticky error, and grow the candidate buffer on overflow
