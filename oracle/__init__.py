@@ -39,13 +39,17 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+# energy densities (Sec. 3.1): the paper's Neo-Hookean, stable Neo-Hookean, fixed corotated, as-rigid-as-possible
+NH, SNH, FCR, ARAP = 0, 1, 2, 3
+
+
 class _Params(C.Structure):
     _fields_ = [("nv", C.c_int32), ("nt", C.c_int32), ("rest_x", C.c_void_p), ("tets", C.c_void_p),
                 ("youngs_per_tet", C.c_void_p), ("youngs", C.c_double), ("poisson", C.c_double),
                 ("density", C.c_double), ("h", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
                 ("gravity", C.c_double * 3), ("has_plane", C.c_int32), ("plane_n", C.c_double * 3),
                 ("plane_o", C.c_double), ("fixed", C.c_void_p), ("beta_rule", C.c_int32), ("pnorm", C.c_int32),
-                ("excl_factor", C.c_double)]
+                ("excl_factor", C.c_double), ("model", C.c_int32)]
 
 
 class _Scalars(C.Structure):
@@ -150,7 +154,7 @@ class Oracle:
     """The oracle's model of one scene (rest data, surface, exclusion set) and its operations."""
 
     def __init__(self, rest_x, tets, *, youngs, poisson, density, dt, dhat, kappa, gravity=(0, 0, 0), plane=None,
-                 fixed=None, youngs_per_tet=None, beta_rule=0, pnorm=0, excl_factor=1.5):
+                 fixed=None, youngs_per_tet=None, beta_rule=0, pnorm=0, excl_factor=1.5, model=0):
         lib = _load()
         self._X = _f64(rest_x).reshape(-1, 3)
         self._T = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
@@ -168,7 +172,7 @@ class Oracle:
             pr.plane_n[:] = list(plane[0])
             pr.plane_o = float(plane[1])
         pr.fixed = _ptr(self._F)
-        pr.beta_rule, pr.pnorm, pr.excl_factor = beta_rule, pnorm, excl_factor
+        pr.beta_rule, pr.pnorm, pr.excl_factor, pr.model = beta_rule, pnorm, excl_factor, model
         self._m = lib.or_model_new(C.byref(pr))
         if not self._m:
             raise OracleError(1, lib.or_last_error().decode())

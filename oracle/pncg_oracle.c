@@ -10,6 +10,8 @@
  * What it computes, by paper section:
  *   - incremental potential E(x) = 1/2 (x - xt)^T M (x - xt) + h^2 Psi(x) + kappa sum_C b(d_k)   (Sec. 3, Eq. E)
  *   - Neo-Hookean Psi = mu/2 (I2 - 3) - mu log I3 + lambda/2 (log I3)^2                        (Sec. 3.1)
+ *     and the other densities of the invariants I1 = tr(S), I2, I3: stable Neo-Hookean, fixed corotated,
+ *     as-rigid-as-possible (the materials of Table 1), I1 through the polar decomposition F = R S   (Sec. 3.1)
  *     with its gradient, its Hessian diagonal and p^T H p through the six-term split
  *     sum_i (Psi_ii h_i + Psi_i h_{i+3}) using vec(dF/dx) as an explicit 9x12 matrix            (Sec. 3.1)
  *   - the log barrier b(d) and its gradient / diagonal / p^T H p through t and c_0..c_3          (Sec. 3.2, Eqs. 8-13)
@@ -73,7 +75,18 @@ typedef struct {
     int32_t beta_rule;             /* 0 = PR+, 1 = DK */
     int32_t pnorm;                 /* 0 = max vertex 2-norm, 1 = max abs component */
     double excl_factor;            /* rest-pose exclusion radius in units of dhat (Sec. 5.1 uses 1.5) */
+    int32_t model;                 /* energy density: OR_NH, OR_SNH, OR_FCR, OR_ARAP (Sec. 3.1, Table 1) */
 } or_params;
+
+/* energy densities in the invariants I1 = tr(S) (F = R S), I2 = tr(F^T F), I3 = det F of Sec. 3.1:
+ *   NH   mu/2 (I2 - 3) - mu log I3 + lambda/2 (log I3)^2        (the paper's Neo-Hookean)
+ *   SNH  mu/2 (I2 - 3) - mu (I3 - 1) + lambda/2 (I3 - 1)^2       (stable Neo-Hookean)
+ *   FCR  mu (I2 - 2 I1 + 3) + lambda/2 (I3 - 1)^2               (fixed corotated: mu |F - R|^2 + ...)
+ *   ARAP mu (I2 - 2 I1 + 3)                                      (as-rigid-as-possible: mu |F - R|^2) */
+#define OR_NH 0
+#define OR_SNH 1
+#define OR_FCR 2
+#define OR_ARAP 3
 
 typedef struct {
     int32_t type;       /* OR_PT: v[0] point, v[1..3] triangle; OR_EE: v[0]-v[1] and v[2]-v[3] */
@@ -467,7 +480,8 @@ void or_model_free(or_model *m)
 
 or_model *or_model_new(const or_params *p)
 {
-    if (!p || p->nv <= 0 || p->nt <= 0 || !p->rest_x || !p->tets || !(p->h > 0) || !(p->dhat > 0) || p->kappa < 0) {
+    if (!p || p->nv <= 0 || p->nt <= 0 || !p->rest_x || !p->tets || !(p->h > 0) || !(p->dhat > 0) || p->kappa < 0 ||
+        p->model < OR_NH || p->model > OR_ARAP) {
         set_err("invalid parameters");
         return NULL;
     }
@@ -621,12 +635,88 @@ void or_surface(const or_model *m, int32_t *tri, int32_t *edge, int32_t *svert)
 typedef struct {
     double F[3][3];
     double J[9][12];
-    double I2, I3, logI3;
-    double g2[9], g3[9];          /* gradients of I2 and I3 with respect to vec(F) */
+    double I1, I2, I3, logI3;
+    double g1[9], g2[9], g3[9];   /* gradients of I1, I2 and I3 with respect to vec(F) */
+    double H1[9][9];              /* Hessian of I1 (FCR, ARAP only; zero otherwise) */
     double H3[9][9];              /* Hessian of I3; H2 = 2 I */
-    double Psi2, Psi3, Psi22, Psi33;
+    double Psi1, Psi2, Psi3, Psi11, Psi22, Psi33;
     double scale;                 /* h^2 V_e */
 } tet_terms;
+
+/*
+ * Eigen-decomposition of a symmetric 3x3 matrix A by cyclic Jacobi rotations (Golub and Van Loan, Sec. 8.5):
+ * A = V diag(ev) V^T, V orthonormal with det V = +1.  A is overwritten.
+ */
+static void sym_eig3(double A[3][3], double ev[3], double V[3][3])
+{
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        double nrm = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2] + 2.0 * off;
+        if (off <= 1e-34 * nrm) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* the rotation in the (p, q) plane that zeroes A[p][q] */
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; ++k) {   /* A <- A G */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {   /* A <- G^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {   /* V <- V G */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) ev[i] = A[i][i];
+    double d = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) - V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+               V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+    if (d < 0) for (int i = 0; i < 3; ++i) V[i][2] = -V[i][2];
+}
+
+/*
+ * I1 = tr(S) of the polar decomposition F = R S (Sec. 3.1), for det F > 0: F^T F = V Sigma^2 V^T, U = F V Sigma^-1,
+ * R = U V^T, I1 = sum sigma_i.  g1 = vec(R).  H1 = sum_i lambda_i q_i q_i^T over the three twist modes
+ * q_i = vec(U T_i V^T) / sqrt(2) (T_i the skew generator about axis i) with lambda_i = 2 / (sigma_j + sigma_k),
+ * (i, j, k) cyclic: the second derivative of tr(S) is zero along the stretches and flips, and dR[dF] rotates with
+ * the skew part of U^T dF V scaled by 1 / (sigma_j + sigma_k).
+ */
+static void polar_terms(tet_terms *T)
+{
+    double C[3][3], sg2[3], V[3][3], U[3][3], sg[3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) C[a][b] = T->F[0][a] * T->F[0][b] + T->F[1][a] * T->F[1][b] + T->F[2][a] * T->F[2][b];
+    sym_eig3(C, sg2, V);
+    for (int i = 0; i < 3; ++i) sg[i] = sqrt(sg2[i] > 0 ? sg2[i] : 0.0);
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 3; ++i)
+            U[a][i] = (T->F[a][0] * V[0][i] + T->F[a][1] * V[1][i] + T->F[a][2] * V[2][i]) / sg[i];
+    T->I1 = sg[0] + sg[1] + sg[2];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            T->g1[3 * b + a] = U[a][0] * V[b][0] + U[a][1] * V[b][1] + U[a][2] * V[b][2];   /* R_ab, vec column-wise */
+    memset(T->H1, 0, sizeof T->H1);
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        double lam = 2.0 / (sg[j] + sg[k]);
+        /* T_i has +1 at (j, k) and -1 at (k, j): q = vec(U T_i V^T) / sqrt(2), (U T_i V^T)_ab = U_aj V_bk - U_ak V_bj */
+        double q[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) q[3 * b + a] = (U[a][j] * V[b][k] - U[a][k] * V[b][j]) / sqrt(2.0);
+        for (int r = 0; r < 9; ++r)
+            for (int c = 0; c < 9; ++c) T->H1[r][c] += lam * q[r] * q[c];
+    }
+}
 
 static int tet_eval(const or_model *m, int32_t e, const double *x, tet_terms *T)
 {
@@ -672,17 +762,43 @@ static int tet_eval(const or_model *m, int32_t e, const double *x, tet_terms *T)
     if (!(T->I3 > 0.0)) return OR_ERR_INVERTED;
     double mu = m->mu[e], lam = m->lam[e];
     T->logI3 = log(T->I3);
-    T->Psi2 = mu / 2.0;
-    T->Psi22 = 0.0;
-    T->Psi3 = (lam * T->logI3 - mu) / T->I3;
-    T->Psi33 = (mu + lam * (1.0 - T->logI3)) / (T->I3 * T->I3);
+    T->I1 = 3.0;
+    memset(T->g1, 0, sizeof T->g1);
+    memset(T->H1, 0, sizeof T->H1);
+    T->Psi1 = T->Psi11 = T->Psi22 = 0.0;
+    switch (m->p.model) {
+    case OR_SNH:
+        T->Psi2 = mu / 2.0;
+        T->Psi3 = -mu + lam * (T->I3 - 1.0);
+        T->Psi33 = lam;
+        break;
+    case OR_FCR:
+    case OR_ARAP:
+        polar_terms(T);
+        T->Psi1 = -2.0 * mu;
+        T->Psi2 = mu;
+        T->Psi3 = m->p.model == OR_FCR ? lam * (T->I3 - 1.0) : 0.0;
+        T->Psi33 = m->p.model == OR_FCR ? lam : 0.0;
+        break;
+    default:   /* OR_NH */
+        T->Psi2 = mu / 2.0;
+        T->Psi3 = (lam * T->logI3 - mu) / T->I3;
+        T->Psi33 = (mu + lam * (1.0 - T->logI3)) / (T->I3 * T->I3);
+    }
     T->scale = m->p.h * m->p.h * m->vol[e];
     return OR_OK;
 }
 
-static double nh_psi(double mu, double lam, const tet_terms *T)
+/* the energy density of the model at the tet's invariants */
+static double tet_psi(const or_model *m, int32_t e, const tet_terms *T)
 {
-    return mu / 2.0 * (T->I2 - 3.0) - mu * T->logI3 + lam / 2.0 * T->logI3 * T->logI3;
+    double mu = m->mu[e], lam = m->lam[e];
+    switch (m->p.model) {
+    case OR_SNH: return mu / 2.0 * (T->I2 - 3.0) - mu * (T->I3 - 1.0) + lam / 2.0 * (T->I3 - 1.0) * (T->I3 - 1.0);
+    case OR_FCR: return mu * (T->I2 - 2.0 * T->I1 + 3.0) + lam / 2.0 * (T->I3 - 1.0) * (T->I3 - 1.0);
+    case OR_ARAP: return mu * (T->I2 - 2.0 * T->I1 + 3.0);
+    default: return mu / 2.0 * (T->I2 - 3.0) - mu * T->logI3 + lam / 2.0 * T->logI3 * T->logI3;
+    }
 }
 
 /* ------------------------------------------------------------------------------------------------ energy, gradient, diag, pHp */
@@ -707,7 +823,7 @@ int or_energy(const or_model *m, const double *x, const double *xtilde, double *
         tet_terms T;
         int st = tet_eval(m, e, x, &T);
         if (st) { set_err("inverted tet"); return st; }
-        Eel += T.scale * nh_psi(m->mu[e], m->lam[e], &T);
+        Eel += T.scale * tet_psi(m, e, &T);
     }
     pair_list L = {0};
     int st = find_pairs(m, x, m->p.dhat, 1, 0, &L);
@@ -736,7 +852,7 @@ int or_energy(const or_model *m, const double *x, const double *xtilde, double *
  * Gradient g and Jacobi diagonal diag(H) of E at x (Eqs. E, Hessian), unmasked (kinematic vertices included).
  *   inertia:  g += M (x - xt), diag += m
  *   elastic:  g += h^2 V J^T (Psi2 g2 + Psi3 g3);  diag += h^2 V sum_i (Psi_ii diag(h_i) + Psi_i diag(h_{i+3}))
- *             with h_i = J^T g_i g_i^T J and h_{i+3} = J^T H_i J (the I1 terms vanish for Neo-Hookean)
+ *             with h_i = J^T g_i g_i^T J and h_{i+3} = J^T H_i J (the I1 terms vanish for NH and SNH)
  *   barrier:  g += kappa b'/d (dt/dx) t  (Eq. 8);  diag from Eqs. 9-11
  *   n_active receives the number of active pairs (NULL allowed).
  */
@@ -754,23 +870,28 @@ int or_grad_diag(const or_model *m, const double *x, const double *xtilde, doubl
         if (st) { set_err("inverted tet"); return st; }
         const int32_t *v = m->tet + 4 * (size_t)e;
         double dPsi[9];
-        for (int r = 0; r < 9; ++r) dPsi[r] = T.Psi2 * T.g2[r] + T.Psi3 * T.g3[r];
-        double Jg2[12], Jg3[12], dg[12], dh[12];
+        for (int r = 0; r < 9; ++r) dPsi[r] = T.Psi1 * T.g1[r] + T.Psi2 * T.g2[r] + T.Psi3 * T.g3[r];
+        double Jg1[12], Jg2[12], Jg3[12], dg[12], dh[12];
         for (int q = 0; q < 12; ++q) {
-            double s0 = 0, s2 = 0, s3 = 0;
-            for (int r = 0; r < 9; ++r) { s0 += T.J[r][q] * dPsi[r]; s2 += T.J[r][q] * T.g2[r]; s3 += T.J[r][q] * T.g3[r]; }
-            dg[q] = s0; Jg2[q] = s2; Jg3[q] = s3;
+            double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            for (int r = 0; r < 9; ++r) {
+                s0 += T.J[r][q] * dPsi[r]; s1 += T.J[r][q] * T.g1[r];
+                s2 += T.J[r][q] * T.g2[r]; s3 += T.J[r][q] * T.g3[r];
+            }
+            dg[q] = s0; Jg1[q] = s1; Jg2[q] = s2; Jg3[q] = s3;
         }
-        /* diag(J^T H J) for H2 = 2 I and H3 */
+        /* diag(J^T H J) for H1, H2 = 2 I and H3 */
         for (int q = 0; q < 12; ++q) {
-            double h5 = 0, h6 = 0;
+            double h4 = 0, h5 = 0, h6 = 0;
             for (int r = 0; r < 9; ++r) {
                 h5 += T.J[r][q] * 2.0 * T.J[r][q];
-                double HJ = 0;
-                for (int s = 0; s < 9; ++s) HJ += T.H3[r][s] * T.J[s][q];
+                double HJ = 0, H1J = 0;
+                for (int s = 0; s < 9; ++s) { HJ += T.H3[r][s] * T.J[s][q]; H1J += T.H1[r][s] * T.J[s][q]; }
                 h6 += T.J[r][q] * HJ;
+                h4 += T.J[r][q] * H1J;
             }
-            dh[q] = T.Psi22 * Jg2[q] * Jg2[q] + T.Psi33 * Jg3[q] * Jg3[q] + T.Psi2 * h5 + T.Psi3 * h6;
+            dh[q] = T.Psi11 * Jg1[q] * Jg1[q] + T.Psi22 * Jg2[q] * Jg2[q] + T.Psi33 * Jg3[q] * Jg3[q] +
+                    T.Psi1 * h4 + T.Psi2 * h5 + T.Psi3 * h6;
         }
         for (int i = 0; i < 4; ++i)
             for (int a = 0; a < 3; ++a) {
@@ -833,16 +954,19 @@ int or_pHp(const or_model *m, const double *x, const double *p, double *out)
         double pe[12], Jp[9];
         for (int i = 0; i < 4; ++i) for (int a = 0; a < 3; ++a) pe[3 * i + a] = p[3 * (size_t)v[i] + a];
         for (int r = 0; r < 9; ++r) { double acc = 0; for (int q = 0; q < 12; ++q) acc += T.J[r][q] * pe[q]; Jp[r] = acc; }
-        double g2Jp = 0, g3Jp = 0, h5 = 0, h6 = 0;
+        double g1Jp = 0, g2Jp = 0, g3Jp = 0, h4 = 0, h5 = 0, h6 = 0;
         for (int r = 0; r < 9; ++r) {
+            g1Jp += T.g1[r] * Jp[r];
             g2Jp += T.g2[r] * Jp[r];
             g3Jp += T.g3[r] * Jp[r];
             h5 += Jp[r] * 2.0 * Jp[r];
-            double HJp = 0;
-            for (int q = 0; q < 9; ++q) HJp += T.H3[r][q] * Jp[q];
+            double HJp = 0, H1Jp = 0;
+            for (int q = 0; q < 9; ++q) { HJp += T.H3[r][q] * Jp[q]; H1Jp += T.H1[r][q] * Jp[q]; }
             h6 += Jp[r] * HJp;
+            h4 += Jp[r] * H1Jp;
         }
-        s += T.scale * (T.Psi22 * g2Jp * g2Jp + T.Psi33 * g3Jp * g3Jp + T.Psi2 * h5 + T.Psi3 * h6);
+        s += T.scale * (T.Psi11 * g1Jp * g1Jp + T.Psi22 * g2Jp * g2Jp + T.Psi33 * g3Jp * g3Jp + T.Psi1 * h4 +
+                        T.Psi2 * h5 + T.Psi3 * h6);
     }
     pair_list L = {0};
     int st = find_pairs(m, x, m->p.dhat, 1, 0, &L);
