@@ -67,11 +67,21 @@ typedef struct {
                                needs the persistent form.  NULL = one scene */
 } sim_mesh;
 
-/* Neo-Hookean material (Sec. 3.1): mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)). */
+/* Energy densities in the invariants I1 = tr(S) (F = R S), I2 = tr(F^T F), I3 = det F of Sec. 3.1 (sim_material.model):
+ *   SIM_MAT_NH   mu/2 (I2 - 3) - mu log I3 + lambda/2 (log I3)^2   the paper's Neo-Hookean (default)
+ *   SIM_MAT_SNH  mu/2 (I2 - 3) - mu (I3 - 1) + lambda/2 (I3 - 1)^2  stable Neo-Hookean
+ *   SIM_MAT_FCR  mu (I2 - 2 I1 + 3) + lambda/2 (I3 - 1)^2          fixed corotated (mu |F - R|^2 + ...)
+ *   SIM_MAT_ARAP mu (I2 - 2 I1 + 3)                                 as-rigid-as-possible (mu |F - R|^2)
+ * FCR and ARAP (the I1 densities) run in the FP64 form only; sim_eval_hvp and sim_adjoint_step support NH only.
+ * Every density treats det F <= 0 as an error (SIM_ERR_INVERTED). */
+enum { SIM_MAT_NH = 0, SIM_MAT_SNH = 1, SIM_MAT_FCR = 2, SIM_MAT_ARAP = 3 };
+
+/* Material (Sec. 3.1): mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)). */
 typedef struct {
     double density;                /* rho, kg/m^3; lumped mass m_v = sum_e rho V_e / 4 */
     double youngs, poisson;        /* E (Pa), nu */
     const double *youngs_per_tet;  /* [n_tets] host, per-tet E overriding youngs; NULL = uniform */
+    int32_t model;                 /* SIM_MAT_NH (0, default), SIM_MAT_SNH, SIM_MAT_FCR or SIM_MAT_ARAP */
 } sim_material;
 
 typedef struct {

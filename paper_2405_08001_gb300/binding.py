@@ -18,6 +18,7 @@ SIM_OK, SIM_ERR_INVALID_ARG, SIM_ERR_CUDA, SIM_ERR_OOM, SIM_ERR_INVERTED, SIM_ER
     SIM_ERR_NONFINITE, SIM_ERR_TIMEOUT, SIM_ERR_CAPACITY = range(9)
 SIM_FP64, SIM_FP32_MIXED = 0, 1
 SIM_BETA_PR_PLUS, SIM_BETA_DK = 0, 1
+SIM_MAT_NH, SIM_MAT_SNH, SIM_MAT_FCR, SIM_MAT_ARAP = 0, 1, 2, 3
 SIM_PNORM_VERTEX2, SIM_PNORM_COMPONENT_INF = 0, 1
 SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED, SIM_SCATTER_BLOCK = 0, 1, 2
 TRACE_COLUMNS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "n_active", "capped")
@@ -30,7 +31,7 @@ class sim_mesh(C.Structure):
 
 class sim_material(C.Structure):
     _fields_ = [("density", C.c_double), ("youngs", C.c_double), ("poisson", C.c_double),
-                ("youngs_per_tet", C.c_void_p)]
+                ("youngs_per_tet", C.c_void_p), ("model", C.c_int32)]
 
 
 class sim_options(C.Structure):
@@ -158,7 +159,7 @@ def sim_default_options() -> sim_options:
 
 
 def sim_create(rest_x, tets, *, density, youngs, poisson, dt, dhat, kappa, x0=None, v0=None, fixed=None,
-               youngs_per_tet=None, scene_of_vert=None, options: sim_options | None = None):
+               youngs_per_tet=None, scene_of_vert=None, options: sim_options | None = None, model: int = SIM_MAT_NH):
     """sim_create with host arrays; returns the opaque handle (a c_void_p value)."""
     lib = load()
     rx = np.ascontiguousarray(rest_x, dtype=np.float64).reshape(-1, 3)
@@ -175,7 +176,7 @@ def sim_create(rest_x, tets, *, density, youngs, poisson, dt, dhat, kappa, x0=No
             keep.append(a)
             setattr(m, name, a.ctypes.data)
     mat = sim_material()
-    mat.density, mat.youngs, mat.poisson = density, youngs, poisson
+    mat.density, mat.youngs, mat.poisson, mat.model = density, youngs, poisson, int(model)
     if youngs_per_tet is not None:
         e = np.ascontiguousarray(youngs_per_tet, dtype=np.float64)
         keep.append(e)
@@ -426,13 +427,13 @@ def options_for(scene, precision=SIM_FP64, **kw) -> sim_options:
 class Sim:
     """Owning wrapper of a handle: Sim(scene, precision=..., **options)."""
 
-    def __init__(self, scene, precision=SIM_FP64, options: sim_options | None = None, **kw):
+    def __init__(self, scene, precision=SIM_FP64, options: sim_options | None = None, model: int = SIM_MAT_NH, **kw):
         self.scene = scene
         self.options = options if options is not None else options_for(scene, precision, **kw)
         self.h = sim_create(scene.rest_x, scene.tets, density=scene.density, youngs=scene.youngs,
                             poisson=scene.poisson, dt=scene.dt, dhat=scene.dhat, kappa=scene.kappa, x0=scene.x0,
                             v0=scene.v0, fixed=scene.fixed, youngs_per_tet=scene.youngs_per_tet,
-                            scene_of_vert=scene.scene_of_vert, options=self.options)
+                            scene_of_vert=scene.scene_of_vert, options=self.options, model=model)
         self.nv = scene.n_verts
 
     def close(self):

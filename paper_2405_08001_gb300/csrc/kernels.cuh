@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "ffloat.cuh"
 #include "geometry.cuh"
+#include "material.cuh"
 
 namespace pncg {
 
@@ -24,6 +25,8 @@ template <typename R> struct Dev {
     float4 *xbh;                       // FP32 form: xh at the last candidate build (displacement check)
     const float *G0;                   // FP32 form: [12][nt] rest metric Dm^T Dm of each tet as float-float
                                        // (hi of entries 00 01 02 11 12 22, then lo)
+    float4 *tS;                        // FP32 form: [4][nt] of the last gradient pass per tet: S = 2 dPsi/dC and
+                                       // C^-1 (entries 00 01 02 11 12 22 each), k1, k2, 0, 0 (tet_pHp_vec)
     R4 *g[2], *dg[2];                  // ping-pong by iteration parity; g.w = plane curvature kappa b'', dg.w = xtil.w
     R4 *p;
     R4 *pg, *pnext;                    // persistent form: P g of the current iteration, the next direction
@@ -37,6 +40,7 @@ template <typename R> struct Dev {
     const R *hv;                       // [nt] h^2 V_e
     const R *escale;                   // [nt] E_e / E or nullptr
     R mu, lam;
+    int model;                         // energy density: MAT_NH, MAT_SNH, MAT_FCR, MAT_ARAP (material.cuh)
     // contacts
     const int4 *cand;                  // candidates: PT (v, t0, t1, t2), EE (-1 - a0, a1, b0, b1)
     int cand_cap;
@@ -321,14 +325,14 @@ template <typename R> __device__ inline void load_tet_in(const Dev<R> &D, int e,
 }
 
 // First Piola-Kirchhoff stress of the FP32 form, evaluated from the metric change so that it stays accurate for
-// small strains under any rotation.  With C = F^T F and the Neo-Hookean density of Sec. 3.1 written in C,
-//   P = F C^-1 (mu (C - I) + lambda log J I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
-// which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly.  The metric change G = Ds^T Ds - Dm^T Dm is
+// small strains under any rotation.  With C = F^T F and a density of I2 and I3 (Sec. 3.1: NH or SNH) written in C,
+//   P = F C^-1 (mu (C - I) + (mu + Psi_3 J) I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
+// which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly; mu + Psi_3 J is lambda log J for NH.  The metric change G = Ds^T Ds - Dm^T Dm is
 // accumulated in float-float from the float-float current positions and the tet's float-float rest metric, so that
 // rounding never acts on the O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the
 // entries of C - I.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
 __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float> &in, TetF<float> &T, float P[3][3],
-                                         float &Psi33)
+                                         float &Psi33, int e)
 {
     const int4 tv = in.tv;
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
@@ -383,8 +387,23 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
                        A[0][2] * (A[0][1] * A[1][2] - A[1][1] * A[0][2]);
     const float dC = (A[0][0] + A[1][1] + A[2][2]) + (m01 + m02 + m12) + detA;   // det C - 1
     const float detC = 1.0f + dC;
-    const float L = 0.5f * log1pf(dC);                                             // log J
     const float mu = D.mu * in.es, lam = D.lam * in.es;
+    // mJ = mu + Psi_3 J: lambda log J (NH), (J - 1)(lambda J - mu) (SNH) with J - 1 = (det C - 1) / (J + 1)
+    // k1 = J (Psi_33 J + Psi_3) / 4, k2 = -Psi_3 J / 2: the coefficients of p^T H p in C (tet_pHp_vec)
+    float mJ, k1, k2;
+    if (D.model == MAT_SNH) {
+        const float J = sqrtf(detC), Jm1 = dC / (J + 1.0f);
+        mJ = Jm1 * (lam * J - mu);
+        Psi33 = lam;
+        k1 = 0.25f * J * (lam * (J + Jm1) - mu);
+        k2 = 0.5f * J * (mu - lam * Jm1);
+    } else {
+        const float L = 0.5f * log1pf(dC);                                         // log J
+        mJ = lam * L;
+        Psi33 = (mu + lam * (1.0f - L)) / detC;
+        k1 = 0.25f * lam;
+        k2 = 0.5f * (mu - lam * L);
+    }
     // C^-1 = cof(C) / det C (C symmetric)
     const float c00 = 1.0f + A[0][0], c11 = 1.0f + A[1][1], c22 = 1.0f + A[2][2];
     const float ic = 1.0f / detC;
@@ -399,7 +418,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) M[a][b] = mu * A[a][b] + (a == b ? lam * L : 0.0f);
+        for (int b = 0; b < 3; ++b) M[a][b] = mu * A[a][b] + (a == b ? mJ : 0.0f);
     float S[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -410,24 +429,32 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) P[a][b] = sc * (T.F[a][0] * S[0][b] + T.F[a][1] * S[1][b] + T.F[a][2] * S[2][b]);
-    Psi33 = (mu + lam * (1.0f - L)) / detC;
+    if (e >= 0) {   // S (symmetric: C^-1 commutes with C - I), C^-1, k1, k2 for the p^T H p pass
+        const size_t n = (size_t)D.nt;
+        D.tS[e] = make_float4(S[0][0], 0.5f * (S[0][1] + S[1][0]), 0.5f * (S[0][2] + S[2][0]), S[1][1]);
+        D.tS[n + e] = make_float4(0.5f * (S[1][2] + S[2][1]), S[2][2], Ci[0][0], Ci[0][1]);
+        D.tS[2 * n + e] = make_float4(Ci[0][2], Ci[1][1], Ci[1][2], Ci[2][2]);
+        D.tS[3 * n + e] = make_float4(k1, k2, 0.0f, 0.0f);
+    }
     return true;
 }
 
-// Element gradient and Jacobi diagonal (Sec. 3.1 split; NH has Psi_22 = 0 and the H3 term has a zero
-// diagonal, so diag_i[a] = h^2 V (mu |w_i|^2 + Psi_33 (cof(F) w_i)_a^2)).  The contributions go to the
+// Element gradient and Jacobi diagonal (Sec. 3.1 split; no density here has Psi_11 or Psi_22 terms and the H3
+// term has a zero diagonal, so diag_i[a] = h^2 V (2 Psi_2 |w_i|^2 + Psi_33 (cof(F) w_i)_a^2 + Psi_1 d2I1 entry)).  The contributions go to the
 // per-(tet, corner) buffer (segmented scatter), to the block's shared accumulators sacc ([6][SCATTER_MAXU],
 // indexed by the chunk-local vertex; block scatter) or straight to the global accumulators.
 template <typename R>
-__device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4][3], R dv[4][3])
+__device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4][3], R dv[4][3], int e = -1)
 {
     const int4 tv = in.tv;
     TetF<R> T;
     R P[3][3], Psi33;
     const R sc = in.hv;
     const R mu = D.mu * in.es, lam = D.lam * in.es;
+    R c2 = mu;        // 2 Psi_2
+    R Psi1 = R(0);    // the I1 term (FCR, ARAP; FP64 form)
     if constexpr (sizeof(R) == 4) {
-        if (!tet_stress_metric(D, in, T, P, Psi33)) return false;
+        if (!tet_stress_metric(D, in, T, P, Psi33, e)) return false;
     } else {
         R ds[3][3];
         tet_ds<R>(D, tv, ds);
@@ -437,14 +464,33 @@ __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4
             for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
         tet_F_from<R>(ds, T);
         if (!(T.J > R(0))) { flag_error(D.ctrl, ERR_INVERTED); return false; }
-        const R L = log(T.J);
-        const R Psi3 = (lam * L - mu) / T.J;
-        Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
+        const MatTerms<R> mt = mat_terms<R>(D.model, mu, lam, T.J);
+        Psi33 = mt.Psi33;
+        c2 = mt.c2;
+        Psi1 = mt.Psi1;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) P[a][b] = sc * (mu * T.F[a][b] + Psi3 * T.cf[a][b]);
+            for (int b = 0; b < 3; ++b) P[a][b] = sc * (c2 * T.F[a][b] + mt.Psi3 * T.cf[a][b]);
+        if (Psi1 != R(0)) {   // FCR, ARAP: Psi_1 R in the stress, Psi_1 d2I1 on the diagonal
+            Polar pol;
+            polar_of(T.F, pol);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) P[a][b] += sc * Psi1 * pol.R[a][b];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                double w[3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    w[b] = i == 0 ? -(T.w[0][b] + T.w[1][b] + T.w[2][b]) : T.w[i - 1][b];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) dv[i][a] = sc * Psi1 * polar_h1_diag(pol, w, a);
+            }
+        }
     }
+    const bool i1 = Psi1 != R(0);
 #pragma unroll
     for (int i = 1; i < 4; ++i) {
         const R *w = T.w[i - 1];
@@ -453,7 +499,7 @@ __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4
         for (int a = 0; a < 3; ++a) {
             gv[i][a] = P[a][0] * w[0] + P[a][1] * w[1] + P[a][2] * w[2];
             const R cw = T.cf[a][0] * w[0] + T.cf[a][1] * w[1] + T.cf[a][2] * w[2];
-            dv[i][a] = sc * (mu * ww + Psi33 * cw * cw);
+            dv[i][a] = (i1 ? dv[i][a] : R(0)) + sc * (c2 * ww + Psi33 * cw * cw);
         }
     }
     {
@@ -465,7 +511,7 @@ __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4
         for (int a = 0; a < 3; ++a) {
             gv[0][a] = -(gv[1][a] + gv[2][a] + gv[3][a]);
             const R cw = T.cf[a][0] * w0[0] + T.cf[a][1] * w0[1] + T.cf[a][2] * w0[2];
-            dv[0][a] = sc * (mu * ww + Psi33 * cw * cw);
+            dv[0][a] = (i1 ? dv[0][a] : R(0)) + sc * (c2 * ww + Psi33 * cw * cw);
         }
     }
     return true;
@@ -476,7 +522,7 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
 {
     const int4 tv = in.tv;
     R gv[4][3], dv[4][3];
-    if (!tet_grad_eval<R>(D, in, gv, dv)) return;
+    if (!tet_grad_eval<R>(D, in, gv, dv, e)) return;
     if (D.segmented) {
         const int q0 = 4 * e;
         const int n4 = 4 * D.nt;
@@ -845,8 +891,8 @@ __global__ void __launch_bounds__(VB) k_dir(Dev<R> D, int par)
 
 // ------------------------------------------------------------------------------------------ a6-a7: p^T H p, step
 
-// h^2 V [mu |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF]] (Sec. 3.1 with H2 = 2I, H3 the det Hessian)
-// for the direction values P0..P3 of the tet's vertices.
+// h^2 V [2 Psi_2 |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF] + Psi_1 d2I1(F)[dF, dF]] (Sec. 3.1 with
+// H2 = 2I, H3 the det Hessian, H1 the Hessian of tr(S)) for the direction values P0..P3 of the tet's vertices.
 template <typename R>
 __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const typename V4<R>::T &P0,
                                 const typename V4<R>::T &P1, const typename V4<R>::T &P2, const typename V4<R>::T &P3)
@@ -863,11 +909,52 @@ __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const ty
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) dF[a][b] = dp[a][0] * T.w[0][b] + dp[a][1] * T.w[1][b] + dp[a][2] * T.w[2][b];
+    if constexpr (sizeof(R) == 4) {
+        // FP32 form: the second derivative along dF of Psi written in C = F^T F,
+        //   S : dF^T dF + k1 (tr C^-1 E)^2 + k2 tr(C^-1 E C^-1 E),   E = dF^T F + F^T dF,
+        // with S = 2 dPsi/dC, C^-1, k1 = J (Psi_33 J + Psi_3) / 4, k2 = -Psi_3 J / 2 from the gradient pass at
+        // the same x (formed there from the metric change, accurate for small strains).  A direction that rotates
+        // the tet cancels inside E, so the large terms mu |dF|^2 and Psi_3 d2det(F)[dF, dF] of the I2/I3 form,
+        // which cancel for it, never meet in float.
+        const size_t n = (size_t)D.nt;
+        const float4 q0 = __ldcg(D.tS + e), q1 = __ldcg(D.tS + n + e), q2 = __ldcg(D.tS + 2 * n + e);
+        const float4 q3 = __ldcg(D.tS + 3 * n + e);
+        const float S00 = q0.x, S01 = q0.y, S02 = q0.z, S11 = q0.w, S12 = q1.x, S22 = q1.y;
+        const float C00 = q1.z, C01 = q1.w, C02 = q2.x, C11 = q2.y, C12 = q2.z, C22 = q2.w;
+        const float k1 = q3.x, k2 = q3.y;
+        float E[3][3], DD[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                float fe = 0.0f, dd = 0.0f;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    fe += dF[r][a] * T.F[r][b] + T.F[r][a] * dF[r][b];
+                    dd += dF[r][a] * dF[r][b];
+                }
+                E[a][b] = E[b][a] = fe;
+                DD[a][b] = DD[b][a] = dd;
+            }
+        const float Ci[3][3] = {{C00, C01, C02}, {C01, C11, C12}, {C02, C12, C22}};
+        float X[3][3];   // C^-1 E
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) X[a][b] = Ci[a][0] * E[0][b] + Ci[a][1] * E[1][b] + Ci[a][2] * E[2][b];
+        const float trX = X[0][0] + X[1][1] + X[2][2];
+        float trX2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) trX2 += X[a][b] * X[b][a];
+        const float SD = S00 * DD[0][0] + S11 * DD[1][1] + S22 * DD[2][2] +
+                         2.0f * (S01 * DD[0][1] + S02 * DD[0][2] + S12 * DD[1][2]);
+        return D.hv[e] * (SD + k1 * trX * trX + k2 * trX2);
+    }
     R mu, lam;
     tet_material<R>(D, e, mu, lam);
-    const R L = log(T.J);
-    const R Psi3 = (lam * L - mu) / T.J;
-    const R Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
+    const MatTerms<R> mt = mat_terms<R>(D.model, mu, lam, T.J);
     R n2 = 0, g3 = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -879,7 +966,15 @@ __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const ty
     v3<R> d0 = mkv(dF[0][0], dF[1][0], dF[2][0]), d1 = mkv(dF[0][1], dF[1][1], dF[2][1]),
           d2 = mkv(dF[0][2], dF[1][2], dF[2][2]);
     const R h3 = R(2) * (dot(d0, cross(d1, f2)) + dot(d0, cross(f1, d2)) + dot(f0, cross(d1, d2)));
-    return D.hv[e] * (mu * n2 + Psi33 * g3 * g3 + Psi3 * h3);
+    R q = mt.c2 * n2 + mt.Psi33 * g3 * g3 + mt.Psi3 * h3;
+    if constexpr (sizeof(R) == 8) {
+        if (mt.Psi1 != R(0)) {
+            Polar pol;
+            polar_of(T.F, pol);
+            q += mt.Psi1 * polar_h1(pol, dF);
+        }
+    }
+    return D.hv[e] * q;
 }
 
 template <typename R>
@@ -1063,8 +1158,13 @@ __global__ void __launch_bounds__(EB) k_energy(Dev<R> D, int ntb, int nvb)
             else {
                 double mu = D.mu, lam = D.lam;
                 if (D.escale) { mu *= D.escale[e]; lam *= D.escale[e]; }
-                const double L = log(J);
-                s[1] = double(D.hv[e]) * (0.5 * mu * (I2 - 3.0) - mu * L + 0.5 * lam * L * L);
+                double I1 = 3.0;
+                if (D.model == MAT_FCR || D.model == MAT_ARAP) {
+                    Polar pol;
+                    polar_of(T.F, pol);
+                    I1 = pol.trS;
+                }
+                s[1] = double(D.hv[e]) * mat_psi(D.model, mu, lam, I1, I2, J);
             }
         }
     } else if (b < ntb + nvb) {

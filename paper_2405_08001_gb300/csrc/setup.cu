@@ -120,8 +120,14 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }
+    if (mat->model < SIM_MAT_NH || mat->model > SIM_MAT_ARAP) { err = "unknown material model"; return SIM_ERR_INVALID_ARG; }
+    if ((mat->model == SIM_MAT_FCR || mat->model == SIM_MAT_ARAP) && opt.precision == SIM_FP32_MIXED) {
+        err = "the corotated densities (FCR, ARAP) run in the FP64 form";
+        return SIM_ERR_INVALID_ARG;
+    }
     const int nv = mesh->n_verts, nt = mesh->n_tets;
     m.nv = nv; m.nt = nt; m.h = dt; m.dhat = dhat; m.kappa = kappa; m.opt = opt;
+    m.model = mat->model;
     const double nu = mat->poisson;
     const double Eb = mat->youngs_per_tet ? 1.0 : mat->youngs;
     m.nu = nu;

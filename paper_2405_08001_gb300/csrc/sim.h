@@ -16,6 +16,7 @@ namespace pncg {
 struct HostMesh {
     int nv = 0, nt = 0, nf = 0, ne = 0, ns = 0, nfix = 0;
     double h = 0, dhat = 0, kappa = 0, mu = 0, lam = 0;
+    int model = 0;   // energy density (SIM_MAT_*)
     double nu = 0;                         // Poisson ratio
     sim_options opt;
     std::vector<double> X, x0, v0;         // [nv][3] rest, initial positions and velocities

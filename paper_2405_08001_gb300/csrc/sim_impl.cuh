@@ -632,6 +632,7 @@ public:
     {
         CK(cudaSetDevice(dev));
         if (!x || !v || !out) return fail(SIM_ERR_INVALID_ARG, "x, v and out are required");
+        if (M.model != SIM_MAT_NH) return fail(SIM_ERR_INVALID_ARG, "the Hessian-vector product supports Neo-Hookean only");
         sim_status r = adj_alloc();
         if (r) return r;
         r = eval_setup(x, nullptr);
@@ -650,6 +651,7 @@ public:
         CK(cudaSetDevice(dev));
         if (!x1 || !ax1 || !av1 || !ax0 || !av0 || max_iters <= 0 || !(tol > 0))
             return fail(SIM_ERR_INVALID_ARG, "x1, the adjoints and a positive tolerance and iteration cap are required");
+        if (M.model != SIM_MAT_NH) return fail(SIM_ERR_INVALID_ARG, "the adjoint step supports Neo-Hookean only");
         sim_status r = adj_alloc();
         if (r) return r;
         r = eval_setup(x1, nullptr);   // H at x_{t+1}: candidates, active pairs and the gradient pass there
@@ -831,6 +833,7 @@ private:
         AL(D.g[0], nv); AL(D.g[1], nv); AL(D.dg[0], nv); AL(D.dg[1], nv); AL(D.p, nv);
         D.xh = D.xl = nullptr;
         D.G0 = nullptr;
+        D.tS = nullptr;
         D.xbh = nullptr;
         D.pg = D.pnext = nullptr;
         if (sizeof(R) == 4) {
@@ -838,6 +841,7 @@ private:
             float *g0;
             AL(g0, 12 * (size_t)nt);
             D.G0 = g0;
+            AL(D.tS, 4 * (size_t)nt);
         }
         double *mass; AL(mass, nv); D.mass = mass;
         int *fs; AL(fs, nv); D.fix_slot = fs;
@@ -848,7 +852,7 @@ private:
         R *es = nullptr;
         if (!M.escale.empty()) AL(es, nt);
         D.escale = es;
-        D.mu = R(M.mu); D.lam = R(M.lam);
+        D.mu = R(M.mu); D.lam = R(M.lam); D.model = M.model;
         D.h = M.h; D.dhat = M.dhat; D.kappa = M.kappa; D.eps = M.opt.eps;
         // default candidate slack: r = 0.5 L - dhat (L the mean surface edge at rest) within [2, 6] dhat, so that
         // dhat + r stays below about half an edge and the candidates stay near neighbours; 6 dhat measured the

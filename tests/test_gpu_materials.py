@@ -1,0 +1,116 @@
+"""GPU parity of the other energy densities (Sec. 3.1 invariants; sim_material.model): stable Neo-Hookean in both
+forms, fixed corotated and as-rigid-as-possible in the FP64 form, against the oracle of the same model.  The
+library forms the I1 terms from a Newton polar iteration and the axial form of d2 tr(S); the oracle from the
+twist modes of an SVD, so the two derivations check each other.  Evaluation at a rotated, sheared and noisy state
+with contacts, then lock-step iterations of a contact step, at the single-scene tolerances."""
+import numpy as np
+import pytest
+
+from paper_2405_08001_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-5}
+CASES = [(1, 0), (1, 1), (2, 0), (3, 0)]   # (model, precision): SNH both forms, FCR and ARAP in FP64
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2405_08001_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def deformed_blocks(seed):
+    """The two-block scene with the upper block's rest shape sheared and rotated against its current one, so that
+    F is far from a rotation (R != I, the twist modes excited) while the blocks touch."""
+    sc = S.two_blocks(seed)
+    rng = np.random.default_rng(seed + 50)
+    na = S.kuhn_grid(3, 3, 3)[0].shape[0]
+    A = np.array([[1.0, 0.15, 0.0], [0.0, 1.0, 0.1], [0.05, 0.0, 1.0]])
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    Q = Q if np.linalg.det(Q) > 0 else -Q
+    up = sc.rest_x[na:]
+    c = up.mean(0)
+    sc.rest_x = sc.rest_x.copy()
+    sc.rest_x[na:] = (up - c) @ (Q @ A).T + c   # rest shape of the upper block: sheared and rotated
+    return sc
+
+
+@pytest.mark.parametrize("model,prec", CASES)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_diag_pHp_energy(B, O, model, prec, seed):
+    sc = deformed_blocks(seed)
+    sim = B.Sim(sc, precision=prec, model=model)
+    o = O.Oracle.from_scene(sc, model=model)
+    rng = np.random.default_rng(7)
+    x = sc.x0 + 2e-5 * rng.normal(size=sc.x0.shape)
+    xt = sc.x0 + 1e-4 * rng.normal(size=sc.x0.shape)
+    g, d = B.sim_eval_gradient(sim.h, x, xt)
+    go, do, na = o.grad_diag(x, xt)
+    assert na > 0, "contacts active"
+    assert rel(g, go) < TOL[prec], rel(g, go)
+    assert rel(d, do) < TOL[prec], rel(d, do)
+    for _ in range(2):
+        p = rng.normal(size=x.shape)
+        assert abs(B.sim_eval_pHp(sim.h, x, p) - o.pHp(x, p)) / abs(o.pHp(x, p)) < TOL[prec]
+    E, _ = B.sim_eval_energy(sim.h, x, xt)
+    Eo, _ = O.Oracle.energy(o, x, xt)
+    assert abs(E - Eo) / abs(Eo) < 1e-10
+    sim.close()
+
+
+@pytest.mark.parametrize("model,prec", CASES)
+def test_lockstep_contact_step(B, O, model, prec):
+    sc = deformed_blocks(2)
+    sim = B.Sim(sc, precision=prec, model=model)
+    o = O.Oracle.from_scene(sc, model=model)
+    sim.step(1)
+    B.sim_begin_step(sim.h, None)
+    worst = dict.fromkeys(("g", "P", "p", "pHp", "alpha", "dx"), 0.0)
+    for k in range(sc.iters):
+        x, g, P, p, xt, _ = B.sim_get_iterate(sim.h)
+        xo, go, Po, po = x.copy(), g.copy(), P.copy(), p.copy()
+        o.iteration(xo, xt, go, Po, po, k)
+        B.sim_iterate(sim.h, 1)
+        x1, g1, P1, p1, _, s1 = B.sim_get_iterate(sim.h)
+        pd = O.ncg_direction(g1, P1, g, P, p, k, 0)[0]
+        pHp_ref = o.pHp(x, p1)
+        a_ref = O.ncg_alpha(s1["gp"], s1["pHp"], s1["pmax"], sc.dhat)[0]
+        e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
+                 alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1))
+        for kk in worst:
+            worst[kk] = max(worst[kk], e[kk])
+    B.sim_end_step(sim.h)
+    sim.close()
+    for kk, v in worst.items():
+        assert v < TOL[prec], (kk, {q: f"{w:.3e}" for q, w in worst.items()})
+
+
+def test_unsupported_combinations_are_rejected(B):
+    sc = S.two_blocks(0)
+    for model in (2, 3):
+        with pytest.raises(B.SimError) as ei:
+            B.Sim(sc, precision=1, model=model)
+        assert ei.value.status == B.SIM_ERR_INVALID_ARG
+    with pytest.raises(B.SimError) as ei:
+        B.Sim(sc, precision=0, model=4)
+    assert ei.value.status == B.SIM_ERR_INVALID_ARG
+    sim = B.Sim(sc, precision=0, model=1)
+    with pytest.raises(B.SimError) as ei:
+        B.sim_eval_hvp(sim.h, sc.x0, np.ones_like(sc.x0))
+    assert ei.value.status == B.SIM_ERR_INVALID_ARG
+    sim.close()
