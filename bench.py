@@ -41,6 +41,25 @@ def rank_info():
     return ws, rank, local
 
 
+def max_over_ranks(value: float) -> float:
+    """The largest of every rank's value (the whole job's time is its slowest rank's); the value itself without a
+    process group.  NCCL reduces a device tensor, gloo a host one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, K: int, iters: int, total_ms: float) -> float:
+    """Whole-job NCG iterations per second: each of the ws ranks advances its own replica by K time steps of
+    `iters` iterations, and the job takes total_ms (the slowest rank's time)."""
+    return ws * K * iters / (total_ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -238,12 +257,8 @@ def run_ours(args):
         return sim, times, st
 
     sim32, t32, st32 = one_form(B.SIM_FP32_MIXED, K)
-    total_ms = sum(t32)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * K * iters / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(t32))
+    value = job_value(ws, K, iters, total_ms)
 
     # kernel-by-kernel GPU times of three more steps (after the timed region) for the roofline; they continue the
     # run from the state the timed window left
