@@ -139,3 +139,34 @@ def test_update_is_each_objects_own_step(oracle_mod):
             a = min(au, -gp / sp[ob]["pHp"]) if sp[ob]["pHp"] > 0 else au   # p^T H p <= 0: the cap alone
             assert sp[ob]["alpha"] == pytest.approx(a, rel=1e-14)
             np.testing.assert_allclose(x[sl] - xk[sl], a * p[sl], rtol=1e-9, atol=1e-14 * np.abs(xk[sl]).max())
+
+
+def test_split_step_runs_the_iterations_and_stops_objects_under_eps(oracle_mod):
+    """step_split: iters iterations without the eps rule; with it, an object whose Delta E fell below eps Delta E_0
+    takes no further step, and the step ends when every object has stopped.  v = (x - x^t) / h."""
+    sc = S.objects(0)
+    o = oracle_mod.Oracle.from_scene(sc)
+    off = _offsets(sc)
+    x, v = sc.x0.copy(), sc.v0.copy()
+    assert o.step_split(x, v, off, iters=9) == 9
+    np.testing.assert_allclose(v, (x - sc.x0) / sc.dt, rtol=1e-14, atol=1e-300)
+    # the same step by hand, with the eps rule: the iterations, the objects that stop and where
+    x1, v1 = sc.x0.copy(), sc.v0.copy()
+    done = o.step_split(x1, v1, off, iters=200, eps=1e-2)
+    x2 = sc.x0.copy()
+    xt = o.predict(x2, sc.v0, None)
+    g, P, p = np.zeros_like(x2), np.zeros_like(x2), np.zeros_like(x2)
+    state, moving, k, stops = [None] * 3, np.ones(3, np.int32), 0, {}
+    while k < 200 and moving.any():
+        before = x2.copy()
+        sp = o.iteration_split(x2, xt, g, P, p, off, state, moving)
+        k += 1
+        for ob in range(3):
+            sl = slice(off[ob], off[ob + 1])
+            if not moving[ob]:
+                np.testing.assert_array_equal(x2[sl], before[sl])   # a stopped object stays put
+            elif sp[ob]["dE"] < 1e-2 * sp[ob]["dE0"]:
+                moving[ob] = 0
+                stops[ob] = k
+    assert done == k and len(stops) == 3 and len(set(stops.values())) > 1   # the objects stop at different iterations
+    np.testing.assert_array_equal(x1, x2)
