@@ -113,6 +113,21 @@ def test_inertia_only_converges_in_one_iteration(oracle_mod):
     np.testing.assert_allclose(P, 1.0 / np.repeat(o.mass()[:, None], 3, axis=1), rtol=1e-15)
 
 
+def test_free_fall_time_step_is_implicit_euler(oracle_mod):
+    """A whole time step (or_step) without stiffness or contact: implicit Euler under gravity in closed form,
+    x1 = x0 + h v0 + h^2 g and v1 = v0 + h g."""
+    sc = S.cube_drop(n=3)
+    o = oracle_mod.Oracle(sc.rest_x, sc.tets, youngs=0.0, poisson=0.3, density=1000.0, dt=sc.dt, dhat=10.0,
+                          kappa=0.0, gravity=sc.gravity)
+    x0 = sc.x0.copy()
+    v0 = np.tile(np.array([0.3, -0.2, 0.5]), (sc.n_verts, 1))   # a rigid translation: no tet deforms
+    x, v = x0.copy(), v0.copy()
+    o.step(x, v, None, iters=3)
+    gv = np.array(sc.gravity)
+    np.testing.assert_allclose(x, x0 + sc.dt * v0 + sc.dt ** 2 * gv, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(v, v0 + sc.dt * gv, rtol=0, atol=1e-12)
+
+
 def test_step_equals_repeated_iterations_and_kinematic_targets(oracle_mod):
     sc = S.twisted_bar(nx=2, ny=2, nz=6, size=(0.02, 0.02, 0.06), dhat=1e-3)
     o = oracle_mod.Oracle.from_scene(sc)
