@@ -105,6 +105,14 @@ def test_distance_closed_forms(oracle_mod):
     x = np.array([[0, 0, 0], [1, 0, 0], [0.5, 0.3, 0], [2, 0.3, 0]], float)
     d, c, t = oracle_mod.pair_geometry(1, x)
     assert d == pytest.approx(0.3, rel=1e-14)
+    # nearly parallel segments crossing over each other at their midpoints (angles of 1 degree and 0.01 degree):
+    # interior closest points, d = the height; no endpoint comes that close
+    for ang in (np.radians(1.0), np.radians(0.01)):
+        dy = np.tan(ang)
+        x = np.array([[-1, 0, 0], [1, 0, 0], [-1, -dy, 0.02], [1, dy, 0.02]], float)
+        d, c, t = oracle_mod.pair_geometry(1, x)
+        assert d == pytest.approx(0.02, rel=1e-12)
+        np.testing.assert_allclose(c, [0.5, 0.5, -0.5, -0.5], atol=1e-9)
 
 
 def _two_block_oracle(oracle_mod, seed, **kw):
