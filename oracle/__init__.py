@@ -84,6 +84,8 @@ def _load():
             "or_ncg_alpha": (None, [D, D, D, D, P]),
             "or_iteration": (C.c_int, [P, P, P, P, P, P, P]),
             "or_iteration_split": (C.c_int, [P, I32, P, P, P, P, P, P, P, P]),
+            "or_iteration_groups": (C.c_int, [P, I32, P, P, P, P, P, P, P, P]),
+            "or_contact_vertices": (C.c_int, [P, P, P]),
             "or_step": (C.c_int, [P, P, P, P, I32, D, P, P]),
             "or_predict": (None, [P, P, P, P, P]),
             "or_intersections": (I32, [P, P]),
@@ -288,6 +290,57 @@ class Oracle:
         for o in range(nobj):
             state[o] = {"k": out[o]["k"], "dE0": out[o]["dE0"]}
         return out
+
+    def iteration_groups(self, x, xtilde, g, P, p, group, state, moving=None):
+        """One PNCG iteration with splitting over arbitrary vertex groups (Sec. 5.2): group[i] in 0..G-1 for each
+        vertex; state and moving as in iteration_split.  Returns the per-group scalars."""
+        for a in (x, g, P, p):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        grp = np.ascontiguousarray(group, dtype=np.int32)
+        ng = int(grp.max()) + 1
+        ss = (_Scalars * ng)()
+        for q in range(ng):
+            st = state[q] or {}
+            ss[q].k, ss[q].dE0 = int(st.get("k", 0)), float(st.get("dE0", 0.0))
+        mv = None if moving is None else np.ascontiguousarray(moving, dtype=np.int32)
+        _check(_load().or_iteration_groups(self._m, ng, _ptr(grp), _ptr(mv), _ptr(x), _ptr(_f64(xtilde)), _ptr(g),
+                                           _ptr(P), _ptr(p), ss))
+        out = [{f: getattr(ss[q], f) for f, _ in _Scalars._fields_} for q in range(ng)]
+        for q in range(ng):
+            state[q] = {"k": out[q]["k"], "dE0": out[q]["dE0"]}
+        return out
+
+    def contact_vertices(self, x):
+        """1 for the vertices of the active pairs and those within dhat of the plane at x, else 0."""
+        mark = np.zeros(self.nv, np.int32)
+        _check(_load().or_contact_vertices(self._m, _ptr(_f64(x)), _ptr(mark)))
+        return mark
+
+    def step_parts(self, x, v, obj, targets=None, iters=50, eps=0.0):
+        """One time step with every object split into its collision and non-collision parts (Sec. 5.2), in place on
+        x and v: after the prediction and the kinematic targets, the vertices in contact at x_0 form each object's
+        collision part; the parts then iterate as the groups of iteration_groups (eps rule per part).  obj: the
+        object of each vertex.  Returns (iterations done, group labels)."""
+        xt = self.predict(x, v, targets)
+        x0 = x.copy()
+        if targets is not None and self.fixed is not None:
+            x[self.fixed.astype(bool)] = _f64(targets).reshape(-1, 3)
+        raw = 2 * np.asarray(obj, dtype=np.int64) + self.contact_vertices(x)
+        _, group = np.unique(raw, return_inverse=True)
+        group = group.astype(np.int32)
+        ng = int(group.max()) + 1
+        g, P, p = np.zeros_like(x), np.zeros_like(x), np.zeros_like(x)
+        state, moving = [None] * ng, np.ones(ng, dtype=np.int32)
+        k = 0
+        while k < iters and moving.any():
+            sc = self.iteration_groups(x, xt, g, P, p, group, state, moving)
+            k += 1
+            if eps > 0.0:
+                for q in range(ng):
+                    if moving[q] and sc[q]["dE"] < eps * sc[q]["dE0"]:
+                        moving[q] = 0
+        v[:] = (x - x0) / self.dt
+        return k, group
 
     def step_split(self, x, v, off, targets=None, iters=50, eps=0.0):
         """One time step with per-object splitting, in place on x and v: the prediction and kinematic targets of

@@ -1159,60 +1159,113 @@ int or_iteration(const or_model *m, double *x, const double *xtilde, double *g, 
 }
 
 /*
- * One iteration with per-object splitting (Sec. 5.2): the vertices form nobj objects, object o the contiguous range
- * off[o] .. off[o+1]-1.  Gradient and preconditioner are those of the whole scene (pairs between two objects
- * included).  Each object then takes its own beta and direction over its own entries (Sec. 4.1-4.2), its own max
- * |p_v|, and its own step along p_o, which is p with every other object's entries zero: alpha_o = min(dhat /
- * (2 max |p_v|), -g^T p_o / p_o^T H p_o) (Sec. 4.3), i.e. the step of the quadratic model of E along p_o with the
- * other objects held still.  All p_o^T H p_o are taken at x_k before any object moves.  moving (nullable): objects
- * with moving[o] = 0 (converged under the eps rule) keep their direction but take no step.  s: nobj scalars, each
- * with its own k and dE0.
+ * One iteration with splitting (Sec. 5.2) over ngroups vertex groups, group[i] in 0 .. ngroups-1 for vertex i (a
+ * group need not be contiguous: an object, or the collision or non-collision part of one).  Gradient and
+ * preconditioner are those of the whole scene (pairs between groups included).  Each group then takes its own beta
+ * and direction over its own entries (in vertex order; Sec. 4.1-4.2), its own max |p_v|, and its own step along
+ * p_G, which is p with every other group's entries zero: alpha_G = min(dhat / (2 max |p_v|), -g^T p_G / p_G^T H p_G)
+ * (Sec. 4.3), i.e. the step of the quadratic model of E along p_G with the other groups held still.  All p_G^T H p_G
+ * are taken at x_k before any group moves.  moving (nullable): groups with moving[G] = 0 (converged under the eps
+ * rule) keep their direction but take no step.  s: ngroups scalars, each with its own k and dE0.
  */
-int or_iteration_split(const or_model *m, int32_t nobj, const int32_t *off, const int32_t *moving, double *x,
-                       const double *xtilde, double *g, double *P, double *p, or_ncg_scalars *s)
+int or_iteration_groups(const or_model *m, int32_t ngroups, const int32_t *group, const int32_t *moving, double *x,
+                        const double *xtilde, double *g, double *P, double *p, or_ncg_scalars *s)
 {
     int32_t nv = m->p.nv;
     size_t n = 3 * (size_t)nv;
-    if (nobj < 1 || off[0] != 0 || off[nobj] != nv) { set_err("object ranges must cover the vertices"); return OR_ERR_ARG; }
-    for (int32_t o = 0; o < nobj; ++o)
-        if (off[o + 1] < off[o]) { set_err("object ranges must be non-decreasing"); return OR_ERR_ARG; }
+    if (ngroups < 1) { set_err("at least one group"); return OR_ERR_ARG; }
+    for (int32_t i = 0; i < nv; ++i)
+        if (group[i] < 0 || group[i] >= ngroups) { set_err("group label out of range"); return OR_ERR_ARG; }
     double *g1 = malloc(sizeof(double) * n), *d1 = malloc(sizeof(double) * n), *P1 = malloc(sizeof(double) * n);
-    double *po = calloc(n, sizeof(double)), *al = malloc(sizeof(double) * 5 * (size_t)nobj);
-    if (!g1 || !d1 || !P1 || !po || !al) { free(g1); free(d1); free(P1); free(po); free(al); return OR_ERR_OOM; }
+    double *po = calloc(n, sizeof(double)), *al = malloc(sizeof(double) * 5 * (size_t)ngroups);
+    double *t = malloc(sizeof(double) * 5 * n);   /* a group's entries gathered: g1, P1, g, P, p */
+    int32_t *idx = malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    if (!g1 || !d1 || !P1 || !po || !al || !t || !idx) {
+        free(g1); free(d1); free(P1); free(po); free(al); free(t); free(idx);
+        return OR_ERR_OOM;
+    }
     int32_t nact = 0;
     int st = or_grad_diag(m, x, xtilde, g1, d1, &nact);
     if (st) goto done;
     jacobi(m, g1, d1, P1);
     int32_t nplane = count_plane(m, x);
-    for (int32_t o = 0; o < nobj; ++o) {
-        size_t q0 = 3 * (size_t)off[o];
-        int32_t no = 3 * (off[o + 1] - off[o]);
-        or_ncg_direction(no, g1 + q0, P1 + q0, g + q0, P + q0, p + q0, s[o].k, m->p.beta_rule, &s[o].beta, &s[o].gp,
-                         &s[o].restarted);
-        s[o].pmax = or_pmax(off[o + 1] - off[o], p + q0, m->p.pnorm);
+    for (int32_t G = 0; G < ngroups; ++G) {
+        int32_t nq = 0;
+        for (int32_t i = 0; i < nv; ++i) if (group[i] == G) idx[nq++] = i;
+        double *tg1 = t, *tP1 = t + n, *tg = t + 2 * n, *tP = t + 3 * n, *tp = t + 4 * n;
+        for (int32_t j = 0; j < nq; ++j)
+            for (int a = 0; a < 3; ++a) {
+                size_t q = 3 * (size_t)idx[j] + a, r = 3 * (size_t)j + a;
+                tg1[r] = g1[q]; tP1[r] = P1[q]; tg[r] = g[q]; tP[r] = P[q]; tp[r] = p[q];
+            }
+        or_ncg_direction(3 * nq, tg1, tP1, tg, tP, tp, s[G].k, m->p.beta_rule, &s[G].beta, &s[G].gp, &s[G].restarted);
+        s[G].pmax = or_pmax(nq, tp, m->p.pnorm);
+        for (int32_t j = 0; j < nq; ++j)
+            for (int a = 0; a < 3; ++a) p[3 * (size_t)idx[j] + a] = tp[3 * (size_t)j + a];
     }
-    for (int32_t o = 0; o < nobj; ++o) {
-        size_t q0 = 3 * (size_t)off[o], q1 = 3 * (size_t)off[o + 1];
-        memset(po, 0, sizeof(double) * n);
-        memcpy(po + q0, p + q0, sizeof(double) * (q1 - q0));
-        st = or_pHp(m, x, po, &s[o].pHp);
+    for (int32_t G = 0; G < ngroups; ++G) {
+        for (int32_t i = 0; i < nv; ++i)
+            for (int a = 0; a < 3; ++a) po[3 * (size_t)i + a] = group[i] == G ? p[3 * (size_t)i + a] : 0.0;
+        st = or_pHp(m, x, po, &s[G].pHp);
         if (st) goto done;
-        or_ncg_alpha(s[o].gp, s[o].pHp, s[o].pmax, m->p.dhat, al + 5 * (size_t)o);
+        or_ncg_alpha(s[G].gp, s[G].pHp, s[G].pmax, m->p.dhat, al + 5 * (size_t)G);
     }
-    for (int32_t o = 0; o < nobj; ++o) {
-        const double *a = al + 5 * (size_t)o;
-        double step = (moving && !moving[o]) ? 0.0 : a[0];
-        for (size_t q = 3 * (size_t)off[o]; q < 3 * (size_t)off[o + 1]; ++q) x[q] += step * p[q];
-        s[o].alpha = step; s[o].alpha_bar = a[1]; s[o].alpha_up = a[2]; s[o].dE = a[3]; s[o].capped = (int32_t)a[4];
-        s[o].n_active = nact; s[o].n_plane = nplane;
-        if (s[o].k == 0) s[o].dE0 = s[o].dE;
-        s[o].k += 1;
+    for (int32_t G = 0; G < ngroups; ++G) {
+        const double *a = al + 5 * (size_t)G;
+        double step = (moving && !moving[G]) ? 0.0 : a[0];
+        for (int32_t i = 0; i < nv; ++i)
+            if (group[i] == G)
+                for (int c = 0; c < 3; ++c) x[3 * (size_t)i + c] += step * p[3 * (size_t)i + c];
+        s[G].alpha = step; s[G].alpha_bar = a[1]; s[G].alpha_up = a[2]; s[G].dE = a[3]; s[G].capped = (int32_t)a[4];
+        s[G].n_active = nact; s[G].n_plane = nplane;
+        if (s[G].k == 0) s[G].dE0 = s[G].dE;
+        s[G].k += 1;
     }
     memcpy(g, g1, sizeof(double) * n);
     memcpy(P, P1, sizeof(double) * n);
 done:
-    free(g1); free(d1); free(P1); free(po); free(al);
+    free(g1); free(d1); free(P1); free(po); free(al); free(t); free(idx);
     return st;
+}
+
+/*
+ * Per-object splitting (Sec. 5.2) with the objects as contiguous vertex ranges off[o] .. off[o+1]-1: the group
+ * iteration above with group = object.
+ */
+int or_iteration_split(const or_model *m, int32_t nobj, const int32_t *off, const int32_t *moving, double *x,
+                       const double *xtilde, double *g, double *P, double *p, or_ncg_scalars *s)
+{
+    int32_t nv = m->p.nv;
+    if (nobj < 1 || off[0] != 0 || off[nobj] != nv) { set_err("object ranges must cover the vertices"); return OR_ERR_ARG; }
+    for (int32_t o = 0; o < nobj; ++o)
+        if (off[o + 1] < off[o]) { set_err("object ranges must be non-decreasing"); return OR_ERR_ARG; }
+    int32_t *group = malloc(sizeof(int32_t) * (size_t)nv);
+    if (!group) return OR_ERR_OOM;
+    for (int32_t o = 0; o < nobj; ++o)
+        for (int32_t i = off[o]; i < off[o + 1]; ++i) group[i] = o;
+    int st = or_iteration_groups(m, nobj, group, moving, x, xtilde, g, P, p, s);
+    free(group);
+    return st;
+}
+
+/*
+ * The vertices in contact at x: mark[i] = 1 for every vertex of a pair of the active set (d < dhat, rest-pose
+ * exclusions applied) and every vertex within dhat of the plane, else 0.  The collision part of an object for
+ * the split of Sec. 5.2.
+ */
+int or_contact_vertices(const or_model *m, const double *x, int32_t *mark)
+{
+    for (int32_t i = 0; i < m->p.nv; ++i) mark[i] = 0;
+    pair_list L = {0};
+    int st = find_pairs(m, x, m->p.dhat, 1, 0, &L);
+    if (st) { free(L.v); return st; }
+    for (int32_t k = 0; k < L.n; ++k)
+        for (int i = 0; i < 4; ++i) mark[L.v[k].v[i]] = 1;
+    free(L.v);
+    if (m->p.has_plane)
+        for (int32_t i = 0; i < m->p.nv; ++i)
+            if (dot3(m->plane_n, x + 3 * (size_t)i) - m->p.plane_o < m->p.dhat) mark[i] = 1;
+    return OR_OK;
 }
 
 /*

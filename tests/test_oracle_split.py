@@ -170,3 +170,91 @@ def test_split_step_runs_the_iterations_and_stops_objects_under_eps(oracle_mod):
                 stops[ob] = k
     assert done == k and len(stops) == 3 and len(set(stops.values())) > 1   # the objects stop at different iterations
     np.testing.assert_array_equal(x1, x2)
+
+
+def test_group_labels_are_names_only(oracle_mod):
+    """Non-contiguous groups: renaming the labels changes nothing (bit for bit)."""
+    sc = S.objects(1)
+    o = oracle_mod.Oracle.from_scene(sc)
+    rng = np.random.default_rng(3)
+    lab = rng.integers(0, 3, size=sc.n_verts).astype(np.int32)
+    perm = np.array([2, 0, 1], np.int32)
+    x, xt, g, P, p = _start(o, sc)
+    y, h, Q, q = x.copy(), g.copy(), P.copy(), p.copy()
+    s1, s2 = [None] * 3, [None] * 3
+    for k in range(5):
+        a = o.iteration_groups(x, xt, g, P, p, lab, s1)
+        b = o.iteration_groups(y, xt, h, Q, q, perm[lab], s2)
+        for G in range(3):
+            assert a[G]["alpha"] == b[perm[G]]["alpha"] and a[G]["pHp"] == b[perm[G]]["pHp"]
+        np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(p, q)
+
+
+def test_part_pHp_is_the_masked_elastic_form(oracle_mod):
+    """One deformed block split into two parts across its tets (no contact): each part's p_S^T H p_S equals the
+    quadratic form of p_S (zero outside the part) with the mass matrix plus the Hessian assembled by central
+    differences of the gradient -- tets spanning both parts contribute to each with the other's entries zero."""
+    X, T = S.kuhn_grid(2, 2, 2, size=(0.02, 0.02, 0.02))
+    o = oracle_mod.Oracle(X, T, youngs=1e5, poisson=0.4, density=1000.0, dt=0.02, dhat=1e-9, kappa=0.0,
+                          excl_factor=0.0)
+    rng = np.random.default_rng(8)
+    x = X + 1.5e-3 * rng.normal(size=X.shape)
+    xt = x + 1e-3 * rng.normal(size=X.shape)
+    part = (X[:, 2] > 0.011).astype(np.int32)                 # upper layer against the rest
+    g, P, p = np.zeros_like(x), np.zeros_like(x), np.zeros_like(x)
+    xk = x.copy()
+    sp = o.iteration_groups(x, xt, g, P, p, part, [None] * 2)
+    n = x.size
+    H = np.zeros((n, n))
+    eps = 1e-7
+    for i in range(n):
+        e = np.zeros(n); e[i] = eps
+        H[:, i] = (o.grad_diag(xk + e.reshape(x.shape), xt)[0] - o.grad_diag(xk - e.reshape(x.shape), xt)[0]).ravel() / (2 * eps)
+    H = 0.5 * (H + H.T)
+    for G in range(2):
+        pg = np.where((part == G)[:, None], p, 0.0).ravel()
+        assert sp[G]["pHp"] == pytest.approx(pg @ H @ pg, rel=1e-6), G
+    pf = p.ravel()
+    assert abs(pf @ H @ pf - sp[0]["pHp"] - sp[1]["pHp"]) > 1e-3 * abs(pf @ H @ pf)   # the cross terms are left out
+
+
+def test_contact_vertices_are_those_of_the_active_set(oracle_mod):
+    sc = S.two_blocks(2)
+    o = oracle_mod.Oracle.from_scene(sc)
+    x = sc.x0.copy()
+    x[:, 2] += 0.5 * sc.dhat - x[:, 2].min()                  # the lowest vertex within dhat of the plane
+    mark = o.contact_vertices(x)
+    idx = o.active_pairs(x)[0]
+    want = np.zeros(sc.n_verts, np.int32)
+    want[np.unique(idx[:, 1:].ravel())] = 1
+    n, off = sc.plane
+    want[(x @ np.asarray(n)) - off < sc.dhat] = 1
+    assert len(idx) > 0 and want.sum() > len(np.unique(idx[:, 1:].ravel()))
+    np.testing.assert_array_equal(mark, want)
+
+
+def test_step_with_collision_and_free_parts(oracle_mod):
+    """Two touching blocks, each split into its collision part (the vertices in contact at x_0) and the rest: four
+    groups; a free part steps further than the collision part of its object; v = (x - x^t) / h."""
+    sc = S.two_blocks(0)
+    o = oracle_mod.Oracle.from_scene(sc)
+    obj = np.concatenate([np.zeros(S.kuhn_grid(3, 3, 3)[0].shape[0], np.int32),
+                          np.ones(sc.n_verts - S.kuhn_grid(3, 3, 3)[0].shape[0], np.int32)])
+    x, v = sc.x0.copy(), sc.v0.copy()
+    k, group = o.step_parts(x, v, obj, iters=6)
+    assert k == 6 and group.max() + 1 == 4
+    np.testing.assert_allclose(v, (x - sc.x0) / sc.dt, rtol=1e-14, atol=1e-300)
+    # one more iteration by hand from a fresh step: the parts' steps
+    x2, v2 = x.copy(), v.copy()
+    xt = o.predict(x2, v2, None)
+    mark = o.contact_vertices(x2)
+    raw = 2 * obj + mark
+    _, grp = np.unique(raw, return_inverse=True)
+    g, P, p = np.zeros_like(x2), np.zeros_like(x2), np.zeros_like(x2)
+    sp = o.iteration_groups(x2, xt, g, P, p, grp.astype(np.int32), [None] * (grp.max() + 1))
+    names = np.unique(raw)
+    for ob in (0, 1):
+        if 2 * ob + 1 in names:
+            free, coll = sp[list(names).index(2 * ob)], sp[list(names).index(2 * ob + 1)]
+            assert free["alpha"] > coll["alpha"]
