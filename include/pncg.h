@@ -304,8 +304,18 @@ sim_status sim_get_sizes(sim_handle h, int32_t *out);
 /* Releases the handle and its device buffers (synchronises its stream first).  NULL is ignored. */
 void sim_destroy(sim_handle h);
 
-/* One-line description of the last failure of h (or of the last failed sim_create when h is NULL). */
+/* One-line description of the last failure of h (or of the last failed sim_create or sim_selftest_wait when h is
+   NULL). */
 const char *sim_last_error(sim_handle h);
+
+/*
+ * Failure-detection self-test (no handle).  Runs one bounded device wait that nothing completes: a one-block kernel
+ * arrives at a counter that expects two arrivals and polls it with the grid barriers' wait, whose limit is limit_s
+ * seconds here (0 < limit_s <= 4) instead of 4 s.  Returns SIM_ERR_TIMEOUT, the expected outcome, after about
+ * limit_s, and leaves the context usable; SIM_ERR_INVALID_ARG for a limit out of range; SIM_ERR_CUDA without a
+ * device.  sim_last_error(NULL) describes the outcome.
+ */
+sim_status sim_selftest_wait(double limit_s);
 
 /* Name of a status code. */
 const char *sim_status_string(sim_status s);

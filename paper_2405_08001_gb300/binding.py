@@ -111,6 +111,7 @@ def load():
         "sim_get_sizes": (C.c_int, [P, P]),
         "sim_destroy": (None, [P]),
         "sim_last_error": (C.c_char_p, [P]),
+        "sim_selftest_wait": (C.c_int, [D]),
         "sim_pHp_noalloc": (C.c_int, [I32, I32, P, P, P, P, P, D, D, D, P, P]),
         "sim_noalloc_last_error": (C.c_char_p, []),
     }
@@ -399,6 +400,14 @@ def sim_pHp_noalloc(x, p, rest_x, tets, mass, youngs, poisson, dt, out, stream=N
 
 def sim_noalloc_last_error() -> str:
     return load().sim_noalloc_last_error().decode()
+
+
+def sim_selftest_wait(limit_s: float = 0.05):
+    """The failure-detection self-test (a bounded device wait that nothing completes): (status, message).  The
+    expected status is SIM_ERR_TIMEOUT."""
+    lib = load()
+    st = lib.sim_selftest_wait(float(limit_s))
+    return st, lib.sim_last_error(None).decode()
 
 
 def sim_destroy(h):

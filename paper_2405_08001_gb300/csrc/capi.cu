@@ -248,6 +248,11 @@ void sim_destroy(sim_handle h)
     delete h;
 }
 
+sim_status sim_selftest_wait(double limit_s)
+{
+    return pncg::wait_selftest(limit_s, g_create_err);
+}
+
 const char *sim_last_error(sim_handle h)
 {
     if (!h || !h->impl) return g_create_err.c_str();

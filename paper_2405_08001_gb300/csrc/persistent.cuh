@@ -55,6 +55,25 @@ __device__ inline unsigned long long global_ns()
     return t;
 }
 
+// Polls *count until it reaches target.  Every 32 polls it reads the global nanosecond timer: once limit_ns have
+// passed since the first reading it sets ERR_TIMEOUT in *err and gives up, and it also gives up at once when
+// another waiter has set that bit.  Returns false when it gave up.
+__device__ inline bool wait_count(const unsigned int *count, unsigned int target, uint32_t *err,
+                                  unsigned long long limit_ns)
+{
+    unsigned long long t0 = 0;
+    int n = 0;
+    while ((int)(ld_relaxed(count) - target) < 0) {
+        if ((++n & 31) == 0) {
+            if (*(volatile uint32_t *)err & ERR_TIMEOUT) return false;
+            const unsigned long long t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) { atomicOr(err, ERR_TIMEOUT); return false; }
+        }
+    }
+    return true;
+}
+
 // The block's writes are ordered before its arrival by the CTA barrier and the release add (a release operation is a
 // cumulative fence followed by the add, so no separate fence is needed; the add needs no round trip).  The lead
 // thread polls the counter with relaxed loads and, once it has seen every arrival, orders the block's later reads
@@ -68,16 +87,7 @@ __device__ inline void grid_barrier(Bar &br, Ctrl *c)
         const bool rec = br.arrive && (int)br.n <= br.max;
         if (rec) br.arrive[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();
         red_release_add(br.count, 1u);
-        unsigned long long t0 = 0;
-        int n = 0;
-        while ((int)(ld_relaxed(br.count) - target) < 0) {
-            if ((++n & 31) == 0) {
-                if ((volatile uint32_t &)c->err & ERR_TIMEOUT) break;
-                const unsigned long long t = global_ns();
-                if (t0 == 0) t0 = t;
-                else if (t - t0 > BARRIER_LIMIT_NS) { atomicOr(&c->err, ERR_TIMEOUT); break; }
-            }
-        }
+        wait_count(br.count, target, &c->err, BARRIER_LIMIT_NS);
         fence_acq_rel();
         if (rec) {
             br.depart[(size_t)(br.n - 1) * gridDim.x + blockIdx.x] = global_ns();

@@ -79,6 +79,7 @@ public:
 };
 
 Sim *make_sim_f64();
+sim_status wait_selftest(double limit_s, std::string &msg);
 Sim *make_sim_f32();
 
 // kernels reported by sim_profile_step, in order

@@ -52,6 +52,16 @@ def test_no_cpu_fallback_without_a_device(lib):
     assert "no CUDA device" in str(ei.value)
 
 
+def test_wait_selftest_reports_no_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2405_08001_gb300 import binding
+    st, msg = binding.sim_selftest_wait(0.05)
+    assert st == binding.SIM_ERR_CUDA and "no CUDA device" in msg
+    assert binding.sim_selftest_wait(5.0)[0] == binding.SIM_ERR_INVALID_ARG
+
+
 def test_default_options_and_status_strings(lib):
     from paper_2405_08001_gb300 import binding
     o = binding.sim_default_options()

@@ -1,8 +1,9 @@
 """Edge cases of the library on the GPU: inputs sim_create must reject (an empty mesh, an index out of range, an
 inverted rest tet, non-finite positions, options out of range), the smallest mesh (one tet: four vertices, far
-below one block of threads; lock-step against the oracle in both precisions), and the degenerate case of a mesh
+below one block of threads; lock-step against the oracle in both precisions), the degenerate case of a mesh
 whose every vertex is kinematic (p = 0, so max |p_v| = 0 and alpha = 0: the step only moves the vertices to their
-targets)."""
+targets), and an expiring bounded device wait (the failure-detection self-test: a wait that nothing completes gives
+up after its limit with SIM_ERR_TIMEOUT, and the context stays usable)."""
 import numpy as np
 import pytest
 
@@ -128,3 +129,19 @@ def test_all_vertices_kinematic(B, prec):
     np.testing.assert_allclose(v, (tg - sc.x0) / sc.dt, rtol=1e-12)
     assert sc_["alpha"] == 0.0 and sc_["pmax"] == 0.0 and sc_["gp"] == 0.0
     assert st["iters_done"] == sc.iters
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable(B):
+    import time
+    t0 = time.perf_counter()
+    st, msg = B.sim_selftest_wait(0.05)
+    dt = time.perf_counter() - t0
+    assert st == B.SIM_ERR_TIMEOUT, msg
+    assert dt < 3.0
+    assert B.sim_selftest_wait(0.0)[0] == B.SIM_ERR_INVALID_ARG
+    sc = S.cube_drop(n=3)
+    sim = B.Sim(sc, precision=0)
+    sim.step(1)
+    _, _, stats = B.sim_get_state(sim.h)
+    sim.close()
+    assert stats["iters_done"] == sc.iters
