@@ -130,7 +130,9 @@ def algorithmic_bytes(kernel: str, prec: int, sizes: dict, n_cand: int, n_active
     and the directions are 4-vectors of the element type (16 B float, 32 B double).  Per tet: 4 indices (16 B),
     D_m^-1 (9 values), h^2 V (1 value) and, in the FP32 form, the float-float rest metric (12 floats).  Candidates:
     int4 (16 B); active pairs (64 B float form, 112 B double form) written by the gradient pass and read by p^T H p.
-    The persistent step stores P g in the beta pass and forms the direction inside the p^T H p pass."""
+    The persistent step stores P g in the beta pass and forms the direction inside the p^T H p pass.  The FP32
+    form's per-tet p^T H p record (64 B written by the gradient pass, read by the p^T H p pass) is an
+    implementation choice for accuracy, not a quantity of the method, and is not counted."""
     T, V = sizes["n_tets"], sizes["n_verts"]
     r = 4 if prec == 1 else 8
     v4 = 4 * r
