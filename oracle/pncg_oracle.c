@@ -28,9 +28,10 @@
  *   - the barrier Hessian freezes the closest-point coefficients c (Sec. 3.2 states d2t/dx2 = 0).
  *   - closest points: PT interior projection (2x2 normal equations), else the three clamped point-edge cases;
  *     EE interior solution (2x2), else the four clamped point-edge cases; ties keep the first case in that order.
- *   - preconditioner P_ii = 1 / max(diag_ii, m_v): the Jacobi preconditioner of Sec. 4.2 wherever the diagonal is at
- *     least the vertex mass; below that (the barrier term (b'/d) c_i^2 of Eq. 10 is negative) the inertia diagonal
- *     alone, which keeps P continuous and bounded by 1/m_v; kinematic vertices get P = 0, g = 0.
+ *   - preconditioner P_ii = 1 / diag_ii, the Jacobi preconditioner of Sec. 4.2, wherever diag_ii > 1e-3 m_v; the
+ *     inertia diagonal alone, P_ii = 1 / m_v, where diag_ii <= 1e-3 m_v.  The barrier term (b'/d) c_i^2 of Eq. 9-10
+ *     is negative (b' < 0 inside dhat), so on contact vertices diag(H) can reach zero or fall below it, where
+ *     diag(H)^-1 is unbounded or negative (not a preconditioner); kinematic vertices get P = 0, g = 0.
  *   - PR+ beta = max(0, g1^T P1 (g1 - g0) / (g0^T P0 g0)); restart (beta = 0) when g^T p >= 0 after forming p.
  *   - ||p||_inf in the step cap is the largest per-vertex Euclidean length (the cap bounds vertex displacement
  *     by dhat/2, Sec. 4.3); the largest absolute component is an option.
@@ -1102,14 +1103,18 @@ void or_ncg_alpha(double gp, double pHp, double pmax, double dhat, double *out)
     out[4] = capped;
 }
 
-/* Jacobi preconditioner P = 1 / max(diag, m_v) (Sec. 4.2); kinematic vertices get g = 0 and P = 0 */
+/* smallest diagonal entry, as a fraction of the vertex mass, that the Jacobi preconditioner inverts */
+#define OR_JACOBI_FLOOR 1e-3
+
+/* Jacobi preconditioner P = diag(H)^-1 (Sec. 4.2) where diag > 1e-3 m_v, else 1 / m_v; kinematic vertices get
+   g = 0 and P = 0 */
 static void jacobi(const or_model *m, double *g1, const double *d1, double *P1)
 {
     for (int32_t i = 0; i < m->p.nv; ++i)
         for (int a = 0; a < 3; ++a) {
             size_t q = 3 * (size_t)i + a;
             if (m->fixed[i]) { g1[q] = 0.0; P1[q] = 0.0; continue; }
-            P1[q] = 1.0 / (d1[q] > m->mass[i] ? d1[q] : m->mass[i]);
+            P1[q] = d1[q] > OR_JACOBI_FLOOR * m->mass[i] ? 1.0 / d1[q] : 1.0 / m->mass[i];
         }
 }
 

@@ -744,10 +744,10 @@ __global__ void __launch_bounds__(VB) k_gather(Dev<R> D, int par)
 
 // ------------------------------------------------------------------------------------------ a4: beta reductions
 
-// Preconditioner entry of a free vertex (Sec. 4.2): 1 / max(diag, m).  The Jacobi entry 1/diag wherever the
-// diagonal is at least the vertex mass; the inertia diagonal where the negative barrier term (b'/d) c_i^2 of
-// Eq. 10 pulls it lower, which keeps P continuous and bounded by 1/m.
-template <typename R> __device__ inline R precond(R d, R m) { return R(1) / (d > m ? d : m); }
+// Preconditioner entry of a free vertex of mass m (Sec. 4.2): the Jacobi entry 1/diag wherever diag > 1e-3 m, the
+// inertia diagonal 1/m elsewhere.  The barrier term (b'/d) c_i^2 of Eq. 9-10 is negative inside dhat, so the
+// tangential entries of a contact vertex can reach zero or go negative, where 1/diag is unbounded or negative.
+template <typename R> __device__ inline R precond(R d, R m) { return R(1) / (d > R(1e-3) * m ? d : m); }
 
 __device__ inline float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ inline double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }

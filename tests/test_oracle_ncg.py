@@ -208,19 +208,69 @@ def test_drop_and_blocks_runs_are_penetration_free(oracle_mod):
             assert len(d) == 0 or d.min() > 0
 
 
-def test_preconditioner_is_jacobi_clamped_at_the_mass(oracle_mod):
-    """Sec. 4.2 gives P = diag(H)^-1.  The barrier term (b'/d) c_i^2 of Eq. 10 is negative, so contact vertices can
-    have diag(H) below the mass (even negative); there P falls back to the inertia diagonal 1/m."""
+def test_preconditioner_is_jacobi_where_the_diagonal_is_positive(oracle_mod):
+    """Sec. 4.2 gives P = diag(H)^-1.  The barrier term (b'/d) c_i^2 of Eq. 9-10 is negative (b' < 0 inside dhat),
+    so the tangential entries of contact vertices have diag(H) far below zero on these scenes; there (diag <= 1e-3 m)
+    P falls back to the inertia diagonal 1/m, everywhere else it is 1/diag."""
     sc = S.two_blocks(1)
     o = oracle_mod.Oracle.from_scene(sc)
     x = sc.x0.copy()
     xt = o.predict(x, sc.v0)
     _, diag, na = o.grad_diag(x, xt)
     m = np.repeat(o.mass()[:, None], 3, axis=1)
-    low = diag < m
-    assert na > 0 and low.any() and (~low).any()
+    low = diag <= 1e-3 * m
+    assert na > 0 and (diag < 0).any() and (~low).any()
     g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
     o.iteration(x, xt, g, P, p, 0)
     np.testing.assert_array_equal(P[low], 1.0 / m[low])
     np.testing.assert_allclose(P[~low], 1.0 / diag[~low], rtol=1e-15)
-    assert np.all(P <= 1.0 / m)
+    assert np.all(P > 0)
+
+
+def _vertex_over_face(d, dhat=1e-3, L=0.01, youngs=1e3):
+    """Two tets: A with its face z = 0 on top, B with its lowest vertex b0 at height d over the interior of that
+    face (every other primitive pair farther than dhat apart).  The only active pair is (b0, A's top face), with
+    t = (0, 0, d) and c_0 = 1, so the x entry of b0's diagonal is m + h^2 (elastic) + kappa b'(d) / d (Eq. 9-10)."""
+    A = np.array([[0, 0, 0], [L, 0, 0], [0, L, 0], [0, 0, -L]], float)
+    b0 = np.array([0.25 * L, 0.25 * L, d])
+    Bv = np.array([b0, b0 + [L, 0, L], b0 + [0, L, L], b0 + [0, 0, L]])
+    X = np.concatenate([A, Bv])
+    T = np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32)
+    for t in T:                                 # positive rest orientation
+        D = (X[t[1:]] - X[t[0]]).T
+        if np.linalg.det(D) < 0:
+            t[[1, 2]] = t[[2, 1]]
+    return S.Scene(name="vertex_over_face", rest_x=X, tets=T, x0=X.copy(), v0=np.zeros_like(X), youngs=youngs,
+                   poisson=0.3, density=1000.0, dt=1.0 / 60.0, dhat=dhat, kappa=1e4, gravity=(0.0, 0.0, 0.0),
+                   plane=None, iters=1, steps=1)
+
+
+@pytest.mark.parametrize("ratio", [0.5e-3, 2e-3, 0.5, 2.0])
+def test_preconditioner_floor_is_a_thousandth_of_the_mass(oracle_mod, ratio):
+    """Places b0 so that its tangential diagonal entry is `ratio` times its mass and checks the preconditioner on
+    either side of the floor: 1/diag at 2e-3 m, 0.5 m and 2 m (the paper's P), 1/m at 0.5e-3 m.  Moving the floor by
+    a factor of four either way, or back to the mass, fails one of the cases."""
+    def entry(d):
+        sc = _vertex_over_face(d)
+        o = oracle_mod.Oracle.from_scene(sc)
+        _, diag, na = o.grad_diag(sc.x0, sc.x0)
+        return sc, o, diag, na
+    b0 = 4
+    lo, hi = 1e-6 * 1e-3, 1e-3
+    sc, o, diag, na = entry(0.5 * (lo + hi))
+    m = o.mass()[b0]
+    for _ in range(200):                        # diag_x(b0) increases with d: bisect for ratio * m
+        mid = 0.5 * (lo + hi)
+        sc, o, diag, na = entry(mid)
+        if diag[b0, 0] < ratio * m:
+            lo = mid
+        else:
+            hi = mid
+    sc, o, diag, na = entry(hi)
+    assert na == 1
+    assert abs(diag[b0, 0] / (ratio * m) - 1.0) < 1e-3, diag[b0, 0] / m
+    x = sc.x0.copy()
+    g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
+    o.iteration(x, sc.x0, g, P, p, 0)
+    want = 1.0 / m if ratio < 1e-3 else 1.0 / diag[b0, 0]
+    assert abs(P[b0, 0] / want - 1.0) < 1e-12, (P[b0, 0] * m, want * m)
