@@ -277,11 +277,15 @@ const char *sim_kernel_name(int32_t i);
  * allocator (a game engine or a renderer that loads this library as a plugin), or a real-time thread that must
  * never block in the driver's allocator.  The paper has no counterpart: it is an allocation-free variant of the
  * library's p^T H p reduction (the sum sim_eval_pHp returns for a scene without contact).
- *   x, p, rest_x: device [n_verts][3]; tets: device [n_tets][4]; mass: device [n_verts] (lumped masses);
+ *   x, p, rest_x: device [n_verts][3]; tets: device [n_tets][4], every rest tet positively oriented
+ *   (det[X1-X0, X2-X0, X3-X0] > 0); mass: device [n_verts] (lumped masses);
  *   youngs, poisson: Neo-Hookean material; dt: time step (the elastic term is scaled by dt^2);
- *   out: device, one double receiving p^T M p + dt^2 sum_e V_e p_e^T (d2 Psi / dx2) p_e (NaN if a tet is inverted);
+ *   out: device, one double receiving p^T M p + dt^2 sum_e V_e p_e^T (d2 Psi / dx2) p_e; NaN if a current tet is
+ *   inverted or a rest tet has non-positive volume (the buffers are not read back, so no status reports it);
  *   cuda_stream: cudaStream_t to launch on (NULL = the legacy default stream).  Asynchronous: *out is ready when the
  *   stream reaches it.
+ *   Every buffer and the stream must belong to the calling thread's current device (the scratch is looked up for
+ *   that device); tet indices must lie in [0, n_verts): they are not checked on the device.
  * No memory is allocated: the kernel's scratch (one partial sum per block of 256 threads and an arrival counter)
  * is a file-scope __device__ array of 512 KiB that every GPU loading the library keeps until the process exits.
  * Limits: n_verts and n_tets at most 16,777,216 each (65,536 blocks); larger sizes return SIM_ERR_INVALID_ARG

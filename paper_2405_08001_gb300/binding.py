@@ -387,13 +387,51 @@ def sim_get_scene_scalars(h, max_scenes=1024):
     return {c: out[: n.value, i].copy() for i, c in enumerate(SCENE_SCALAR_COLS)}
 
 
+def _noalloc_args(x, p, rest_x, tets, mass, out, stream):
+    """Checks sim_pHp_noalloc's arguments on the host, before anything reaches the device: every array a contiguous
+    CUDA tensor of the right type on one device (the stream's, if one is given), matching sizes.  Returns
+    (device, n_verts, n_tets)."""
+    import torch
+    named = (("x", x, torch.float64), ("p", p, torch.float64), ("rest_x", rest_x, torch.float64),
+             ("tets", tets, torch.int32), ("mass", mass, torch.float64), ("out", out, torch.float64))
+    for name, a, dt in named:
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"sim_pHp_noalloc: {name} must be a CUDA tensor, not {type(a).__name__}")
+        if not a.is_cuda:
+            raise TypeError(f"sim_pHp_noalloc: {name} must be a CUDA tensor (it is on {a.device})")
+        if a.dtype != dt or not a.is_contiguous():
+            raise TypeError(f"sim_pHp_noalloc: {name} must be a contiguous {dt} tensor")
+    dev = x.device
+    for name, a, _ in named:
+        if a.device != dev:
+            raise ValueError(f"sim_pHp_noalloc: {name} is on {a.device}, x on {dev}")
+    if stream is not None and stream.device != dev:
+        raise ValueError(f"sim_pHp_noalloc: the stream belongs to {stream.device}, the tensors to {dev}")
+    if x.numel() == 0 or x.numel() % 3:
+        raise ValueError("sim_pHp_noalloc: x must hold n_verts x 3 values, n_verts > 0")
+    nv = x.numel() // 3
+    for name, a, n in (("p", p, 3 * nv), ("rest_x", rest_x, 3 * nv), ("mass", mass, nv)):
+        if a.numel() != n:
+            raise ValueError(f"sim_pHp_noalloc: {name} has {a.numel()} values, {n} expected")
+    if tets.numel() == 0 or tets.numel() % 4:
+        raise ValueError("sim_pHp_noalloc: tets must hold n_tets x 4 indices, n_tets > 0")
+    if out.numel() < 1:
+        raise ValueError("sim_pHp_noalloc: out must hold one value")
+    return dev, nv, tets.numel() // 4
+
+
 def sim_pHp_noalloc(x, p, rest_x, tets, mass, youngs, poisson, dt, out, stream=None):
     """Allocation-free p^T H p (inertia + elastic, no contact) on caller-owned CUDA tensors; asynchronous on
-    `stream` (a torch.cuda.Stream or None).  out: a 1-element float64 CUDA tensor."""
-    nv, nt = x.numel() // 3, tets.numel() // 4
-    args = [_ptr(a)[0] for a in (x, p, rest_x)] + [_ptr(tets, np.int32)[0], _ptr(mass)[0]]
-    st = load().sim_pHp_noalloc(nv, nt, *args, float(youngs), float(poisson), float(dt), _ptr(out)[0],
-                                None if stream is None else stream.cuda_stream)
+    `stream` (a torch.cuda.Stream or None).  x, p, rest_x: float64 [n_verts, 3]; tets: int32 [n_tets, 4] with
+    indices in [0, n_verts); mass: float64 [n_verts]; out: a 1-element float64 tensor.  All on one device; the call
+    is made with that device current.  Host arrays, CPU tensors or mismatched sizes raise TypeError / ValueError
+    before anything is launched."""
+    import torch
+    dev, nv, nt = _noalloc_args(x, p, rest_x, tets, mass, out, stream)
+    with torch.cuda.device(dev):
+        st = load().sim_pHp_noalloc(nv, nt, x.data_ptr(), p.data_ptr(), rest_x.data_ptr(), tets.data_ptr(),
+                                    mass.data_ptr(), float(youngs), float(poisson), float(dt), out.data_ptr(),
+                                    None if stream is None else stream.cuda_stream)
     if st != SIM_OK:
         raise SimError(st, load().sim_noalloc_last_error().decode())
 

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_pHp_noalloc(NoAllocScratch *scr,
             cf[2][b] = F[0][b1] * F[1][b2] - F[1][b1] * F[0][b2];
         }
         const double J = F[0][0] * cf[0][0] + F[1][0] * cf[1][0] + F[2][0] * cf[2][0];
-        if (J > 0.0) {
+        if (J > 0.0 && det > 0.0) {
             const double L = log(J);
             const double Psi3 = (lam * L - mu) / J, Psi33 = (mu + lam * (1.0 - L)) / (J * J);
             double n2 = 0.0, g3 = 0.0;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_pHp_noalloc(NoAllocScratch *scr,
             const double h3 = 2.0 * (tri(d0, d1, f2) + tri(d0, f1, d2) + tri(f0, d1, d2));
             s[0] += h2 * (det / 6.0) * (mu * n2 + Psi33 * g3 * g3 + Psi3 * h3);
         } else {
-            s[0] = nan("");
+            s[0] = nan("");     // an inverted current tet, or a rest tet of non-positive volume
         }
     }
     pncg::block_sum<1>(s, sh);

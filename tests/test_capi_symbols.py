@@ -69,3 +69,35 @@ def test_default_options_and_status_strings(lib):
     assert lib.sim_status_string(binding.SIM_ERR_INVERTED) == b"SIM_ERR_INVERTED"
     assert lib.sim_abi_version() >= 1
     assert lib.sim_kernel_count() == len(binding.sim_kernel_names()) > 5
+
+
+def test_noalloc_binding_rejects_host_memory_before_any_launch():
+    """sim_pHp_noalloc hands raw pointers to a kernel: the binding refuses numpy arrays and CPU tensors (host
+    pointers would reach the device) with a TypeError, without calling into the library."""
+    import torch
+    from paper_2405_08001_gb300 import binding
+    x = np.zeros((4, 3))
+    t = np.array([[0, 1, 2, 3]], np.int32)
+    m = np.ones(4)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        binding.sim_pHp_noalloc(x, x, x, t, m, 1e5, 0.4, 0.01, np.zeros(1))
+    xt = torch.zeros(4, 3, dtype=torch.float64)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        binding.sim_pHp_noalloc(xt, xt, xt, torch.from_numpy(t), torch.ones(4, dtype=torch.float64), 1e5, 0.4, 0.01,
+                                torch.zeros(1, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("case", ["null_x", "null_out", "zero_verts", "dt", "poisson_half", "poisson_low"])
+def test_noalloc_rejects_invalid_arguments_before_touching_the_device(lib, case):
+    """The C entry point checks its arguments before any CUDA call: null pointers, empty meshes, dt <= 0 and a
+    Poisson ratio outside (-1, 0.5) return SIM_ERR_INVALID_ARG with a message (no device is needed to see it)."""
+    from paper_2405_08001_gb300 import binding
+    buf = np.zeros(64)
+    ptr = buf.ctypes.data
+    args = dict(nv=4, nt=1, x=ptr, out=ptr, dt=0.01, poisson=0.4)
+    args.update({"null_x": dict(x=None), "null_out": dict(out=None), "zero_verts": dict(nv=0), "dt": dict(dt=0.0),
+                 "poisson_half": dict(poisson=0.5), "poisson_low": dict(poisson=-1.0)}[case])
+    st = lib.sim_pHp_noalloc(args["nv"], args["nt"], args["x"], ptr, ptr, ptr, ptr, 1e5, args["poisson"], args["dt"],
+                             args["out"], None)
+    assert st == binding.SIM_ERR_INVALID_ARG
+    assert "invalid argument" in lib.sim_noalloc_last_error().decode()
