@@ -138,6 +138,8 @@ typedef struct {
     double dE0, dE_last;   /* Delta E of the first and the last iteration */
     int32_t launch_form;   /* the form time steps run in now: 1 = persistent, 0 = one kernel per phase */
     int32_t n_scenes;      /* independent scenes (1 without scene_of_vert) */
+    int32_t n_near_fp64;   /* FP32 form: pair evaluations of the last step (or of the last sim_eval_* call) whose
+                              distance fell below 1e-3 dhat, where the barrier terms are evaluated in double */
 } sim_stats;
 
 /* Scalars of the most recent iteration (Algorithm 1). */

@@ -77,6 +77,7 @@ def _load():
             "or_pair_geometry": (D, [I32, P, P, P]),
             "or_energy": (C.c_int, [P, P, P, P, P]),
             "or_grad_diag": (C.c_int, [P, P, P, P, P, P]),
+            "or_grad_diag_scale": (C.c_int, [P, P, P, P, P]),
             "or_pHp": (C.c_int, [P, P, P, P]),
             "or_active_pairs": (C.c_int, [P, P, I32, D, I32, P, P, P, I32, P]),
             "or_ncg_direction": (C.c_int, [I32, P, P, P, P, P, I32, I32, P, P, P]),
@@ -231,6 +232,16 @@ class Oracle:
         na = C.c_int32()
         _check(_load().or_grad_diag(self._m, _ptr(x), _ptr(xt), _ptr(g), _ptr(d), C.byref(na)))
         return g, d, na.value
+
+    def grad_diag_scale(self, x, xtilde):
+        """Per-entry sums of the magnitudes of the contributions to g and diag(H) at x: the scale a rounding error of
+        each term is relative to (inertia, each tet's force, each barrier force; m, each elastic and barrier term of
+        the diagonal)."""
+        x, xt = _f64(x), _f64(xtilde)
+        gs = np.zeros((self.nv, 3))
+        ds = np.zeros((self.nv, 3))
+        _check(_load().or_grad_diag_scale(self._m, _ptr(x), _ptr(xt), _ptr(gs), _ptr(ds)))
+        return gs, ds
 
     def pHp(self, x, p):
         x, p = _f64(x), _f64(p)

@@ -856,13 +856,28 @@ int or_energy(const or_model *m, const double *x, const double *xtilde, double *
  *             with h_i = J^T g_i g_i^T J and h_{i+3} = J^T H_i J (the I1 terms vanish for NH and SNH)
  *   barrier:  g += kappa b'/d (dt/dx) t  (Eq. 8);  diag from Eqs. 9-11
  *   n_active receives the number of active pairs (NULL allowed).
+ * With absmode set, every contribution to a vertex is added by the Euclidean length of its 3-vector instead (the
+ * scale a rounding error of that vector is relative to, whatever the coordinate axes; the per-entry scale of the
+ * parity tests), to all three entries: g receives m |x - xt| plus, per tet, h^2 V |dPsi/dF|_F |w_i| (the stress
+ * taken as a whole; w_i the vertex's row of dF/dx) plus kappa |b'/d| |c_i| |t| per pair and kappa |b'| per plane
+ * contact; diag receives m plus, per tet, the magnitudes of the six terms with each Jg_k entry replaced by the length
+ * of the vertex's 3-vector Jg_k, plus kappa (|b''/d^2 - b'/d^3| c_i^2 |t|^2 + |b'/d| c_i^2) per pair and
+ * kappa |b''| per plane contact.
  */
-int or_grad_diag(const or_model *m, const double *x, const double *xtilde, double *g, double *diag, int32_t *n_active)
+static int grad_diag_impl(const or_model *m, const double *x, const double *xtilde, double *g, double *diag,
+                          int32_t *n_active, int absmode)
 {
+#define ACC(t) (absmode ? fabs(t) : (t))
     int32_t nv = m->p.nv;
     for (int32_t i = 0; i < nv; ++i)
         for (int a = 0; a < 3; ++a) {
-            g[3 * (size_t)i + a] = m->mass[i] * (x[3 * (size_t)i + a] - xtilde[3 * (size_t)i + a]);
+            if (absmode) {
+                double dx[3];
+                sub3(x + 3 * (size_t)i, xtilde + 3 * (size_t)i, dx);
+                g[3 * (size_t)i + a] = m->mass[i] * sqrt(dot3(dx, dx));
+            } else {
+                g[3 * (size_t)i + a] = m->mass[i] * (x[3 * (size_t)i + a] - xtilde[3 * (size_t)i + a]);
+            }
             diag[3 * (size_t)i + a] = m->mass[i];
         }
     for (int32_t e = 0; e < m->p.nt; ++e) {
@@ -881,6 +896,23 @@ int or_grad_diag(const or_model *m, const double *x, const double *xtilde, doubl
             }
             dg[q] = s0; Jg1[q] = s1; Jg2[q] = s2; Jg3[q] = s3;
         }
+        if (absmode) {   /* Euclidean lengths of the vertex's 3-vectors: dPsi w_i and J g_k restricted to vertex i */
+            double nP = 0.0;
+            for (int r = 0; r < 9; ++r) nP += dPsi[r] * dPsi[r];
+            nP = sqrt(nP);
+            for (int i = 0; i < 4; ++i) {
+                double nw = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+                for (int b = 0; b < 3; ++b) nw += T.J[3 * b][3 * i] * T.J[3 * b][3 * i];
+                for (int a = 0; a < 3; ++a) {
+                    const int q = 3 * i + a;
+                    n1 += Jg1[q] * Jg1[q]; n2 += Jg2[q] * Jg2[q]; n3 += Jg3[q] * Jg3[q];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    dg[3 * i + a] = nP * sqrt(nw);
+                    Jg1[3 * i + a] = sqrt(n1); Jg2[3 * i + a] = sqrt(n2); Jg3[3 * i + a] = sqrt(n3);
+                }
+            }
+        }
         /* diag(J^T H J) for H1, H2 = 2 I and H3 */
         for (int q = 0; q < 12; ++q) {
             double h4 = 0, h5 = 0, h6 = 0;
@@ -891,8 +923,8 @@ int or_grad_diag(const or_model *m, const double *x, const double *xtilde, doubl
                 h6 += T.J[r][q] * HJ;
                 h4 += T.J[r][q] * H1J;
             }
-            dh[q] = T.Psi11 * Jg1[q] * Jg1[q] + T.Psi22 * Jg2[q] * Jg2[q] + T.Psi33 * Jg3[q] * Jg3[q] +
-                    T.Psi1 * h4 + T.Psi2 * h5 + T.Psi3 * h6;
+            dh[q] = ACC(T.Psi11 * Jg1[q] * Jg1[q]) + ACC(T.Psi22 * Jg2[q] * Jg2[q]) + ACC(T.Psi33 * Jg3[q] * Jg3[q]) +
+                    ACC(T.Psi1 * h4) + ACC(T.Psi2 * h5) + ACC(T.Psi3 * h6);
         }
         for (int i = 0; i < 4; ++i)
             for (int a = 0; a < 3; ++a) {
@@ -912,11 +944,18 @@ int or_grad_diag(const or_model *m, const double *x, const double *xtilde, doubl
         or_barrier_fn(d, dh_, bb);
         double coef_tt = kap * (bb[2] / (d * d) - bb[1] / (d * d * d));  /* multiplies (dt/dx t)(dt/dx t)^T */
         double coef_I = kap * bb[1] / d;                                 /* multiplies (dt/dx)(dt/dx)^T */
+        const double tn = sqrt(dot3(P->t, P->t));
         for (int i = 0; i < 4; ++i)
             for (int a = 0; a < 3; ++a) {
                 double ct = P->c[i] * P->t[a];
-                g[3 * (size_t)P->v[i] + a] += coef_I * ct;
-                diag[3 * (size_t)P->v[i] + a] += coef_tt * ct * ct + coef_I * P->c[i] * P->c[i];
+                if (absmode) {
+                    const double ctn = fabs(P->c[i]) * tn;
+                    g[3 * (size_t)P->v[i] + a] += fabs(coef_I) * ctn;
+                    diag[3 * (size_t)P->v[i] + a] += fabs(coef_tt) * ctn * ctn + fabs(coef_I) * P->c[i] * P->c[i];
+                } else {
+                    g[3 * (size_t)P->v[i] + a] += coef_I * ct;
+                    diag[3 * (size_t)P->v[i] + a] += coef_tt * ct * ct + coef_I * P->c[i] * P->c[i];
+                }
             }
     }
     if (n_active) *n_active = L.n;
@@ -929,13 +968,30 @@ int or_grad_diag(const or_model *m, const double *x, const double *xtilde, doubl
             double bb[3];
             or_barrier_fn(d, dh_, bb);
             for (int a = 0; a < 3; ++a) {
-                g[3 * (size_t)i + a] += kap * bb[1] * m->plane_n[a];
-                diag[3 * (size_t)i + a] += kap * bb[2] * m->plane_n[a] * m->plane_n[a];
+                if (absmode) {
+                    g[3 * (size_t)i + a] += fabs(kap * bb[1]) * sqrt(dot3(m->plane_n, m->plane_n));
+                    diag[3 * (size_t)i + a] += fabs(kap * bb[2]) * dot3(m->plane_n, m->plane_n);
+                } else {
+                    g[3 * (size_t)i + a] += kap * bb[1] * m->plane_n[a];
+                    diag[3 * (size_t)i + a] += kap * bb[2] * m->plane_n[a] * m->plane_n[a];
+                }
             }
         }
     for (size_t q = 0; q < 3 * (size_t)nv; ++q)
         if (!isfinite(g[q]) || !isfinite(diag[q])) { set_err("non-finite gradient"); return OR_ERR_NONFINITE; }
     return OR_OK;
+#undef ACC
+}
+
+int or_grad_diag(const or_model *m, const double *x, const double *xtilde, double *g, double *diag, int32_t *n_active)
+{
+    return grad_diag_impl(m, x, xtilde, g, diag, n_active, 0);
+}
+
+/* Per-entry magnitude sums of the contributions to g and diag(H) at x (grad_diag_impl's absmode). */
+int or_grad_diag_scale(const or_model *m, const double *x, const double *xtilde, double *gs, double *ds)
+{
+    return grad_diag_impl(m, x, xtilde, gs, ds, NULL, 1);
 }
 
 /*

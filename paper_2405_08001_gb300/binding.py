@@ -46,7 +46,8 @@ class sim_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("iters_done", C.c_int32), ("n_candidates", C.c_int32),
                 ("n_active", C.c_int32), ("n_rebuilds", C.c_int32), ("n_capped", C.c_int32),
                 ("n_surface_tris", C.c_int32), ("n_surface_edges", C.c_int32), ("n_surface_verts", C.c_int32),
-                ("dE0", C.c_double), ("dE_last", C.c_double), ("launch_form", C.c_int32), ("n_scenes", C.c_int32)]
+                ("dE0", C.c_double), ("dE_last", C.c_double), ("launch_form", C.c_int32), ("n_scenes", C.c_int32),
+                ("n_near_fp64", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -28,7 +28,7 @@ const char *const kProfiledNames[N_PROFILED] = {"k_predict", "bp_boxes", "bp_cou
 
 extern "C" {
 
-int32_t sim_abi_version(void) { return 2; }
+int32_t sim_abi_version(void) { return 3; }
 
 const char *sim_status_string(sim_status s)
 {

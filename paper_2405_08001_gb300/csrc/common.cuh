@@ -46,6 +46,8 @@ struct Ctrl {
     int32_t k;             // index of the next iteration within the step
     int32_t n_rebuilds;
     int32_t n_capped;
+    int32_t n_near64;      // FP32 form: pair evaluations that took the double branch (d < 1e-3 dhat) since the
+                           // step started (or since the last sim_eval_* set-up)
     int32_t iters_done;
     int32_t converged;     // eps rule fired in this step
     int32_t restarted;

@@ -51,6 +51,20 @@ struct ffacc {
         s = t;
         c = __fadd_rn(c, __fadd_rn(err, e));
     }
+    // adds x y for a float-float x and a float y (Dot2: the FMA TwoProd of the heads, the tail's product into the
+    // compensation)
+    __device__ inline void add_prod_f(ffl x, float y)
+    {
+        const float p = __fmul_rn(x.h, y);
+        float e = __fmaf_rn(x.h, y, -p);
+        e = __fmaf_rn(x.l, y, e);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ inline ffl ff() const { return {s, c}; }
     // subtracts the float-float value h + l
     __device__ inline void sub_ff(float h, float l)
     {

@@ -23,7 +23,8 @@ template <typename R> struct Dev {
     double4_32a *x, *xt, *xtil, *v, *xb;   // xtil.w = mass (free vertex) or -1 (kinematic)
     float4 *xh, *xl;                   // FP32 form: float-float copy of x (hi, lo); null in the FP64 form
     float4 *xbh;                       // FP32 form: xh at the last candidate build (displacement check)
-    const float *G0;                   // FP32 form: [12][nt] rest metric Dm^T Dm of each tet as float-float
+    const float *G0;                   // FP32 form: [14][nt] rest metric Dm^T Dm of each tet as float-float (six
+                                       // heads, six tails), then det Dm as float-float
                                        // (hi of entries 00 01 02 11 12 22, then lo)
     float4 *tS;                        // FP32 form: [4][nt] of the last gradient pass per tet: S = 2 dPsi/dC and
                                        // C^-1 (entries 00 01 02 11 12 22 each), k1, k2, 0, 0 (tet_pHp_vec)
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(VB) k_predict(Dev<R> D)
         double m = finish_max(D.part, 0, sh);
         if (threadIdx.x == 0) {
             Ctrl *c = D.ctrl;
-            c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->iters_done = 0; c->converged = 0;
+            c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->n_near64 = 0; c->iters_done = 0; c->converged = 0;
             c->n_active = 0; c->dE0 = 0.0; c->gPg_prev = 0.0;
             if (!skip) request_rebuild_if(D, m);
         }
@@ -307,7 +308,7 @@ template <typename R> struct TetIn {
     int4 tv;
     R w[3][3];
     R hv, es;
-    float g0[12];   // FP32 form: rest metric entries 00 01 02 11 12 22, heads then tails
+    float g0[14];   // FP32 form: rest metric entries 00 01 02 11 12 22, heads then tails; det Dm head, tail
 };
 template <typename R> __device__ inline void load_tet_in(const Dev<R> &D, int e, TetIn<R> &in)
 {
@@ -320,17 +321,21 @@ template <typename R> __device__ inline void load_tet_in(const Dev<R> &D, int e,
     in.es = D.escale ? D.escale[e] : R(1);
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
-        for (int q = 0; q < 12; ++q) in.g0[q] = D.G0[q * D.nt + e];
+        for (int q = 0; q < 14; ++q) in.g0[q] = D.G0[q * D.nt + e];
     }
 }
 
 // First Piola-Kirchhoff stress of the FP32 form, evaluated from the metric change so that it stays accurate for
 // small strains under any rotation.  With C = F^T F and a density of I2 and I3 (Sec. 3.1: NH or SNH) written in C,
-//   P = F C^-1 (mu (C - I) + (mu + Psi_3 J) I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
-// which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly; mu + Psi_3 J is lambda log J for NH.  The metric change G = Ds^T Ds - Dm^T Dm is
-// accumulated in float-float from the float-float current positions and the tet's float-float rest metric, so that
-// rounding never acts on the O(1) parts that cancel; log J = log1p(det C - 1) / 2 with det C - 1 expanded in the
-// entries of C - I.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the diagonal.
+//   P = F^-T (mu (C - I) + (mu + Psi_3 J) I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
+// which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly; mu + Psi_3 J is lambda log J for NH.  The metric
+// change G = Ds^T Ds - Dm^T Dm is accumulated in float-float from the float-float current positions and the tet's
+// float-float rest metric, and C - I = W^T G W is formed with compensated products, so that rounding never acts on
+// the parts that cancel.  J - 1 = (det Ds - det Dm) / det Dm comes from det Ds in float-float and the tet's
+// float-float det Dm: under large shear a nearly incompressible tet keeps J near 1 while the entries of C - I are
+// of order one, and det C - 1 expanded in those entries cancels (lambda log J then carried about 1e-5 of the
+// stress).  F^-T = cof(F) / J.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the
+// diagonal.
 __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float> &in, TetF<float> &T, float P[3][3],
                                          float &Psi33, int e)
 {
@@ -347,7 +352,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int a = 0; a < 3; ++a) ds[a][c] = ff_sub(comp(xh[c + 1], a), comp(xl[c + 1], a), comp(xh[0], a), comp(xl[0], a));
-    float G[3][3];
+    ffl G[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -357,7 +362,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc.add_prod(ds[a][i], ds[a][j], 1.0f);
             acc.sub_ff(g0h[q], g0l[q]);
-            G[i][j] = G[j][i] = acc.value();
+            G[i][j] = G[j][i] = acc.ff();
         }
     float dsf[3][3];
 #pragma unroll
@@ -370,35 +375,57 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
         for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
     tet_F_from<float>(dsf, T);
     if (!(T.J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
-    // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc)
-    float GW[3][3], A[3][3];
+    // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc), both products compensated (Dot2): their terms are
+    // up to cond(Dm)^2 times larger than A and cancel, which in plain float costs about 1e-6 of the stress on
+    // strongly sheared tets
+    ffl GW[3][3];
+    float A[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) GW[i][b] = G[i][0] * T.w[0][b] + G[i][1] * T.w[1][b] + G[i][2] * T.w[2][b];
+        for (int b = 0; b < 3; ++b) {
+            ffacc acc;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc.add_prod_f(G[i][j], T.w[j][b]);
+            GW[i][b] = acc.ff();
+        }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = a; b < 3; ++b) A[a][b] = A[b][a] = T.w[0][a] * GW[0][b] + T.w[1][a] * GW[1][b] + T.w[2][a] * GW[2][b];
-    const float m01 = A[0][0] * A[1][1] - A[0][1] * A[0][1];
-    const float m02 = A[0][0] * A[2][2] - A[0][2] * A[0][2];
-    const float m12 = A[1][1] * A[2][2] - A[1][2] * A[1][2];
-    const float detA = A[0][0] * m12 - A[0][1] * (A[0][1] * A[2][2] - A[1][2] * A[0][2]) +
-                       A[0][2] * (A[0][1] * A[1][2] - A[1][1] * A[0][2]);
-    const float dC = (A[0][0] + A[1][1] + A[2][2]) + (m01 + m02 + m12) + detA;   // det C - 1
-    const float detC = 1.0f + dC;
+        for (int b = a; b < 3; ++b) {
+            ffacc acc;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) acc.add_prod_f(GW[i][b], T.w[i][a]);
+            A[a][b] = A[b][a] = acc.value();
+        }
+    // J - 1 from det Ds (float-float; the edge vectors ds[a][c] = component a of edge c) and det Dm
+    float Jm1;
+    {
+        ffn a[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[r][c] = ffn(ds[r][c].h, ds[r][c].l);
+        const ffn det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                        a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                        a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+        const ffn dd = det - ffn(in.g0[12], in.g0[13]);
+        Jm1 = __fdiv_rn(__fadd_rn(dd.h, dd.l), in.g0[12]);
+    }
+    const float J = 1.0f + Jm1;
+    if (!(J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
+    const float detC = J * J;
     const float mu = D.mu * in.es, lam = D.lam * in.es;
-    // mJ = mu + Psi_3 J: lambda log J (NH), (J - 1)(lambda J - mu) (SNH) with J - 1 = (det C - 1) / (J + 1)
+    // mJ = mu + Psi_3 J: lambda log J (NH), (J - 1)(lambda J - mu) (SNH)
     // k1 = J (Psi_33 J + Psi_3) / 4, k2 = -Psi_3 J / 2: the coefficients of p^T H p in C (tet_pHp_vec)
     float mJ, k1, k2;
     if (D.model == MAT_SNH) {
-        const float J = sqrtf(detC), Jm1 = dC / (J + 1.0f);
         mJ = Jm1 * (lam * J - mu);
         Psi33 = lam;
         k1 = 0.25f * J * (lam * (J + Jm1) - mu);
         k2 = 0.5f * J * (mu - lam * Jm1);
     } else {
-        const float L = 0.5f * log1pf(dC);                                         // log J
+        const float L = log1pf(Jm1);                                                // log J
         mJ = lam * L;
         Psi33 = (mu + lam * (1.0f - L)) / detC;
         k1 = 0.25f * lam;
@@ -424,11 +451,12 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) S[a][b] = Ci[a][0] * M[0][b] + Ci[a][1] * M[1][b] + Ci[a][2] * M[2][b];
-    const float sc = in.hv;
+    // P = F^-T M with F^-T = cof(F) / J (T.cf[a][c] is the cofactor of F_ac)
+    const float sc = in.hv, sj = sc / J;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) P[a][b] = sc * (T.F[a][0] * S[0][b] + T.F[a][1] * S[1][b] + T.F[a][2] * S[2][b]);
+        for (int b = 0; b < 3; ++b) P[a][b] = sj * (T.cf[a][0] * M[0][b] + T.cf[a][1] * M[1][b] + T.cf[a][2] * M[2][b]);
     if (e >= 0) {   // S (symmetric: C^-1 commutes with C - I), C^-1, k1, k2 for the p^T H p pass
         const size_t n = (size_t)D.nt;
         D.tS[e] = make_float4(S[0][0], 0.5f * (S[0][1] + S[1][0]), 0.5f * (S[0][2] + S[2][0]), S[1][1]);
@@ -668,6 +696,7 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
         v3<double> td;
         double dd = pair_geom<double>(ee, ldcg4(D.x + v.x), ldcg4(D.x + v.y), ldcg4(D.x + v.z), ldcg4(D.x + v.w), cd, td);
         if (!(dd > 0.0)) { flag_error(D.ctrl, ERR_PENETRATION); return; }
+        atomicAdd(&D.ctrl->n_near64, 1);
         double b1, b2;
         barrier_d12<double>(dd, D.dhat, b1, b2);
         A = R(D.kappa * (b2 / (dd * dd) - b1 / (dd * dd * dd)));

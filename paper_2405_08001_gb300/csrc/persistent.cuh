@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         dE0 = 0.0;
         converged = 0;
         if (lead) {
-            c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->iters_done = 0; c->converged = 0;
+            c->k = 0; c->n_rebuilds = 0; c->n_capped = 0; c->n_near64 = 0; c->iters_done = 0; c->converged = 0;
             c->n_active = 0; c->dE0 = 0.0; c->gPg_prev = 0.0;
         }
         if (D.nseg > 1) seg_reset<R>(D);

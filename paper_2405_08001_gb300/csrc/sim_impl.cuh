@@ -270,6 +270,7 @@ public:
             st->dE_last = hctrl->dE;
             st->launch_form = persist ? 1 : 0;
             st->n_scenes = M.nseg;
+            st->n_near_fp64 = hctrl->n_near64;
         }
         return r;
     }
@@ -343,6 +344,7 @@ public:
         k_reinit<R><<<nb, 256, 0, s>>>(D, 0);
         force_rebuild();
         zero_active();
+        zero_near64();
         launch_bp();
         launch_grad(0);
         k_copy_count<<<1, 1, 0, s>>>(dctrl);
@@ -839,7 +841,7 @@ private:
         if (sizeof(R) == 4) {
             AL(D.xh, nv); AL(D.xl, nv); AL(D.xbh, nv);
             float *g0;
-            AL(g0, 12 * (size_t)nt);
+            AL(g0, 14 * (size_t)nt);
             D.G0 = g0;
             AL(D.tS, 4 * (size_t)nt);
         }
@@ -1004,8 +1006,8 @@ private:
         if ((st = up(B.obj, M.obj.data(), sizeof(int) * nv))) return st;
         if (B.excl && (st = up(B.excl, M.excl.data(), sizeof(unsigned long long) * M.excl.size()))) return st;
         if (D.G0) {
-            // rest metric Dm^T Dm per tet in double, stored as float-float
-            std::vector<float> g0(12 * (size_t)nt);
+            // rest metric Dm^T Dm and det Dm (six times the rest volume) per tet in double, stored as float-float
+            std::vector<float> g0(14 * (size_t)nt);
             for (int e = 0; e < nt; ++e) {
                 double dm[3][3];
                 for (int c = 0; c < 3; ++c)
@@ -1018,8 +1020,14 @@ private:
                         g0[(size_t)q * nt + e] = hi;
                         g0[(size_t)(6 + q) * nt + e] = (float)(v - (double)hi);
                     }
+                const double det = dm[0][0] * (dm[1][1] * dm[2][2] - dm[1][2] * dm[2][1]) -
+                                   dm[0][1] * (dm[1][0] * dm[2][2] - dm[1][2] * dm[2][0]) +
+                                   dm[0][2] * (dm[1][0] * dm[2][1] - dm[1][1] * dm[2][0]);
+                const float dh = (float)det;
+                g0[(size_t)12 * nt + e] = dh;
+                g0[(size_t)13 * nt + e] = (float)(det - (double)dh);
             }
-            if ((st = up(D.G0, g0.data(), sizeof(float) * 12 * (size_t)nt))) return st;
+            if ((st = up(D.G0, g0.data(), sizeof(float) * 14 * (size_t)nt))) return st;
         }
         refresh_ff();
         std::memset(hctrl, 0, sizeof(Ctrl));
@@ -1053,6 +1061,11 @@ private:
     {
         static const int32_t zero = 0;
         cudaMemcpyAsync(&dctrl->n_active, &zero, sizeof zero, cudaMemcpyHostToDevice, s);
+    }
+    void zero_near64()
+    {
+        static const int32_t zero = 0;
+        cudaMemcpyAsync(&dctrl->n_near64, &zero, sizeof zero, cudaMemcpyHostToDevice, s);
     }
 
     void refresh_ff() { k_refresh_ff<R><<<(M.nv + 255) / 256, 256, 0, s>>>(D); }

@@ -5,6 +5,7 @@ tolerances as the single-scene tests."""
 import numpy as np
 import pytest
 
+from _parity import direction_entry, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -28,10 +29,6 @@ def O(oracle_mod):
     return oracle_mod
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
-
-
 def small_batch(seed=5, n_scenes=6):
     """Six cubes of 2 to 4 cells per side, a few millimetres above the plane (they reach it within two steps)."""
     sc = S.batched(n_scenes=n_scenes, seed=seed, n_min=2, n_max=4, cell=0.0125, spacing=0.2, steps=4, iters=12)
@@ -46,11 +43,13 @@ def small_batch(seed=5, n_scenes=6):
 def batched_lockstep(B, O, sim, sc, iters, prec):
     """Lock-step iterations of one time step: after every GPU iteration each scene's gradient, preconditioner,
     direction, p^T H p, max |p_v|, step and update are compared with the oracle of that scene from the GPU's own
-    inputs (as in the single-scene protocol).  Returns the worst relative errors over scenes and iterations."""
+    inputs (as in the single-scene protocol), as relative 2-norms, entry by entry and over contact vertices.
+    Returns the worst errors over scenes and iterations."""
     ranges = sc.scene_ranges()
     oracles = [O.Oracle.from_scene(sc.subscene(s)) for s in range(len(ranges))]
     B.sim_begin_step(sim.h, None)
-    keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx")
+    keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "g_entry", "P_entry", "g_contact", "P_contact", "p_entry",
+            "dx_entry")
     worst = dict.fromkeys(keys, 0.0)
     for k in range(iters):
         x, g, P, p, xt, _ = B.sim_get_iterate(sim.h)
@@ -69,6 +68,9 @@ def batched_lockstep(B, O, sim, sc, iters, prec):
             e = dict(g=rel(g1[sl], go), P=rel(P1[sl], Po), p=rel(p1[sl].ravel(), pd),
                      pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref), pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref,
                      alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref), dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]))
+            e.update(grad_errors(o, x[sl], xt[sl], g1[sl], go, P=P1[sl], Po=Po))
+            e["p_entry"] = direction_entry(p1[sl], P1[sl], g1[sl], scal["beta"][s], p[sl])
+            e["dx_entry"] = update_entry(x1[sl], x[sl], scal["alpha"][s], p1[sl])
             for kk in worst:
                 worst[kk] = max(worst[kk], e[kk])
     B.sim_end_step(sim.h)
@@ -145,6 +147,8 @@ def test_batched_full_size_256_scenes(B, O):
         go, Po, po = g[sl].copy(), P[sl].copy(), p[sl].copy()
         o.iteration(x[sl].copy(), xt[sl], go, Po, po, 0)
         assert rel(g1[sl], go) < TOL[1], s
+        for k, v in grad_errors(o, x[sl], xt[sl], g1[sl], go, P=P1[sl], Po=Po).items():
+            assert v < TOL[1], (s, k, v)
         assert abs(scal["pHp"][s] - o.pHp(x[sl], p1[sl])) / abs(o.pHp(x[sl], p1[sl])) < TOL[1], s
     B.sim_end_step(sim.h)
     sim.close()

@@ -6,6 +6,7 @@ with contacts, then lock-step iterations of a contact step, at the single-scene 
 import numpy as np
 import pytest
 
+from _parity import direction_entry, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -28,10 +29,6 @@ def B():
 @pytest.fixture(scope="module")
 def O(oracle_mod):
     return oracle_mod
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def deformed_blocks(seed):
@@ -64,6 +61,8 @@ def test_gradient_diag_pHp_energy(B, O, model, prec, seed):
     assert na > 0, "contacts active"
     assert rel(g, go) < TOL[prec], rel(g, go)
     assert rel(d, do) < TOL[prec], rel(d, do)
+    for k, v in grad_errors(o, x, xt, g, go, d, do).items():
+        assert v < TOL[prec], (k, v)
     for _ in range(2):
         p = rng.normal(size=x.shape)
         assert abs(B.sim_eval_pHp(sim.h, x, p) - o.pHp(x, p)) / abs(o.pHp(x, p)) < TOL[prec]
@@ -80,18 +79,21 @@ def test_lockstep_contact_step(B, O, model, prec):
     o = O.Oracle.from_scene(sc, model=model)
     sim.step(1)
     B.sim_begin_step(sim.h, None)
-    worst = dict.fromkeys(("g", "P", "p", "pHp", "alpha", "dx"), 0.0)
+    worst = dict.fromkeys(("g", "P", "p", "pHp", "alpha", "dx", "g_entry", "P_entry", "g_contact", "P_contact",
+                           "p_entry", "dx_entry"), 0.0)
     for k in range(sc.iters):
         x, g, P, p, xt, _ = B.sim_get_iterate(sim.h)
         xo, go, Po, po = x.copy(), g.copy(), P.copy(), p.copy()
         o.iteration(xo, xt, go, Po, po, k)
         B.sim_iterate(sim.h, 1)
         x1, g1, P1, p1, _, s1 = B.sim_get_iterate(sim.h)
-        pd = O.ncg_direction(g1, P1, g, P, p, k, 0)[0]
+        pd, beta = O.ncg_direction(g1, P1, g, P, p, k, 0)[:2]
         pHp_ref = o.pHp(x, p1)
         a_ref = O.ncg_alpha(s1["gp"], s1["pHp"], s1["pmax"], sc.dhat)[0]
         e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
-                 alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1))
+                 alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1),
+                 p_entry=direction_entry(p1, P1, g1, s1["beta"], p), dx_entry=update_entry(x1, x, s1["alpha"], p1))
+        e.update(grad_errors(o, x, xt, g1, go, P=P1, Po=Po))
         for kk in worst:
             worst[kk] = max(worst[kk], e[kk])
     B.sim_end_step(sim.h)

@@ -1,12 +1,15 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
 
-Tolerances are those of the solver's accuracy target: relative 2-norm error of the per-iteration gradient,
-p^T H p and step <= 1e-10 in the FP64 form and <= 1e-5 in the FP32-mixed form; final energy <= 1e-6; active sets
-equal except for pairs within 1e-6 dhat of the cut-off.
+Tolerances are those of the solver's accuracy target: relative error of the per-iteration gradient, p^T H p and
+step <= 1e-10 in the FP64 form and <= 1e-5 in the FP32-mixed form; final energy <= 1e-6; active sets equal except
+for pairs within 1e-6 dhat of the cut-off.  Vectors are checked three ways at that tolerance: the relative 2-norm
+over all entries, every entry against the sum of the magnitudes of the contributions that make it up (tests/_parity),
+and the relative 2-norm over the entries of contact vertices alone.
 """
 import numpy as np
 import pytest
 
+from _parity import direction_entry, entrywise, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -28,10 +31,6 @@ def B():
 @pytest.fixture(scope="module")
 def O(oracle_mod):
     return oracle_mod
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def lowered_cube(cells=(7, 5, 9)):
@@ -73,6 +72,8 @@ def test_gradient_diag_pHp_energy(B, O, name, make, prec):
     go, do, na = o.grad_diag(x, xt)
     assert rel(g, go) < TOL[prec], rel(g, go)
     assert rel(d, do) < TOL[prec], rel(d, do)
+    for k, v in grad_errors(o, x, xt, g, go, d, do).items():
+        assert v < TOL[prec], (k, v)
     # active set: equal up to pairs at the cut-off
     idx, dist = B.sim_get_contacts(sim.h)
     oi, od, _ = o.active_pairs(x)
@@ -98,6 +99,61 @@ def test_gradient_diag_pHp_energy(B, O, name, make, prec):
     sim.close()
 
 
+def near_contact(frac=1e-4, dhat=1e-3, L=0.01):
+    """Two tets at distance frac * dhat: B's lowest vertex b0 over the interior of A's top face (z = 0), and B's
+    bottom edge (b0, b1) crossing A's face diagonal above its midpoint (a point-triangle and an edge-edge pair whose
+    closest points are interior); A's lowest vertex frac * dhat above the plane.  Every other primitive pair is at
+    least 0.25 L (2.5 dhat) apart."""
+    d = frac * dhat
+    A = np.array([[0, 0, 0], [L, 0, 0], [0, L, 0], [0, 0, -L]], float)
+    b0 = np.array([0.25 * L, 0.25 * L, d])
+    Bv = np.array([b0, [0.75 * L, 0.75 * L, d], b0 + [0, 0.5 * L, L], b0 + [0.5 * L, 0, L]])
+    X = np.concatenate([A, Bv])
+    T = np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32)
+    for t in T:
+        if np.linalg.det((X[t[1:]] - X[t[0]]).T) < 0:
+            t[[2, 3]] = t[[3, 2]]
+    return S.Scene(name="near_contact", rest_x=X, tets=T, x0=X.copy(), v0=np.zeros_like(X), youngs=1e5,
+                   poisson=0.4, density=1000.0, dt=1.0 / 60.0, dhat=dhat, kappa=1e4, gravity=(0.0, 0.0, 0.0),
+                   plane=((0.0, 0.0, 1.0), -L - d), iters=5, steps=1)
+
+
+def test_fp32_near_zero_distance_is_evaluated_in_double(B, O):
+    """FP32 form at d = 1e-4 dhat (a point-triangle and an edge-edge pair, and a vertex above the plane): the pairs
+    take the double evaluation of the barrier (the float distance from coordinates of size L carries an error of
+    about 6e-3 of d there), which the step statistics count, and g, diag(H) and p^T H p match the oracle at the FP32
+    tolerance, entry by entry."""
+    sc = near_contact()
+    o = O.Oracle.from_scene(sc)
+    x = sc.x0.copy()
+    xt = x.copy()
+    idx, dist, _ = o.active_pairs(x)
+    kinds = {int(r[0]) for r in idx}
+    assert kinds == {0, 1} and np.all(np.abs(dist - 1e-4 * sc.dhat) < 1e-3 * 1e-4 * sc.dhat), (idx, dist)
+    sim = B.Sim(sc, precision=1)
+    g, d = B.sim_eval_gradient(sim.h, x, xt)
+    _, _, st = sim.state()
+    assert st["n_near_fp64"] >= len(idx), st
+    go, do, na = o.grad_diag(x, xt)
+    assert na == len(idx)
+    for k, v in grad_errors(o, x, xt, g, go, d, do).items():
+        assert v < TOL[1], (k, v)
+    assert rel(g, go) < TOL[1] and rel(d, do) < TOL[1]
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        p = rng.normal(size=x.shape)
+        ref = o.pHp(x, p)
+        assert abs(B.sim_eval_pHp(sim.h, x, p) - ref) / abs(ref) < TOL[1]
+    # a lock-step iteration from there in both forms
+    for prec in (0, 1):
+        s2 = B.Sim(sc, precision=prec)
+        worst = lockstep(B, O, o, s2, sc, 2, prec)
+        for k in CHECKED:
+            assert worst[k] < TOL[prec], (prec, k, {kk: f"{v:.3e}" for kk, v in worst.items()})
+        s2.close()
+    sim.close()
+
+
 def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
     """Runs `iters` iterations of one step on the GPU; at every iteration the oracle repeats each kernel's work
     from the GPU's own inputs and the worst relative errors are returned:
@@ -107,9 +163,12 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
       pmax  : the largest per-vertex length of the GPU's direction
       alpha : step rule from the GPU's g^T p, p^T H p and max |p_v|
       dx    : the update alpha p
-    plus `chain_p`: the oracle's direction from its own g_{k+1} (rounding of g amplified through beta)."""
+    each vector also entry by entry (g_entry, P_entry, p_entry, dx_entry) and over the contact vertices' entries
+    (g_contact, P_contact), plus `chain_p`: the oracle's direction from its own g_{k+1} (rounding of g amplified
+    through beta)."""
     B.sim_begin_step(sim.h, targets)
-    keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "chain_p")
+    keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "chain_p", "g_entry", "P_entry", "g_contact", "P_contact",
+            "p_entry", "dx_entry")
     worst = dict.fromkeys(keys, 0.0)
     fixed = sc.fixed.astype(bool) if sc.fixed is not None else np.zeros(sc.n_verts, bool)
     for k in range(iters):
@@ -126,6 +185,9 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
         e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
                  pmax=abs(s1["pmax"] - pm_ref) / pm_ref,
                  alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1), chain_p=rel(p1, po))
+        e.update(grad_errors(o, x, xt, g1, go, P=P1, Po=Po, fixed=fixed))
+        e["p_entry"] = direction_entry(p1, P1, g1, s1["beta"], p)
+        e["dx_entry"] = update_entry(x1, x, s1["alpha"], p1)
         for kk in worst:
             worst[kk] = max(worst[kk], e[kk])
     B.sim_end_step(sim.h)
@@ -136,7 +198,8 @@ def o_rule(sc):
     return 0
 
 
-CHECKED = ("g", "P", "p", "pHp", "pmax", "alpha", "dx")
+CHECKED = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "g_entry", "P_entry", "g_contact", "P_contact", "p_entry",
+           "dx_entry")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -271,6 +334,23 @@ def test_twisted_bar_full_size(B, O, prec):
     fx = sc.fixed.astype(bool)
     np.testing.assert_allclose(x[fx], sc.targets(1), rtol=0, atol=1e-15)
     worst = lockstep(B, O, o, sim, sc, 2, prec, targets=sc.targets(2))
+    for k in CHECKED:
+        assert worst[k] < TOL[prec], (k, {kk: f"{v:.3e}" for kk, v in worst.items()})
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_twisted_bar_full_size_in_the_timed_window(B, O, prec):
+    """The 98,304-tet twisted bar at the start of step 100 (the benchmark's timed window, steps 100-119, where the
+    twist has brought tens of thousands of surface pairs within dhat + r): 100 steps through the graph path, then two
+    lock-step iterations of step 100 at full size, entry by entry."""
+    sc = S.twisted_bar()
+    sim = B.Sim(sc, precision=prec)
+    sim.step(100, sc.all_targets(100))
+    x, v, st = sim.state()
+    assert st["step"] == 100 and st["n_candidates"] > 10000, st
+    o = O.Oracle.from_scene(sc)
+    worst = lockstep(B, O, o, sim, sc, 2, prec, targets=sc.targets(100))
     for k in CHECKED:
         assert worst[k] < TOL[prec], (k, {kk: f"{v:.3e}" for kk, v in worst.items()})
     sim.close()

@@ -5,6 +5,7 @@ precisions and with both beta rules; plus the candidate pass pairing primitives 
 import numpy as np
 import pytest
 
+from _parity import direction_entry, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -28,10 +29,6 @@ def O(oracle_mod):
     return oracle_mod
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
-
-
 def _key(row):
     t, a, b, c, d = (int(v) for v in row)
     if t == 0:
@@ -47,11 +44,12 @@ def _offsets(sc):
 def split_lockstep(B, O, sim, sc, iters, rule):
     """After every GPU iteration: the gradient and preconditioner against the oracle's, and per object the
     direction, p_o^T H p_o (the oracle's pHp of the GPU's p with the other objects' entries zero), max |p_v|, the
-    step and the update.  Returns the worst relative errors."""
+    step and the update, as relative 2-norms, entry by entry and over contact vertices.  Returns the worst errors."""
     off = _offsets(sc)
     o = O.Oracle.from_scene(sc, beta_rule=rule)
     B.sim_begin_step(sim.h, None)
-    worst = dict.fromkeys(("g", "P", "p", "pHp", "pmax", "alpha", "dx"), 0.0)
+    worst = dict.fromkeys(("g", "P", "p", "pHp", "pmax", "alpha", "dx", "g_entry", "P_entry", "g_contact",
+                           "P_contact", "p_entry", "dx_entry"), 0.0)
     cross = 0
     for k in range(iters):
         x, g, P, p, xt, _ = B.sim_get_iterate(sim.h)
@@ -61,9 +59,10 @@ def split_lockstep(B, O, sim, sc, iters, rule):
         xo, go, Po, po = x.copy(), g.copy(), P.copy(), p.copy()
         o.iteration_split(xo, xt, go, Po, po, off, [{"k": k, "dE0": 0.0}] * (len(off) - 1))
         e = dict(g=rel(g1, go), P=rel(P1, Po))
+        e.update(grad_errors(o, x, xt, g1, go, P=P1, Po=Po))
         for s in range(len(off) - 1):
             sl = slice(off[s], off[s + 1])
-            pd = O.ncg_direction(g1[sl], P1[sl], g[sl], P[sl], p[sl], k, rule)[0]
+            pd, beta = O.ncg_direction(g1[sl], P1[sl], g[sl], P[sl], p[sl], k, rule)[:2]
             pm = np.zeros_like(p1)
             pm[sl] = p1[sl]
             pHp_ref = o.pHp(x, pm)
@@ -71,7 +70,9 @@ def split_lockstep(B, O, sim, sc, iters, rule):
             a_ref = O.ncg_alpha(scal["gp"][s], scal["pHp"][s], scal["pmax"][s], sc.dhat)[0]
             es = dict(p=rel(p1[sl].ravel(), pd), pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref),
                       pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref, alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref),
-                      dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]))
+                      dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]),
+                      p_entry=direction_entry(p1[sl], P1[sl], g1[sl], scal["beta"][s], p[sl]),
+                      dx_entry=update_entry(x1[sl], x[sl], scal["alpha"][s], p1[sl]))
             e.update({kk: max(e.get(kk, 0.0), v) for kk, v in es.items()})
         for kk in worst:
             worst[kk] = max(worst[kk], e[kk])

@@ -220,3 +220,39 @@ def test_inverted_tet_is_an_error(oracle_mod):
     with pytest.raises(oracle_mod.OracleError) as ei:
         o.grad_diag(x, x)
     assert ei.value.status == 2
+
+
+def test_grad_diag_scale_sums_each_tets_contribution_by_magnitude(oracle_mod):
+    """The per-entry scale of the parity tests.  For a tet, the force on vertex i is -h^2 V P w_i with P the first
+    Piola-Kirchhoff stress of Neo-Hookean, mu (F - F^-T) + lambda log J F^-T, and w_i the i-th row of Dm^-1 (w_0 the
+    negated sum of the rows); its scale, for each of the vertex's three entries, is h^2 V |P|_F |w_i|, computed here
+    with numpy.  For two tets sharing a face, with x~ = x (no inertia force), the scale of each vertex is the sum over
+    the tets that use it; the inertia adds m |x - x~|; and the scales bound |g| and |diag| from above."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], float) * 0.01
+    T = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], np.int32)
+    if np.linalg.det((X[T[1, 1:]] - X[T[1, 0]]).T) < 0:
+        T[1, [1, 2]] = T[1, [2, 1]]
+    rng = np.random.default_rng(3)
+    x = X + 1e-3 * rng.normal(size=X.shape)
+    E, nu, rho, h = 1e5, 0.4, 1000.0, 0.01
+    mu, lam = E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+    o = oracle_mod.Oracle(X, T, youngs=E, poisson=nu, density=rho, dt=h, dhat=1e-4, kappa=1e4)
+    g, d, _ = o.grad_diag(x, x)
+    gs, ds = o.grad_diag_scale(x, x)
+    want = np.zeros_like(x)
+    for t in T:
+        Dm = (X[t[1:]] - X[t[0]]).T
+        W = np.linalg.inv(Dm)
+        F = (x[t[1:]] - x[t[0]]).T @ W
+        Fit = np.linalg.inv(F).T
+        P = mu * (F - Fit) + lam * np.log(np.linalg.det(F)) * Fit
+        V = np.linalg.det(Dm) / 6.0
+        w = np.vstack([-W.sum(axis=0), W])          # w_i[b] = dF_ab / dx_ia
+        for i in range(4):
+            want[t[i]] += h * h * V * np.linalg.norm(P) * np.linalg.norm(w[i])
+    np.testing.assert_allclose(gs, want, rtol=1e-10)
+    assert np.all(gs >= np.abs(g) * (1 - 1e-14)) and np.all(ds >= np.abs(d) * (1 - 1e-14))
+    xt = x + 1e-4 * rng.normal(size=x.shape)
+    gs2, _ = o.grad_diag_scale(x, xt)
+    m = o.mass()[:, None]
+    np.testing.assert_allclose(gs2, want + m * np.linalg.norm(x - xt, axis=1, keepdims=True), rtol=1e-10)
