@@ -123,8 +123,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def method_bytes(prec: int, n_tets: int, n_verts: int, n_active: int, per_tet_youngs: bool = False) -> int:
+    """Algorithmic bytes of one NCG iteration of the method (not of this implementation): every array of the
+    iteration crossing DRAM once per pass.  Per tet, the two element passes (gradient + Jacobi diagonal, p^T H p)
+    each read the 4 indices, D_m^-1 and the rest volume: 2 (16 + 10 r) B with r the element size, i.e. 112 B in FP32
+    and 192 B in FP64, plus 2 r B for a per-tet Young's modulus.  Per vertex 196 B in FP32 and 392 B in FP64: the
+    gradient pass (x, x~, m read; g, diag written), the beta pass (g, diag, g_old, p_old), the direction pass, the p
+    gather and the x update.  Per active pair 34 B (the pair's index list written and read, and its type)."""
+    r = 4 if prec == 1 else 8
+    per_tet = 2 * (16 + 10 * r) + (2 * r if per_tet_youngs else 0)
+    per_vert = 196 if prec == 1 else 392
+    return n_tets * per_tet + n_verts * per_vert + 34 * n_active
+
+
 def algorithmic_bytes(kernel: str, prec: int, sizes: dict, n_cand: int, n_active: int, persistent: bool = False):
-    """Bytes a phase must move at least once (every array read or written counted once).
+    """Bytes a phase of this implementation moves at least once (every array read or written counted once): the
+    implementation's own count, reported beside the method's (method_bytes).
 
     Vertex state: x (double4, 32 B) and, in the FP32 form, its float-float copy (2 x float4); accumulators g, diag
     and the directions are 4-vectors of the element type (16 B float, 32 B double).  Per tet: 4 indices (16 B),
@@ -161,10 +175,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, prec_name: str, phases: bool = False):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
+def recorded_traffic(kernel: str, prec_name: str, phases: bool = False, scene: str = "twisted_bar"):
+    """DRAM bytes per launch from the committed ncu summary of that kernel and workload, if it was taken on the
+    current kernel sources (the summary's dram_bytes_per_launch line, scaled to a full launch where it says so)."""
     form = "_phases" if phases else ""
-    path = os.path.join(ROOT, "profiles", f"{kernel}{form}_twisted_bar_{prec_name}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}{form}_{scene}_{prec_name}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -213,6 +228,121 @@ def time_steps(B, torch, sim, targets, first, K, flush, cfg_steps):
     return times
 
 
+def timed_window(B, torch, sim, stream, flush, first, K, targets=None):
+    """K steps from the current state (step `first`), each bracketed by CUDA events on the solver's stream, L2
+    flushed before each (not timed).  Returns per-step milliseconds."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    keep = []
+    for s in range(K):
+        flush.zero_()
+        ev[s][0].record(stream)
+        keep.append(B.sim_step_async(sim.h, 1, None if targets is None else targets[first + s]))
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def side_workload(B, torch, S, stream, flush, sc, name, desc, unit_scale, unit, K, peak, peak_kind, phases,
+                  per_tet_youngs):
+    """One of the workloads whose working set exceeds L2 (the large pile, the batch): the run's lead-in untimed, then
+    the K last steps of its configured run timed, then one profiled step; the HBM roofline from the method's bytes."""
+    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream, persistent=0 if phases else 1)
+    first = max(3, sc.steps - K)
+    try:
+        for s in range(first):
+            B.sim_step_async(sim.h, 1, None)
+        torch.cuda.synchronize()
+        B.sim_get_state(sim.h, want_x=False, want_v=False)
+        times = timed_window(B, torch, sim, stream, flush, first, K)
+        _, _, st = B.sim_get_state(sim.h, want_x=False, want_v=False)
+        prof = B.sim_profile_step(sim.h, None)
+    except B.SimError as e:
+        sim.close()
+        return {"workload": desc, "error": str(e)}
+    sizes = sim.sizes()
+    sim.close()
+    ms = sum(times) / K
+    mb = st["iters_done"] * method_bytes(1, sizes["n_tets"], sizes["n_verts"], st["n_active"], per_tet_youngs)
+    ib = sum(algorithmic_bytes(k, 1, sizes, st["n_candidates"], st["n_active"], persistent=not phases) * prof[k][1]
+             for k in ("k_grad", "k_pHp", "k_dots", "k_dir", "k_update") if prof.get(k, (0, 0))[1] > 0)
+    ach = mb / (ms * 1e-3) / 1e9
+    return {"workload": desc, "value": round(unit_scale * sc.iters / (ms * 1e-3), 2), "unit": unit,
+            "ms_per_step": round(ms, 4), "time_steps_per_s": round(1e3 / ms, 2), "steps": K,
+            "timed_steps": f"{first}..{first + K - 1} of the {sc.steps}-step run (its last steps), "
+                           f"steps 0..{first - 1} untimed",
+            "roofline": {"bound": "hbm", "kernel": "k_persistent" if not phases else "all iteration kernels",
+                         "achieved": round(ach, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": recorded_traffic("k_persistent", "fp32", scene=name),
+                         "algorithmic_bytes_per_launch": int(mb), "implementation_bytes_per_launch": int(ib),
+                         "bytes_basis": "method bytes per iteration x iterations per step (candidate builds not "
+                                        "counted)"},
+            "phases_us_per_iteration": {k: round(1e3 * v[0] / v[1], 2) for k, v in prof.items()
+                                        if v[1] > 0 and k.startswith("k_")},
+            "stats_last_step": {k: st[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")}}
+
+
+def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, repeat=3):
+    """FP32-mixed against plain FP64 at equal final-energy accuracy on one time step (the benchmark spec's comparison).
+
+    From a saved state, the step is run in each form with K NCG iterations for K in `ks`, and once in FP64 with
+    `kref` iterations as the converged reference x*.  Every end state's energy is evaluated by the FP64 oracle, and
+    its error is err(K) = (E(x_K) - E(x*)) / (E(x_0) - E(x*)), x_0 the step's start (kinematic targets applied).  The
+    target is the plain FP64 form's error at the headline iteration count ks[1]; each form's cost is the time of the
+    fewest iterations in `ks` that reach it (each (form, K) timed `repeat` times from the saved state)."""
+    o = O.Oracle.from_scene(sc)
+    x0, v0 = state
+    fixed = sc.fixed.astype(bool) if sc.fixed is not None else None
+    res = {}
+
+    def run(prec, K, timed):
+        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, iters=K, persistent=1)
+        ms = []
+        try:
+            for r in range(repeat if timed else 1):
+                B.sim_set_state(sim.h, x0, v0)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                keep = B.sim_step_async(sim.h, 1, targets)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            x, _, st = B.sim_get_state(sim.h)
+            xt = B.sim_get_iterate(sim.h)[4]
+        finally:
+            sim.close()
+        return x, xt, (min(ms) if timed else None), st
+
+    xr, xt, _, _ = run(B.SIM_FP64, kref, False)
+    Eref = o.energy(xr, xt)[0]
+    xs = x0.copy()
+    if fixed is not None and targets is not None:
+        xs[fixed] = targets
+    E0 = o.energy(xs, xt)[0]
+    for prec, pname in ((B.SIM_FP64, "fp64"), (B.SIM_FP32_MIXED, "fp32_mixed")):
+        rows = []
+        for K in ks:
+            x, xt2, ms, st = run(prec, K, True)
+            E = o.energy(x, xt2)[0]
+            rows.append({"iters": K, "ms": round(ms, 4), "energy_err": (E - Eref) / (E0 - Eref)})
+        res[pname] = rows
+    target = res["fp64"][1]["energy_err"]
+
+    def cost(rows):
+        for r in rows:
+            if r["energy_err"] <= target * (1 + 1e-9):
+                return r
+        return None
+    c64, c32 = cost(res["fp64"]), cost(res["fp32_mixed"])
+    return {"workload": name, "reference": f"FP64, {kref} iterations (x*); energies by the FP64 oracle",
+            "error": "(E(x_K) - E(x*)) / (E(x_0) - E(x*))", "target_err": target,
+            "fp64": res["fp64"], "fp32_mixed": res["fp32_mixed"],
+            "fp64_ms_at_target": c64["ms"] if c64 else None, "fp32_ms_at_target": c32["ms"] if c32 else None,
+            "fp64_iters_at_target": c64["iters"] if c64 else None,
+            "fp32_iters_at_target": c32["iters"] if c32 else None,
+            "speedup_fp32_over_fp64": round(c64["ms"] / c32["ms"], 3) if (c64 and c32) else None}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -240,6 +370,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)
     sampler.start()
+    peak, peak_kind = measured_peaks()
 
     def one_form(prec, K_, form=1):
         sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else form)
@@ -262,8 +393,8 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(t32))
     value = job_value(ws, K, iters, total_ms)
 
-    # kernel-by-kernel GPU times of three more steps (after the timed region) for the roofline; they continue the
-    # run from the state the timed window left
+    # kernel-by-kernel GPU times of three more steps (after the timed region); they continue the run from the state
+    # the timed window left
     after = first + (K - 1) % max(1, cfg_steps - first) + 1
     prof = {}
     for s in range(3):
@@ -274,34 +405,37 @@ def run_ours(args):
     sizes = sim32.sizes()
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     step_ms = sum(v[0] for v in prof.values()) / 3
-    peak, peak_kind = measured_peaks()
     iter_kernels = ("k_grad", "k_pHp", "k_dots", "k_dir", "k_update")
     phase_bw = {}
     for k in iter_kernels:
         if prof.get(k, (0, 0))[1] > 0:
             b = algorithmic_bytes(k, 1, sizes, stp["n_candidates"], stp["n_active"], persistent=not args.phases)
             phase_bw[k] = round(b / (prof[k][0] / prof[k][1] * 1e-3) / 1e9, 1)
+    n_act = st32["n_active"]
     if args.phases:
-        # the dominant iteration kernel
+        # the dominant iteration kernel; its method bytes are the iteration's share that kernel moves
         dom_all = dom
         dom = max((k for k in iter_kernels if prof.get(k, (0, 0))[1] > 0), key=lambda k: prof[k][0])
         per_launch_ms = prof[dom][0] / prof[dom][1]
-        abytes = algorithmic_bytes(dom, 1, sizes, stp["n_candidates"], stp["n_active"])
+        ibytes = algorithmic_bytes(dom, 1, sizes, stp["n_candidates"], stp["n_active"])
+        mbytes = method_bytes(1, sizes["n_tets"], sizes["n_verts"], n_act) * ibytes / sum(
+            algorithmic_bytes(k, 1, sizes, stp["n_candidates"], stp["n_active"]) for k in iter_kernels)
         traffic = recorded_traffic(dom, "fp32", phases=True)
     else:
-        # the persistent kernel: one launch per time step; its algorithmic bytes are those of the iteration
-        # phases it ran (the candidate build is not counted), its duration the timed step
+        # the persistent kernel: one launch per time step; the method's bytes of its iterations (the candidate
+        # build not counted) over the timed step
         dom_all = dom
         dom = "k_persistent"
         per_launch_ms = total_ms / K
-        abytes = sum(algorithmic_bytes(k, 1, sizes, stp["n_candidates"], stp["n_active"], persistent=True) * prof[k][1] / 3
+        mbytes = st32["iters_done"] * method_bytes(1, sizes["n_tets"], sizes["n_verts"], n_act)
+        ibytes = sum(algorithmic_bytes(k, 1, sizes, stp["n_candidates"], stp["n_active"], persistent=True) * prof[k][1] / 3
                      for k in iter_kernels if prof.get(k, (0, 0))[1] > 0)
         traffic = recorded_traffic(dom, "fp32")
-    achieved = abytes / (per_launch_ms * 1e-3) / 1e9
+    achieved = mbytes / (per_launch_ms * 1e-3) / 1e9
     kernels = {k: {"ms_per_step": round(v[0] / 3, 4), "launches_per_step": v[1] // 3,
                    "us_per_launch": round(1e3 * v[0] / v[1], 3) if v[1] else None,
                    "share": round(v[0] / 3 / step_ms, 4) if step_ms > 0 else None,
-                   **({"achieved_gbs": phase_bw[k]} if k in phase_bw else {})}
+                   **({"implementation_gbs": phase_bw[k]} if k in phase_bw else {})}
                for k, v in prof.items() if v[1] > 0}
     sim32.close()
 
@@ -340,7 +474,8 @@ def run_ours(args):
     iter150 = None if args.no_extras else iter_max_150()
 
     # PR+ against DK (Sec. 4.1): the whole run step by step, untimed; per step the last iteration's energy
-    # decrease relative to the first (the convergence measure of the stopping rule in Sec. 4.4)
+    # decrease relative to the first (the convergence measure of the stopping rule in Sec. 4.4); the FP64 form's
+    # state at the start of step 100 is kept for the equal-accuracy comparison
     conv = None if args.no_extras else {}
     for name, beta in ((("pr_plus", B.SIM_BETA_PR_PLUS), ("dk", B.SIM_BETA_DK)) if not args.no_extras else ()):
         simc = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
@@ -362,103 +497,65 @@ def run_ours(args):
                       "worst_dE_last_over_dE0": float(10 ** lr.max()), "steps": len(ratios),
                       **({"error": err} if err else {})}
 
+    # FP32-mixed against plain FP64 at equal final-energy accuracy (twisted bar step 100 and the batch's step 30)
+    eq = None
+    if not args.no_extras and not args.phases and rank == 0:
+        import oracle as O
+        simr = B.Sim(sc, precision=B.SIM_FP64, cuda_stream=stream.cuda_stream, persistent=1)
+        for s in range(100):
+            B.sim_step_async(simr.h, 1, targets[s])
+        xb, vb, _ = B.sim_get_state(simr.h)
+        simr.close()
+        eq = {"twisted_bar": equal_accuracy(B, torch, O, sc, stream, (xb, vb), sc.targets(100), (25, 50, 75, 100),
+                                            1000, "twisted bar, time step 100 (from the FP64 form's state)")}
+        if not args.no_pile:
+            bsc = S.batched()
+            simr = B.Sim(bsc, precision=B.SIM_FP64, cuda_stream=stream.cuda_stream, persistent=1)
+            for s in range(30):
+                B.sim_step_async(simr.h, 1, None)
+            xb, vb, _ = B.sim_get_state(simr.h)
+            simr.close()
+            eq["batched"] = equal_accuracy(B, torch, O, bsc, stream, (xb, vb), None, (25, 50, 75, 100), 400,
+                                           "batched, 256 scenes, time step 30 (from the FP64 form's state)", repeat=2)
+
     # end to end through the C ABI with host buffers: pinned targets in, positions out, every step (the step is
     # enqueued with sim_step_async; sim_get_state copies the positions out, synchronises and reports any error of
     # the step: one synchronisation per step)
-    e2e = None
-    if True:
-        sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
-        tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
-        x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
-        for s in range(first):
-            B.sim_step_async(sim.h, 1, tg_host[s])
-            B.sim_get_state(sim.h, x_out=x_host, want_v=False)
-        span = max(1, cfg_steps - first)
-        saved = B.sim_get_state(sim.h)[:2] if K > span else None
-        te = 0.0
-        for s in range(K):
-            if s > 0 and s % span == 0:
-                B.sim_set_state(sim.h, *saved)   # not timed, as in the device-timed window
-            t0 = time.perf_counter()
-            B.sim_step_async(sim.h, 1, tg_host[first + s % span])
-            B.sim_get_state(sim.h, x_out=x_host, want_v=False)
-            te += time.perf_counter() - t0
-        sim.close()
-        e2e = {"value": round(K * iters / te, 2), "unit": UNIT, "ms_per_step": round(1e3 * te / K, 4),
-               "h2d_bytes_per_step": int(tg_host[0].numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 8)}
-    # the large pile (ten 16x16x64 bars, 983,040 tets): the same kernels at a size whose working set exceeds L2
-    pile = None
-    if not args.no_pile:
-        psc = S.pile()
-        psim = B.Sim(psc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream,
-                     persistent=0 if args.phases else 1)
-        PW, PK = 3, 5
-        for s in range(PW):
-            B.sim_step_async(psim.h, 1, None)
-        torch.cuda.synchronize()
-        B.sim_get_state(psim.h, want_x=False, want_v=False)
-        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(PK)]
-        for s in range(PK):
-            flush.zero_()
-            pev[s][0].record(stream)
-            B.sim_step_async(psim.h, 1, None)
-            pev[s][1].record(stream)
-        torch.cuda.synchronize()
-        pms = sum(a.elapsed_time(b) for a, b in pev) / PK
-        pprof = B.sim_profile_step(psim.h, None)
-        _, _, pst = B.sim_get_state(psim.h, want_x=False, want_v=False)
-        psizes = psim.sizes()
-        pbytes = sum(algorithmic_bytes(k, 1, psizes, pst["n_candidates"], pst["n_active"], persistent=not args.phases)
-                     * pprof[k][1] for k in ("k_grad", "k_pHp", "k_dots", "k_dir", "k_update") if pprof.get(k, (0, 0))[1] > 0)
-        pach = pbytes / (pms * 1e-3) / 1e9
-        pile = {"workload": "large pile: ten 16x16x64-cell bars (983,040 tets, 187,850 verts) stacked criss-cross on "
-                            "a plane, E=2e5 nu=0.4, dt=1/30, dhat=5e-4, 50 NCG iterations per step, FP32-mixed",
-                "value": round(psc.iters / (pms * 1e-3), 2), "unit": UNIT, "ms_per_step": round(pms, 4),
-                "steps": PK, "warmup": PW,
-                "roofline": {"bound": "hbm", "kernel": "k_persistent" if not args.phases else "all iteration kernels",
-                             "achieved": round(pach, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                             "frac": round(pach / peak, 4), "algorithmic_bytes_per_step": int(pbytes)},
-                "phases_us_per_iteration": {k: round(1e3 * v[0] / v[1], 2) for k, v in pprof.items()
-                                            if v[1] > 0 and k.startswith("k_")},
-                "stats_last_step": {k: pst[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")}}
-        psim.close()
+    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
+    tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
+    x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
+    for s in range(first):
+        B.sim_step_async(sim.h, 1, tg_host[s])
+        B.sim_get_state(sim.h, x_out=x_host, want_v=False)
+    span = max(1, cfg_steps - first)
+    saved = B.sim_get_state(sim.h)[:2] if K > span else None
+    te = 0.0
+    for s in range(K):
+        if s > 0 and s % span == 0:
+            B.sim_set_state(sim.h, *saved)   # not timed, as in the device-timed window
+        t0 = time.perf_counter()
+        B.sim_step_async(sim.h, 1, tg_host[first + s % span])
+        B.sim_get_state(sim.h, x_out=x_host, want_v=False)
+        te += time.perf_counter() - t0
+    sim.close()
+    e2e = {"value": round(K * iters / te, 2), "unit": UNIT, "ms_per_step": round(1e3 * te / K, 4),
+           "h2d_bytes_per_step": int(tg_host[0].numel() * 8), "d2h_bytes_per_step": int(x_host.numel() * 8)}
 
-    # the batched config: 256 independent cubes (2,184,876 tets) in one persistent launch, per-scene beta / alpha
-    batched = None
-    if not args.no_pile and not args.phases:
-        bsc = S.batched()
-        bsim = B.Sim(bsc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream, persistent=1)
-        BW, BK = 3, 5
-        for s in range(BW):
-            B.sim_step_async(bsim.h, 1, None)
-        torch.cuda.synchronize()
-        B.sim_get_state(bsim.h, want_x=False, want_v=False)
-        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(BK)]
-        for s in range(BK):
-            flush.zero_()
-            bev[s][0].record(stream)
-            B.sim_step_async(bsim.h, 1, None)
-            bev[s][1].record(stream)
-        torch.cuda.synchronize()
-        bms = sum(a.elapsed_time(b) for a, b in bev) / BK
-        bprof = B.sim_profile_step(bsim.h, None)
-        _, _, bst = B.sim_get_state(bsim.h, want_x=False, want_v=False)
-        bsizes = bsim.sizes()
-        bbytes = sum(algorithmic_bytes(k, 1, bsizes, bst["n_candidates"], bst["n_active"], persistent=True)
-                     * bprof[k][1] for k in ("k_grad", "k_pHp", "k_dots", "k_update") if bprof.get(k, (0, 0))[1] > 0)
-        bach = bbytes / (bms * 1e-3) / 1e9
-        batched = {"workload": "batched: 256 independent cubes of n^3 cells, n ~ U{4..16} (2,184,876 tets, "
-                               "459,790 verts), random rotations, 0.01-0.05 m over a plane, E ~ U[5e4, 5e5], "
-                               "dt=1/60, dhat=1e-3, 50 NCG iterations per step, per-scene beta and alpha, FP32-mixed",
-                   "value": round(bsc.n_scenes * bsc.iters / (bms * 1e-3), 1), "unit": "scene-iterations/s",
-                   "ms_per_step": round(bms, 4), "time_steps_per_s": round(1e3 / bms, 2), "steps": BK, "warmup": BW,
-                   "roofline": {"bound": "hbm", "kernel": "k_persistent", "achieved": round(bach, 1), "peak": peak,
-                                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(bach / peak, 4),
-                                "algorithmic_bytes_per_step": int(bbytes)},
-                   "phases_us_per_iteration": {k: round(1e3 * v[0] / v[1], 2) for k, v in bprof.items()
-                                               if v[1] > 0 and k.startswith("k_")},
-                   "stats_last_step": {k: bst[k] for k in ("n_candidates", "n_active", "n_rebuilds")}}
-        bsim.close()
+    # the large pile and the batch: the same kernels at sizes whose working set exceeds L2, timed on the last steps
+    # of their configured runs
+    pile = batched = None
+    if not args.no_pile:
+        pile = side_workload(B, torch, S, stream, flush, S.pile(), "large_pile",
+                             "large pile: ten 16x16x64-cell bars (983,040 tets, 187,850 verts) stacked criss-cross "
+                             "on a plane, E=2e5 nu=0.4, dt=1/30, dhat=5e-4, 50 NCG iterations per step, FP32-mixed",
+                             1, UNIT, 5, peak, peak_kind, args.phases, False)
+        if not args.phases:
+            bsc = S.batched()
+            batched = side_workload(B, torch, S, stream, flush, bsc, "batched",
+                                    "batched: 256 independent cubes of n^3 cells, n ~ U{4..16} (2,184,876 tets, "
+                                    "459,790 verts), random rotations, 0.01-0.05 m over a plane, E ~ U[5e4, 5e5], "
+                                    "dt=1/60, dhat=1e-3, 50 NCG iterations per step, per-scene beta and alpha, "
+                                    "FP32-mixed", bsc.n_scenes, "scene-iterations/s", 5, peak, peak_kind, False, True)
 
     clocks = sampler.stop()
 
@@ -488,18 +585,23 @@ def run_ours(args):
             "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
                            "launch": "persistent" if st64["launch_form"] == 1 else "one kernel per phase",
                            "launch_choice": "autotuned (options.persistent = 2)" if not args.phases else "per phase",
-                           "speedup_fp32_over_fp64": round(value / ws / v64, 3)},
+                           "speedup_fp32_over_fp64_equal_iterations": round(value / ws / v64, 3)},
+            "fp32_vs_fp64_equal_accuracy": eq,
             "iter_max_150": iter150,
             "beta_convergence": None if conv is None else
             {"note": "whole 120-step run, FP32-mixed, 50 iterations per step, untimed", **conv},
-            "roofline": {"bound": "hbm", "kernel": dom, "largest_phase": dom_all, "achieved": round(achieved, 1), "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": traffic, "algorithmic_bytes_per_launch": int(abytes),
+            "roofline": {"bound": "hbm", "kernel": dom, "largest_phase": dom_all, "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes_per_launch": int(mbytes),
+                         "implementation_bytes_per_launch": int(ibytes),
+                         "bytes_basis": "method bytes per NCG iteration (112 B/tet + 196 B/vertex + 34 B/active "
+                                        "pair, FP32) x the iterations of one launch; candidate builds not counted",
                          "us_per_launch": round(per_launch_ms * 1e3, 3)},
             "kernels": kernels,
             "large_pile": pile,
             "batched": batched,
-            "stats_last_step": {k: st32[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")},
+            "stats_last_step": {k: st32[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped",
+                                                     "n_near_fp64")},
             "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -507,14 +609,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(sc, budget_s=15.0):
-    """The FP64 oracle as it stands, single-threaded on the host, on a bounded sample of the same workload: NCG
-    iterations of time step 0 of the twisted bar (its contact search included)."""
+BAR_STATE = os.path.join(ROOT, "oracle", "data", "twisted_bar_step100.npz")
+
+
+def _bar_start(sc):
+    """The twisted bar's state at the start of time step 100 (the first step of the GPU's timed window), computed by
+    the oracle alone (oracle/make_bar_state.py); the rest pose at step 0 if the file is missing."""
     import numpy as np
+    if os.path.exists(BAR_STATE):
+        z = np.load(BAR_STATE)
+        return z["x"].copy(), z["v"].copy(), int(z["step"])
+    return sc.x0.copy(), sc.v0.copy(), 0
+
+
+def _oracle_iterations(budget_s, step_first=None):
+    """Worker: NCG iterations of the FP64 oracle on the twisted bar from the step-100 state for budget_s seconds of
+    wall time (at least one); returns (iterations, seconds).  Runs in a process of its own."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
     import oracle
+    from paper_2405_08001_gb300 import scenes as S
+    sc = S.twisted_bar()
     o = oracle.Oracle.from_scene(sc)
-    x, v = sc.x0.copy(), sc.v0.copy()
-    tg = sc.targets(0)
+    x, v, step = _bar_start(sc)
+    tg = sc.targets(step)
     xt = o.predict(x, v, tg)
     x[sc.fixed.astype(bool)] = tg
     g = np.zeros_like(x); P = np.zeros_like(x); p = np.zeros_like(x)
@@ -523,15 +641,34 @@ def cpu_baseline(sc, budget_s=15.0):
     while n < sc.iters and (n == 0 or time.perf_counter() - t0 < budget_s):
         o.iteration(x, xt, g, P, p, n)
         n += 1
-    dt = time.perf_counter() - t0
+    return n, time.perf_counter() - t0, step
+
+
+def cpu_baseline(sc, budget_s=15.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the same workload: NCG iterations of
+    the twisted bar's time step 100 (the first step of the GPU's timed window, its contact search included), from
+    the oracle's own step-100 state.  Single-threaded (the value), and as independent replicas on every host core
+    at once (the oracle is serial; all cores busy), each in a spawned process."""
+    import multiprocessing as mp
+    n, dt, step = _oracle_iterations(budget_s)
+    cores = os.cpu_count() or 1
+    multi = None
+    if cores > 1:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            outs = pool.starmap(_oracle_iterations, [(budget_s / 2,)] * cores)
+        multi = {"value": round(sum(a for a, _, _ in outs) / max(b for _, b, _ in outs), 4), "unit": UNIT,
+                 "cores": cores, "kind": "oracle, one independent replica per core"}
     return {"value": round(n / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} NCG iterations of time step 0 of the 98,304-tet twisted bar (FP64 C oracle, 1 thread, "
-                      f"{dt:.1f} s)"}
+            "sample": f"{n} NCG iterations of time step {step} of the 98,304-tet twisted bar from the oracle's own "
+                      f"step-{step} state (FP64 C oracle, 1 thread, {dt:.1f} s)",
+            "all_cores": multi}
 
 
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on the same workload and metric; each benchmark step is one NCG
-    iteration (a bounded sample), iterations continuing through the time steps of the twist."""
+    iteration (a bounded sample), iterations continuing through the time steps of the twist from the oracle's own
+    state at the start of step 100, the first step of the GPU's timed window."""
     import numpy as np
     ws, rank, local = rank_info()
     if rank != 0:
@@ -540,13 +677,13 @@ def run_reference(args):
     from paper_2405_08001_gb300 import scenes as S
     sc = S.twisted_bar()
     o = oracle.Oracle.from_scene(sc)
-    x, v = sc.x0.copy(), sc.v0.copy()
+    x, v, step0 = _bar_start(sc)
     fx = sc.fixed.astype(bool)
-    state = {"step": -1, "k": sc.iters}
+    state = {"step": step0 - 1, "k": sc.iters}
 
     def one_iteration():
         if state["k"] >= sc.iters:
-            if state["step"] >= 0:
+            if state["step"] >= step0:
                 v[:] = (x - state["xt0"]) / sc.dt
             state["step"] += 1
             tg = sc.targets(state["step"])
@@ -570,9 +707,12 @@ def run_reference(args):
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "step": "one NCG iteration of the FP64 CPU oracle (bounded sample)"},
+            "config": {"workload": WORKLOAD, "step": "one NCG iteration of the FP64 CPU oracle (bounded sample)",
+                       "timed_steps": f"iterations of time steps {step0}.. of the run, from the oracle's own "
+                                      f"step-{step0} state"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 4), "unit": UNIT,
-                             "sample": f"{args.steps} consecutive NCG iterations of the twisted bar, 1 thread"},
+                             "sample": f"{args.steps} consecutive NCG iterations of the twisted bar from time step "
+                                       f"{step0}, 1 thread"},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
