@@ -90,6 +90,8 @@ def _load():
             "or_step": (C.c_int, [P, P, P, P, I32, D, P, P]),
             "or_predict": (None, [P, P, P, P, P]),
             "or_intersections": (I32, [P, P]),
+            "or_hvp": (C.c_int, [P, P, P, P]),
+            "or_adjoint_step": (C.c_int, [P, P, P, P, P, P, P, D, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -384,6 +386,25 @@ class Oracle:
         _check(_load().or_step(self._m, _ptr(x), _ptr(v), _ptr(tg), int(iters), float(eps), _ptr(trace),
                                C.byref(done)))
         return done.value, trace[:done.value]
+
+    def hvp(self, x, v):
+        """H(x) v (frozen closest points; kinematic rows and columns dropped)."""
+        out = np.zeros((self.nv, 3))
+        _check(_load().or_hvp(self._m, _ptr(_f64(x)), _ptr(_f64(v)), _ptr(out)))
+        return out
+
+    def adjoint_step(self, x1, ax1, av1, dE=None, tol=1e-10, max_iters=5000):
+        """The reverse of one time step at its end state x1: (ax0, av0, iters, residual), adding dL/dE_e to dE
+        (float64 [n_tets], updated in place) when given."""
+        ax0 = np.zeros((self.nv, 3))
+        av0 = np.zeros((self.nv, 3))
+        if dE is not None:
+            assert dE.dtype == np.float64 and dE.flags.c_contiguous and dE.size == self.nt
+        it = C.c_int32()
+        res = C.c_double()
+        _check(_load().or_adjoint_step(self._m, _ptr(_f64(x1)), _ptr(_f64(ax1)), _ptr(_f64(av1)), _ptr(ax0),
+                                       _ptr(av0), _ptr(dE), float(tol), int(max_iters), C.byref(it), C.byref(res)))
+        return ax0, av0, it.value, res.value
 
     def intersections(self, x):
         return int(_load().or_intersections(self._m, _ptr(_f64(x))))

@@ -1428,3 +1428,172 @@ int32_t or_intersections(const or_model *m, const double *x)
             if (!(dot3(m->plane_n, x + 3 * (size_t)i) - m->p.plane_o > 0.0)) ++cnt;
     return cnt;
 }
+
+/* ------------------------------------------------------------------------------------------------ differentiation */
+
+/*
+ * H v at x, H the Hessian of E (Eq. Hessian) as p^T H p sees it: the lumped mass, the elastic six-term split of
+ * Sec. 3.1 (sum_i Psi_ii g_i g_i^T + Psi_i H_i mapped by vec(dF/dx)), the barrier with the closest points frozen
+ * (Eq. 9: (b''/d^2 - b'/d^3) (dt/dx t)(dt/dx t)^T + b'/d (dt/dx)(dt/dx)^T) and the plane barrier b'' n n^T.  Rows
+ * and columns of kinematic vertices are dropped (their entries of v are ignored, of out set to zero).  The paper
+ * has no adjoint: this is the vector form of or_pHp (v^T H v equals it), for the oracle's own adjoint step.
+ */
+int or_hvp(const or_model *m, const double *x, const double *v_in, double *out)
+{
+    int32_t nv = m->p.nv;
+    size_t n = 3 * (size_t)nv;
+    double *v = malloc(sizeof(double) * n);
+    if (!v) return OR_ERR_OOM;
+    for (int32_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) v[3 * (size_t)i + a] = m->fixed[i] ? 0.0 : v_in[3 * (size_t)i + a];
+    for (int32_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) out[3 * (size_t)i + a] = m->mass[i] * v[3 * (size_t)i + a];
+    for (int32_t e = 0; e < m->p.nt; ++e) {
+        tet_terms T;
+        int st = tet_eval(m, e, x, &T);
+        if (st) { free(v); set_err("inverted tet"); return st; }
+        const int32_t *vi = m->tet + 4 * (size_t)e;
+        double ve[12], Jv[9], HJv[9];
+        for (int i = 0; i < 4; ++i) for (int a = 0; a < 3; ++a) ve[3 * i + a] = v[3 * (size_t)vi[i] + a];
+        for (int r = 0; r < 9; ++r) { double acc = 0; for (int q = 0; q < 12; ++q) acc += T.J[r][q] * ve[q]; Jv[r] = acc; }
+        double g1Jv = 0, g2Jv = 0, g3Jv = 0;
+        for (int r = 0; r < 9; ++r) { g1Jv += T.g1[r] * Jv[r]; g2Jv += T.g2[r] * Jv[r]; g3Jv += T.g3[r] * Jv[r]; }
+        for (int r = 0; r < 9; ++r) {
+            double H1 = 0, H3 = 0;
+            for (int q = 0; q < 9; ++q) { H1 += T.H1[r][q] * Jv[q]; H3 += T.H3[r][q] * Jv[q]; }
+            HJv[r] = T.Psi11 * g1Jv * T.g1[r] + T.Psi22 * g2Jv * T.g2[r] + T.Psi33 * g3Jv * T.g3[r] + T.Psi1 * H1 +
+                     T.Psi2 * 2.0 * Jv[r] + T.Psi3 * H3;
+        }
+        for (int q = 0; q < 12; ++q) {
+            double acc = 0;
+            for (int r = 0; r < 9; ++r) acc += T.J[r][q] * HJv[r];
+            out[3 * (size_t)vi[q / 3] + q % 3] += T.scale * acc;
+        }
+    }
+    pair_list L = {0};
+    int st = find_pairs(m, x, m->p.dhat, 1, 0, &L);
+    if (st) { free(L.v); free(v); return st; }
+    double kap = m->p.kappa, dh_ = m->p.dhat;
+    for (int32_t k = 0; k < L.n; ++k) {
+        const or_pair *P = &L.v[k];
+        double d = P->d;
+        if (!(d > 0.0)) { free(L.v); free(v); set_err("zero distance"); return OR_ERR_PENETRATION; }
+        double bb[3];
+        or_barrier_fn(d, dh_, bb);
+        double A = kap * (bb[2] / (d * d) - bb[1] / (d * d * d)), Bc = kap * bb[1] / d;
+        double cv[3] = {0, 0, 0};   /* (dt/dx)^T v = sum_i c_i v_i */
+        for (int i = 0; i < 4; ++i) for (int a = 0; a < 3; ++a) cv[a] += P->c[i] * v[3 * (size_t)P->v[i] + a];
+        double cvt = dot3(cv, P->t);
+        for (int i = 0; i < 4; ++i)
+            for (int a = 0; a < 3; ++a) out[3 * (size_t)P->v[i] + a] += P->c[i] * (A * cvt * P->t[a] + Bc * cv[a]);
+    }
+    free(L.v);
+    if (m->p.has_plane)
+        for (int32_t i = 0; i < nv; ++i) {
+            double d;
+            if (plane_d(m, x + 3 * (size_t)i, &d)) { free(v); set_err("vertex below plane"); return OR_ERR_PENETRATION; }
+            if (!(d < dh_)) continue;
+            double bb[3];
+            or_barrier_fn(d, dh_, bb);
+            double nvv = dot3(m->plane_n, v + 3 * (size_t)i);
+            for (int a = 0; a < 3; ++a) out[3 * (size_t)i + a] += kap * bb[2] * nvv * m->plane_n[a];
+        }
+    for (int32_t i = 0; i < nv; ++i)
+        if (m->fixed[i]) for (int a = 0; a < 3; ++a) out[3 * (size_t)i + a] = 0.0;
+    free(v);
+    for (size_t q = 0; q < n; ++q) if (!isfinite(out[q])) { set_err("non-finite H v"); return OR_ERR_NONFINITE; }
+    return OR_OK;
+}
+
+/*
+ * The reverse of one time step x_t -> x_{t+1} = argmin E(x; x~_t), v_{t+1} = (x_{t+1} - x_t)/h, read as the exact
+ * minimiser (grad E(x_{t+1}) = 0, implicit function theorem).  Given ax1 = dL/dx_{t+1} and av1 = dL/dv_{t+1}:
+ *   H(x_{t+1}) lambda = ax1 + av1/h              (kinematic rows dropped), by Jacobi-preconditioned linear CG
+ *   ax0 = dL/dx_t = M lambda - av1/h,   av0 = dL/dv_t = h M lambda   (x~ = x_t + h v_t + h^2 g; kinematic:
+ *                                                                     ax0 = -av1/h, av0 = 0)
+ *   dE[e] += -lambda_e . g_e / E_e               (the tet's elastic gradient g_e is linear in its Young's modulus)
+ * CG runs to ||r|| <= tol ||b|| or max_iters iterations (sums in index order); *iters and *residual report them.
+ */
+int or_adjoint_step(const or_model *m, const double *x1, const double *ax1, const double *av1, double *ax0,
+                    double *av0, double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual)
+{
+    int32_t nv = m->p.nv;
+    size_t n = 3 * (size_t)nv;
+    double h = m->p.h;
+    double *b = calloc(n, sizeof(double)), *lam = calloc(n, sizeof(double)), *r = calloc(n, sizeof(double));
+    double *z = calloc(n, sizeof(double)), *p = calloc(n, sizeof(double)), *q = calloc(n, sizeof(double));
+    double *g = calloc(n, sizeof(double)), *dg = calloc(n, sizeof(double));
+    int st = OR_OK;
+    if (!b || !lam || !r || !z || !p || !q || !g || !dg) { st = OR_ERR_OOM; goto done; }
+    for (int32_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            size_t k = 3 * (size_t)i + a;
+            b[k] = m->fixed[i] ? 0.0 : ax1[k] + av1[k] / h;
+        }
+    /* Jacobi preconditioner of the Hessian at x1 (the same rule as the iteration's, Sec. 4.2) */
+    st = or_grad_diag(m, x1, x1, g, dg, NULL);
+    if (st) goto done;
+    double bb = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        int32_t i = (int32_t)(k / 3);
+        dg[k] = m->fixed[i] ? 0.0 : (dg[k] > OR_JACOBI_FLOOR * m->mass[i] ? 1.0 / dg[k] : 1.0 / m->mass[i]);
+        r[k] = b[k];
+        z[k] = dg[k] * r[k];
+        p[k] = z[k];
+        bb += b[k] * b[k];
+    }
+    double rz = 0.0, rr = bb;
+    for (size_t k = 0; k < n; ++k) rz += r[k] * z[k];
+    int32_t it = 0;
+    double bn = sqrt(bb);
+    while (it < max_iters && sqrt(rr) > tol * bn && bn > 0.0) {
+        st = or_hvp(m, x1, p, q);
+        if (st) goto done;
+        double pq = 0.0;
+        for (size_t k = 0; k < n; ++k) pq += p[k] * q[k];
+        if (!(pq != 0.0) || !isfinite(pq)) { st = OR_ERR_NONFINITE; set_err("CG breakdown"); goto done; }
+        double al = rz / pq;
+        double rz1 = 0.0;
+        rr = 0.0;
+        for (size_t k = 0; k < n; ++k) {
+            lam[k] += al * p[k];
+            r[k] -= al * q[k];
+            z[k] = dg[k] * r[k];
+            rz1 += r[k] * z[k];
+            rr += r[k] * r[k];
+        }
+        double be = rz1 / rz;
+        rz = rz1;
+        for (size_t k = 0; k < n; ++k) p[k] = z[k] + be * p[k];
+        ++it;
+    }
+    for (int32_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            size_t k = 3 * (size_t)i + a;
+            double ml = m->fixed[i] ? 0.0 : m->mass[i] * lam[k];
+            ax0[k] = ml - av1[k] / h;
+            av0[k] = h * ml;
+        }
+    if (dE)
+        for (int32_t e = 0; e < m->p.nt; ++e) {
+            tet_terms T;
+            st = tet_eval(m, e, x1, &T);
+            if (st) { set_err("inverted tet"); goto done; }
+            const int32_t *vi = m->tet + 4 * (size_t)e;
+            double dPsi[9];
+            for (int rr9 = 0; rr9 < 9; ++rr9) dPsi[rr9] = T.Psi1 * T.g1[rr9] + T.Psi2 * T.g2[rr9] + T.Psi3 * T.g3[rr9];
+            double Ee = 2.0 * (1.0 + m->p.poisson) * m->mu[e];
+            double s = 0.0;
+            for (int qq = 0; qq < 12; ++qq) {
+                double acc = 0.0;
+                for (int rr9 = 0; rr9 < 9; ++rr9) acc += T.J[rr9][qq] * dPsi[rr9];
+                s += lam[3 * (size_t)vi[qq / 3] + qq % 3] * T.scale * acc;
+            }
+            dE[e] -= s / Ee;
+        }
+    if (iters) *iters = it;
+    if (residual) *residual = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+done:
+    free(b); free(lam); free(r); free(z); free(p); free(q); free(g); free(dg);
+    return st;
+}

@@ -17,7 +17,9 @@ enum : uint32_t {
 };
 
 // ticket counters of the "last block finishes the reduction" kernels
-enum { TK_PREDICT = 0, TK_DOTS, TK_DIR, TK_PHP, TK_UPDATE, TK_SCAN, TK_ENERGY, TK_MISC, TK_QUERY, TK_COUNT };
+// TK_PAIRS, TK_PAIRS + 1: the persistent gradient pass's candidate cursor, by iteration parity
+enum { TK_PREDICT = 0, TK_DOTS, TK_DIR, TK_PHP, TK_UPDATE, TK_SCAN, TK_ENERGY, TK_MISC, TK_QUERY, TK_PAIRS,
+       TK_PAIRS1, TK_COUNT };
 
 constexpr int TRACE_COLS = 8;   // beta, gp, pHp, pmax, alpha, dE, n_active, capped
 

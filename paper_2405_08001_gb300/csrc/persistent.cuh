@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
     int ncand = (volatile int &)c->n_cand;
     const double disp_lim = 0.5 * D.pad_r * (1.0 - 1e-4);
     Stamper st{A.stamps, A.stamp_kind, A.max_stamps};
+    if (lead) { c->ticket[TK_PAIRS] = 0u; c->ticket[TK_PAIRS1] = 0u; }
     grid_barrier(br, c);
     st.mark(-1);
 
@@ -608,16 +609,24 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                     tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
                 for (int ci = cs.b0 + (int)threadIdx.x; ci < cs.b1; ci += PB) pair_grad<R>(D, ci, par);
             } else {
-                // the block's tets and candidates as one list, so that no thread takes more than its share of both
-                const int nts = ts.b1 - ts.b0, nit = nts + (cs.b1 - cs.b0);
-                for (int q = threadIdx.x; q < nit; q += PB) {
-                    if (q < nts) {
-                        TetIn<R> in;
-                        load_tet_in<R>(D, ts.b0 + q, in);
-                        tet_grad<R>(D, ts.b0 + q, par, in);
-                    } else {
-                        pair_grad<R>(D, cs.b0 + q - nts, par);
-                    }
+                // the block's share of the tets, then candidates 32 at a time per warp from a grid-wide cursor: the
+                // active ones (float-float geometry) cluster in the candidate order, and a fixed share per block
+                // left the blocks holding a contact patch 40 us behind the median one
+                const int nts = ts.b1 - ts.b0;
+                for (int q = threadIdx.x; q < nts; q += PB) {
+                    TetIn<R> in;
+                    load_tet_in<R>(D, ts.b0 + q, in);
+                    tet_grad<R>(D, ts.b0 + q, par, in);
+                }
+                if (lead) c->ticket[TK_PAIRS + ((k + 1) & 1)] = 0u;   // the next iteration's cursor
+                unsigned int *cur = &c->ticket[TK_PAIRS + (k & 1)];
+                const int nc = min(ncand, D.cand_cap), lane = threadIdx.x & 31;
+                for (;;) {
+                    int b0 = 0;
+                    if (lane == 0) b0 = (int)atomicAdd(cur, 32u);
+                    b0 = __shfl_sync(0xffffffffu, b0, 0);
+                    if (b0 >= nc) break;
+                    if (b0 + lane < nc) pair_grad<R>(D, b0 + lane, par);
                 }
             }
         }

@@ -260,9 +260,10 @@ def toss(n: int = 24, side: float = 0.1, dt: float = 1.0 / 60.0, steps: int = 20
 
 def pile(n_bars: int = 10, cells=(16, 16, 64), size=(0.1, 0.1, 0.4), seed: int = 4, youngs: float = 2e5,
          poisson: float = 0.4, dt: float = 1.0 / 30.0, dhat: float = 5e-4, kappa: float = 1e4, iters: int = 50,
-         steps: int = 200) -> Scene:
-    """Bars stacked criss-cross in layers of two (alternating along x and y), 2*dhat vertical gaps, seeded
-    jitter of +-1 mm and +-2 degrees, dropped onto the plane z = 0."""
+         steps: int = 200, gap: float = 2.0, jitter: bool = True) -> Scene:
+    """Bars stacked criss-cross in layers of two (alternating along x and y), gap*dhat vertical gaps, seeded
+    jitter of +-1 mm and +-2 degrees (none with jitter=False), dropped onto the plane z = 0.  With gap < 1 and no
+    jitter every crossing starts face to face within dhat: a contact-dominated stack."""
     rng = np.random.default_rng(seed)
     Xb, Tb = kuhn_grid(*cells, size=size)
     Xb = Xb - np.array([0.5 * size[0], 0.5 * size[1], 0.5 * size[2]])  # centred, long axis z
@@ -275,13 +276,14 @@ def pile(n_bars: int = 10, cells=(16, 16, 64), size=(0.1, 0.1, 0.4), seed: int =
         layer, slot = divmod(b, 2)
         R = lay_x if layer % 2 == 0 else rot_z(math.pi / 2) @ lay_x
         ang = math.radians(rng.uniform(-2.0, 2.0))
-        R = rot_z(ang) @ R
+        R = rot_z(ang if jitter else 0.0) @ R
         Y = Xb @ R.T
         lateral = (slot - 0.5) * 1.5 * size[1]
         shift = np.array([0.0, lateral, 0.0]) if layer % 2 == 0 else np.array([lateral, 0.0, 0.0])
-        shift = shift + np.append(rng.uniform(-1e-3, 1e-3, size=2), 0.0)
+        jit = rng.uniform(-1e-3, 1e-3, size=2)
+        shift = shift + np.append(jit if jitter else np.zeros(2), 0.0)
         Y = Y + shift
-        Y[:, 2] += -Y[:, 2].min() + 2 * dhat + layer * (thick + 2 * dhat)
+        Y[:, 2] += -Y[:, 2].min() + gap * dhat + layer * (thick + gap * dhat)
         Xs.append(Y)
         Ts.append(Tb + off)
         off += Y.shape[0]

@@ -1,6 +1,7 @@
 """GPU tests of the differentiation form: the Hessian-vector kernel against the oracle's p^T H p (polarisation),
-and the adjoint gradients (per-tet Young's modulus, initial velocity) against central finite differences of the
-oracle's own forward run."""
+the adjoint gradients (per-tet Young's modulus, initial velocity) against central finite differences of the
+oracle's own forward run, and every reverse step against the oracle's own adjoint step (on the 3-cell drop and on a
+two-step slice of the 82,944-tet differentiation config)."""
 import numpy as np
 import pytest
 
@@ -200,3 +201,65 @@ def test_differentiation_config_full_size(B, O):
     exact = 2.0 * (cT - target)[None, :] * steps * sc.dt * mass[:, None] / mass.sum()
     assert np.linalg.norm(gv - exact) / np.linalg.norm(exact) < 1e-6
     assert abs(float(gE @ uE)) < 1e-6 * np.linalg.norm(exact) * np.linalg.norm(uE) / np.sqrt(sc.n_tets)
+
+
+def test_adjoint_steps_match_the_oracle_adjoint(B, O):
+    """Each reverse step of the library (sim_adjoint_step) against the oracle's own adjoint step (its CG on its
+    Hessian-vector product, pinned on the CPU) from the same end state and adjoints, along the 3-cell drop's run:
+    dL/dx_t, dL/dv_t and the accumulated dL/dE_e."""
+    sc = drop_scene()
+    rng = np.random.default_rng(21)
+    E0 = np.full(sc.n_tets, 1e5) * (1.0 + 0.2 * rng.uniform(-1, 1, sc.n_tets))
+    import dataclasses
+    s2 = dataclasses.replace(sc, youngs=1.0, youngs_per_tet=E0)
+    sim = B.Sim(s2, precision=0)
+    o = O.Oracle.from_scene(s2)
+    xs = [s2.x0.copy()]
+    for t in range(s2.steps):
+        sim.step(1)
+        xs.append(sim.state()[0])
+    ax = rng.normal(size=s2.x0.shape)
+    av = rng.normal(size=s2.x0.shape)
+    axo, avo = ax.copy(), av.copy()
+    dE, dEo = np.zeros(s2.n_tets), np.zeros(s2.n_tets)
+    for t in range(s2.steps, 0, -1):
+        ax, av, it, res = B.sim_adjoint_step(sim.h, xs[t], ax, av, dE=dE, tol=1e-13, max_iters=20000)
+        axo, avo, ito, reso = o.adjoint_step(xs[t], axo, avo, dE=dEo, tol=1e-13, max_iters=20000)
+        assert res < 1e-12 and reso < 1e-12
+        for a, b in ((ax, axo), (av, avo), (dE, dEo)):
+            assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), (t, np.linalg.norm(a - b) / np.linalg.norm(b))
+    sim.close()
+
+
+def test_differentiation_config_two_step_slice_matches_the_oracle_adjoint(B, O):
+    """The differentiation config at full size (24^3 cells, 82,944 tets, seeded toss velocity, per-tet Young's
+    moduli): two FP64 forward steps through the library, then the two reverse steps of the library and of the oracle
+    from the same checkpoints: dL/dx_0, dL/dv_0 and dL/dE_e agree to the CG tolerance.  The loss adds to the
+    config's |centroid - target|^2 a vertex-wise |x - s|^2 to a seeded shape s: in flight the centroid loss has no
+    elastic part (dL/dE vanishes by momentum conservation), the vertex-wise one does."""
+    import dataclasses
+    sc = S.toss()
+    rng = np.random.default_rng(22)
+    E0 = np.full(sc.n_tets, sc.youngs) * (1.0 + 0.2 * rng.uniform(-1, 1, sc.n_tets))
+    s2 = dataclasses.replace(sc, youngs=1.0, youngs_per_tet=E0)
+    sim = B.Sim(s2, precision=0)
+    o = O.Oracle.from_scene(s2)
+    xs = [s2.x0.copy()]
+    for t in range(2):
+        sim.step(1)
+        xs.append(sim.state()[0])
+    mass = o.mass()
+    target = sc.x0.mean(axis=0) + rng.uniform(-0.02, 0.02, 3)
+    c = (mass[:, None] * xs[-1]).sum(axis=0) / mass.sum()
+    shape = sc.x0 + rng.normal(scale=1e-3, size=sc.x0.shape)
+    ax = 2.0 * (c - target)[None, :] * mass[:, None] / mass.sum() + 2.0 * (xs[-1] - shape)
+    av = np.zeros_like(ax)
+    axo, avo = ax.copy(), av.copy()
+    dE, dEo = np.zeros(s2.n_tets), np.zeros(s2.n_tets)
+    for t in (2, 1):
+        ax, av, it, res = B.sim_adjoint_step(sim.h, xs[t], ax, av, dE=dE, tol=1e-10, max_iters=20000)
+        axo, avo, ito, reso = O.Oracle.adjoint_step(o, xs[t], axo, avo, dE=dEo, tol=1e-10, max_iters=20000)
+        assert res <= 1e-10 and reso <= 1e-10, (res, reso)
+    for a, b in ((ax, axo), (av, avo), (dE, dEo)):
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b), np.linalg.norm(a - b) / np.linalg.norm(b)
+    sim.close()

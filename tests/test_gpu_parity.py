@@ -356,6 +356,23 @@ def test_twisted_bar_full_size_in_the_timed_window(B, O, prec):
     sim.close()
 
 
+def test_contact_stack_full_size(B, O):
+    """The contact-dominated stack the benchmark times beside the pile (983,040 tets, every crossing face to face
+    within dhat: 2.2e5 active pairs at the start, about 7e4 once the barrier has pushed the faces apart),
+    FP32-mixed through the graph path for two steps, then one lock-step iteration at full size, entry by entry and
+    over the contact vertices."""
+    sc = S.pile(gap=0.5, jitter=False, steps=20)
+    sim = B.Sim(sc, precision=1)
+    sim.step(2)
+    x, v, st = sim.state()
+    assert st["n_active"] > 50000 and x[:, 2].min() > 0, st
+    o = O.Oracle.from_scene(sc)
+    worst = lockstep(B, O, o, sim, sc, 1, 1)
+    for k in CHECKED:
+        assert worst[k] < TOL[1], (k, {kk: f"{v:.3e}" for kk, v in worst.items()})
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_equals_eager_and_segmented_is_deterministic(B, prec):
     """Free fall of the drop config (no contact): with the segmented scatter nothing is order-dependent, so graph
