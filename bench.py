@@ -196,6 +196,16 @@ def recorded_traffic(kernel: str, prec_name: str, phases: bool = False, scene: s
         return None
 
 
+SHAPES = {(256, 2): 0, (512, 1): 1, (256, 3): 2, (256, 1): 3}   # sim_options.block_shape of (threads, blocks/SM)
+
+
+def shape_of(st):
+    """The block shape a handle runs (its stats), as sim_options.block_shape and as a report."""
+    key = (st["block_threads"], st["blocks_per_sm"])
+    return SHAPES.get(key, 0), {"threads_per_block": key[0], "blocks_per_sm": key[1],
+                                "launch": "persistent" if st["launch_form"] == 1 else "one kernel per phase"}
+
+
 def window(W, K, cfg_steps):
     """First step of the timed window: the window ends with the configured run's last step (where the twisted
     bar carries the most contact candidates), after at least W untimed warm-up steps."""
@@ -246,8 +256,9 @@ def side_workload(B, torch, S, stream, flush, sc, name, desc, unit_scale, unit, 
                   per_tet_youngs):
     """One of the workloads whose working set exceeds L2 (the large pile, the batch): the run's lead-in untimed, then
     the K last steps of its configured run timed, then one profiled step; the HBM roofline from the method's bytes."""
-    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream, persistent=0 if phases else 1)
-    first = max(3, sc.steps - K)
+    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, cuda_stream=stream.cuda_stream, persistent=0 if phases else 1,
+                block_shape=-1)
+    first = max(12, sc.steps - K)
     try:
         for s in range(first):
             B.sim_step_async(sim.h, 1, None)
@@ -278,26 +289,34 @@ def side_workload(B, torch, S, stream, flush, sc, name, desc, unit_scale, unit, 
                                         "counted)"},
             "phases_us_per_iteration": {k: round(1e3 * v[0] / v[1], 2) for k, v in prof.items()
                                         if v[1] > 0 and k.startswith("k_")},
+            "block_shape": shape_of(st)[1],
             "stats_last_step": {k: st[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")}}
 
 
-def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, repeat=3):
+def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shapes, repeat=3):
     """FP32-mixed against plain FP64 at equal final-energy accuracy on one time step (the comparison the method's
     FP32 form is judged by).
 
     From a saved state the step is taken once per form with max(ks) iterations through the persistent kernel, one
     iteration batch at a time (sim_iterate), and the energy after K iterations is read for every K in `ks`; the
     converged reference x* is the FP64 form after `kref` iterations.  Energies are evaluated by the FP64 oracle:
-    err(K) = (E(x_K) - E(x*)) / (E(x_0) - E(x*)), x_0 the step's start (kinematic targets applied).  The target is
-    the plain FP64 form's error at the headline iteration count ks[1]; each form's cost is the time of a whole step
-    with the fewest iterations in `ks` that reach it (each (form, K) timed `repeat` times from the saved state, the
-    fastest kept)."""
-    o = O.Oracle.from_scene(sc)
+    err(K) = (E(x_K) - E(x*)) / (E(x_0) - E(x*)), x_0 the step's start (kinematic targets applied); with several
+    scenes (a batch) err is taken per scene and the median over scenes is used.  The target is the plain FP64 form's
+    error at the headline iteration count ks[1]; each form's iteration count to reach it is interpolated linearly
+    in K between the bracketing points of its curve, and its cost is the step time interpolated the same way (each
+    (form, K) timed `repeat` times from the saved state, the fastest kept)."""
+    import numpy as np
     x0, v0 = state
     fixed = sc.fixed.astype(bool) if sc.fixed is not None else None
+    ranges = sc.scene_ranges()
+    oracles = [O.Oracle.from_scene(sc.subscene(i) if len(ranges) > 1 else sc) for i in range(len(ranges))]
 
-    def sim_of(prec, K):
-        return B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, iters=K, persistent=1)
+    def energies(x, xt):
+        return np.array([o.energy(x[v0_:v1_], xt[v0_:v1_])[0] for o, (v0_, v1_, _, _) in zip(oracles, ranges)])
+
+    def sim_of(prec, K):   # in the block shape each form's autotuner chose on the benchmark's run
+        return B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, iters=K, persistent=1,
+                     block_shape=shapes[prec])
 
     def timed(prec, K):
         sim = sim_of(prec, K)
@@ -334,33 +353,40 @@ def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, repe
         return out
 
     (xr, xt), = curve(B.SIM_FP64, (kref,))
-    Eref = o.energy(xr, xt)[0]
+    Eref = energies(xr, xt)
     xs = x0.copy()
     if fixed is not None and targets is not None:
         xs[fixed] = targets
-    E0 = o.energy(xs, xt)[0]
+    E0 = energies(xs, xt)
     res = {}
     for prec, pname in ((B.SIM_FP64, "fp64"), (B.SIM_FP32_MIXED, "fp32_mixed")):
         rows = []
         for K, (x, xt2) in zip(ks, curve(prec, ks)):
-            rows.append({"iters": K, "ms": round(timed(prec, K), 4),
-                         "energy_err": (o.energy(x, xt2)[0] - Eref) / (E0 - Eref)})
+            err = (energies(x, xt2) - Eref) / np.where(E0 - Eref != 0.0, E0 - Eref, 1.0)
+            rows.append({"iters": K, "ms": round(timed(prec, K), 4), "energy_err": float(np.median(err))})
         res[pname] = rows
     target = res["fp64"][1]["energy_err"]
 
     def cost(rows):
+        """(iterations, ms) where the error curve first reaches the target, interpolated linearly in K."""
+        prev = None
         for r in rows:
             if r["energy_err"] <= target * (1 + 1e-9):
-                return r
+                if prev is None or prev["energy_err"] == r["energy_err"]:
+                    return float(r["iters"]), r["ms"]
+                f = (prev["energy_err"] - target) / (prev["energy_err"] - r["energy_err"])
+                return (prev["iters"] + f * (r["iters"] - prev["iters"]), prev["ms"] + f * (r["ms"] - prev["ms"]))
+            prev = r
         return None
     c64, c32 = cost(res["fp64"]), cost(res["fp32_mixed"])
     return {"workload": name, "reference": f"FP64, {kref} iterations (x*); energies by the FP64 oracle",
-            "error": "(E(x_K) - E(x*)) / (E(x_0) - E(x*)), K iterations of one trajectory per form",
+            "error": "(E(x_K) - E(x*)) / (E(x_0) - E(x*)) after K iterations of one trajectory per form"
+                     + ("; median over the scenes" if len(ranges) > 1 else ""),
             "target_err": target, "fp64": res["fp64"], "fp32_mixed": res["fp32_mixed"],
-            "fp64_ms_at_target": c64["ms"] if c64 else None, "fp32_ms_at_target": c32["ms"] if c32 else None,
-            "fp64_iters_at_target": c64["iters"] if c64 else None,
-            "fp32_iters_at_target": c32["iters"] if c32 else None,
-            "speedup_fp32_over_fp64": round(c64["ms"] / c32["ms"], 3) if (c64 and c32) else None}
+            "fp64_iters_at_target": round(c64[0], 2) if c64 else None,
+            "fp32_iters_at_target": round(c32[0], 2) if c32 else None,
+            "fp64_ms_at_target": round(c64[1], 4) if c64 else None, "fp32_ms_at_target": round(c32[1], 4) if c32 else None,
+            "speedup_fp32_over_fp64": round(c64[1] / c32[1], 3) if (c64 and c32) else None}
 
 
 def run_ours(args):
@@ -393,8 +419,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
 
     def one_form(prec, K_, form=1):
-        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else form)
-        first_ = window(W, K_, cfg_steps)
+        sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else form,
+                    block_shape=-1)
+        first_ = window(max(W, 12), K_, cfg_steps)   # the autotuner's steps (two per candidate) come first
         for s in range(first_):
             B.sim_step_async(sim.h, 1, targets[s])
         torch.cuda.synchronize()
@@ -410,6 +437,7 @@ def run_ours(args):
         return sim, times, st
 
     sim32, t32, st32 = one_form(B.SIM_FP32_MIXED, K)
+    shape32, shape32_rep = shape_of(st32)
     total_ms = max_over_ranks(sum(t32))
     value = job_value(ws, K, iters, total_ms)
 
@@ -463,6 +491,7 @@ def run_ours(args):
     K64 = min(K, 40)
     # the FP64 form's launch form is autotuned during the warm-up steps (the per-phase form wins for FP64)
     sim64, t64, st64 = one_form(B.SIM_FP64, K64, form=2)
+    shape64, shape64_rep = shape_of(st64)
     sim64.close()
     ms64 = sum(t64) / K64
     v64 = K64 * iters / (sum(t64) / 1e3)
@@ -526,8 +555,9 @@ def run_ours(args):
             B.sim_step_async(simr.h, 1, targets[s])
         xb, vb, _ = B.sim_get_state(simr.h)
         simr.close()
+        shapes = {B.SIM_FP32_MIXED: shape32, B.SIM_FP64: shape64}
         eq = {"twisted_bar": equal_accuracy(B, torch, O, sc, stream, (xb, vb), sc.targets(100), (25, 50, 75, 100),
-                                            1000, "twisted bar, time step 100 (from the FP64 form's state)")}
+                                            1000, "twisted bar, time step 100 (from the FP64 form's state)", shapes)}
         if not args.no_pile:
             bsc = S.batched()
             simr = B.Sim(bsc, precision=B.SIM_FP64, cuda_stream=stream.cuda_stream, persistent=1)
@@ -536,12 +566,13 @@ def run_ours(args):
             xb, vb, _ = B.sim_get_state(simr.h)
             simr.close()
             eq["batched"] = equal_accuracy(B, torch, O, bsc, stream, (xb, vb), None, (25, 50, 75, 100), 400,
-                                           "batched, 256 scenes, time step 30 (from the FP64 form's state)", repeat=2)
+                                           "batched, 256 scenes, time step 30 (from the FP64 form's state)",
+                                           {B.SIM_FP32_MIXED: 0, B.SIM_FP64: 0}, repeat=2)
 
     # end to end through the C ABI with host buffers: pinned targets in, positions out, every step (the step is
     # enqueued with sim_step_async; sim_get_state copies the positions out, synchronises and reports any error of
     # the step: one synchronisation per step)
-    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1)
+    sim = B.Sim(sc, precision=B.SIM_FP32_MIXED, persistent=0 if args.phases else 1, block_shape=shape32)
     tg_host = torch.tensor(sc.all_targets(n_total), dtype=torch.float64).pin_memory()
     x_host = torch.empty((sc.n_verts, 3), dtype=torch.float64).pin_memory()
     for s in range(first):
@@ -607,11 +638,14 @@ def run_ours(args):
                                       f"(the run's last steps, the most contact candidates)"
                                       + (f", repeated from step {first} to make {K}" if first + K > cfg_steps else "")
                                       + f"; steps 0..{first - 1} untimed",
-                       "launch": "one kernel per phase" if args.phases else "one persistent cooperative kernel per step"},
+                       "launch": "one kernel per phase" if args.phases else "one persistent cooperative kernel per step",
+                       "block_shape": shape32_rep},
             "time_steps_per_s": round(K / (total_ms / 1e3), 2),
             "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
                            "launch": "persistent" if st64["launch_form"] == 1 else "one kernel per phase",
-                           "launch_choice": "autotuned (options.persistent = 2)" if not args.phases else "per phase",
+                           "block_shape": shape64_rep,
+                           "launch_choice": "autotuned (options.persistent = 2, block_shape = -1)" if not args.phases
+                           else "per phase",
                            "speedup_fp32_over_fp64_equal_iterations": round(value / ws / v64, 3)},
             "fp32_vs_fp64_equal_accuracy": eq,
             "iter_max_150": iter150,

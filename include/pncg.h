@@ -72,7 +72,7 @@ typedef struct {
  *   SIM_MAT_SNH  mu/2 (I2 - 3) - mu (I3 - 1) + lambda/2 (I3 - 1)^2  stable Neo-Hookean
  *   SIM_MAT_FCR  mu (I2 - 2 I1 + 3) + lambda/2 (I3 - 1)^2          fixed corotated (mu |F - R|^2 + ...)
  *   SIM_MAT_ARAP mu (I2 - 2 I1 + 3)                                 as-rigid-as-possible (mu |F - R|^2)
- * FCR and ARAP (the I1 densities) run in the FP64 form only; sim_eval_hvp and sim_adjoint_step support NH only.
+ * Every density runs in both forms; sim_eval_hvp and sim_adjoint_step support NH only.
  * Every density treats det F <= 0 as an error (SIM_ERR_INVERTED). */
 enum { SIM_MAT_NH = 0, SIM_MAT_SNH = 1, SIM_MAT_FCR = 2, SIM_MAT_ARAP = 3 };
 
@@ -111,9 +111,9 @@ typedef struct {
     int32_t candidate_capacity; /* initial candidate-buffer capacity in pairs; <= 0 = automatic */
     int32_t persistent;   /* 1 (default) = each time step (and each sim_iterate call) is one cooperative launch
                              whose blocks stay resident and meet at grid barriers between the phases of
-                             Algorithm 1; 0 = one kernel per phase; 2 = autotuned: the second time step runs
-                             persistent and the third per phase, each timed on the GPU (those two steps
-                             synchronise), and the faster form runs from then on (sim_stats.launch_form).  Falls
+                             Algorithm 1; 0 = one kernel per phase; 2 = autotuned: from the second time step on,
+                             two steps run persistent and two per phase (interleaved), each timed on the GPU (those
+                             steps synchronise), and the faster form runs from then on (sim_stats.launch_form).  Falls
                              back to 0 when the device cannot launch cooperative kernels; batched scenes always run
                              persistent. */
     int32_t split_objects; /* 0 (default) = the groups of sim_mesh.scene_of_vert are independent scenes (no pair
@@ -124,6 +124,13 @@ typedef struct {
                              |p_v|), -g^T p_o / p_o^T H p_o); a pair between objects a and b adds to p_a^T H p_a
                              and to p_b^T H p_b, each with the other object's entries of p zero.  Needs the
                              persistent form, like batched scenes. */
+    int32_t block_shape;  /* block shape of the persistent form: 0 (default) = 256 threads x 2 blocks per SM,
+                             1 = 512 x 1, 2 = 256 x 3, 3 = 256 x 1 (the compiler fits the registers per thread to
+                             the shape: 128, 128, 85, 255); -1 = autotuned: from the second time step on, each shape
+                             runs two time steps (interleaved), timed on the GPU (those steps synchronise), and the
+                             shape of the fastest step runs from then on (sim_stats.block_threads, blocks_per_sm).
+                             With persistent = 2 the per-phase form is timed as one more candidate.
+                             SIM_SCATTER_BLOCK keeps shape 0. */
 } sim_options;
 
 /* Statistics of the last completed time step. */
@@ -140,6 +147,8 @@ typedef struct {
     int32_t n_scenes;      /* independent scenes (1 without scene_of_vert) */
     int32_t n_near_fp64;   /* FP32 form: pair evaluations of the last step (or of the last sim_eval_* call) whose
                               distance fell below 1e-3 dhat, where the barrier terms are evaluated in double */
+    int32_t block_threads; /* persistent form: threads per block and blocks per SM of the shape in use (0 in the */
+    int32_t blocks_per_sm; /*   per-phase form) */
 } sim_stats;
 
 /* Scalars of the most recent iteration (Algorithm 1). */

@@ -39,7 +39,8 @@ class sim_options(C.Structure):
                 ("gravity", C.c_double * 3), ("has_plane", C.c_int32), ("plane_n", C.c_double * 3),
                 ("plane_o", C.c_double), ("pad_r", C.c_double), ("pnorm", C.c_int32), ("scatter", C.c_int32),
                 ("excl_factor", C.c_double), ("cuda_stream", C.c_void_p), ("use_graph", C.c_int32),
-                ("candidate_capacity", C.c_int32), ("persistent", C.c_int32), ("split_objects", C.c_int32)]
+                ("candidate_capacity", C.c_int32), ("persistent", C.c_int32), ("split_objects", C.c_int32),
+                ("block_shape", C.c_int32)]
 
 
 class sim_stats(C.Structure):
@@ -47,7 +48,7 @@ class sim_stats(C.Structure):
                 ("n_active", C.c_int32), ("n_rebuilds", C.c_int32), ("n_capped", C.c_int32),
                 ("n_surface_tris", C.c_int32), ("n_surface_edges", C.c_int32), ("n_surface_verts", C.c_int32),
                 ("dE0", C.c_double), ("dE_last", C.c_double), ("launch_form", C.c_int32), ("n_scenes", C.c_int32),
-                ("n_near_fp64", C.c_int32)]
+                ("n_near_fp64", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -85,8 +85,8 @@ template <typename R> __device__ inline void seg_reset(const Dev<R> &D)
 // Beta, direction + p^T H p, and update phases of iteration k for nseg > 1 scenes (three grid barriers, as in the
 // single-scene form).  sbuf holds the scenes' beta and alpha (2 x MAX_SCENES doubles).  Returns 1 when some vertex
 // has moved far enough since the candidate build to need a new one.
-template <typename R>
-__device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, unsigned char *sbuf, Bar &br,
+template <typename R, int PB, bool CO>
+__device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh, unsigned char *sbuf, Bar &br,
                                    Stamper &st, RedBufs &rb, int k, int par, int &sred, double disp_lim)
 {
     typedef typename V4<R>::T R4;
@@ -115,20 +115,10 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, uns
                 R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
                 if (Dg.w > R(0)) {
                     const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
-                    R t5[5] = {0, 0, 0, 0, 0}, pg[3];
+                    R th[5], tl[5], pg[3];
+                    beta_terms<R>(gv, dv, g0, p0, Dg.w, D.beta_rule, th, tl, pg);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const R P = precond<R>(dv[a], Dg.w);
-                        const R g = gv[a], y = g - g0[a];
-                        pg[a] = g * P;
-                        if (D.beta_rule == 0) {
-                            t5[0] += pg[a] * y; t5[1] += pg[a] * g; t5[2] += g * p0[a];
-                        } else {
-                            t5[0] += pg[a] * y; t5[1] += y * P * y; t5[2] += y * p0[a]; t5[3] += p0[a] * g; t5[4] += pg[a] * g;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) a5[q].add(t5[q]);
+                    for (int q = 0; q < 5; ++q) a5[q].add_ff(th[q], tl[q]);
                     PG = mk4<R>(pg[0], pg[1], pg[2], R(0));
                 } else if (P0.x != R(0) || P0.y != R(0) || P0.z != R(0)) {
                     D.p[i] = PG;   // a kinematic vertex never moves along p
@@ -209,7 +199,7 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, uns
                 const double bd = sbeta[key];
                 const R b = R(bd);
                 const bool nzb = bd != 0.0;
-                a1[0].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
+                a1[0].add(tet_pHp_vec<R, CO>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
                                          dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
             }
             seg_warp_sum<R, 1>(a1, key, acc, 2);
@@ -304,7 +294,7 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R> &sh, uns
         md = fmax(md, (R)disp2<R>(D, i, X));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) c->n_active = 0;
-    const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
+    const R m = grid_max<R, PB>(md, rb.max_region<PT, R>(), sh, br, c);
     st.mark(11);  // K_UPDATE
     return (double)m >= disp_lim * disp_lim ? 1 : 0;
 }

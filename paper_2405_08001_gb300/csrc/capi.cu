@@ -63,6 +63,7 @@ sim_status sim_default_options(sim_options *o)
     o->candidate_capacity = 0;
     o->persistent = 1;
     o->split_objects = 0;
+    o->block_shape = 0;
     return SIM_OK;
 }
 

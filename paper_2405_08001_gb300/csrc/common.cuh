@@ -181,6 +181,34 @@ __device__ inline void block_sum_acc(const float (&v)[N], double (&out)[N], doub
     }
     __syncthreads();
 }
+// the same for float-float per-thread values (heads v, tails vl)
+template <int N>
+__device__ inline void block_sum_acc(const float (&v)[N], const float (&vl)[N], double (&out)[N], double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        float h = v[q], l = vl[q];
+        warp_sum_ff(h, l);
+        if (lane == 0) sh[warp * N + q] = (double)h + (double)l;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            out[q] = lane < nw ? sh[lane * N + q] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) out[q] += __shfl_down_sync(0xffffffffu, out[q], o);
+        }
+    }
+    __syncthreads();
+}
+template <int N>
+__device__ inline void block_sum_acc(const double (&v)[N], const double (&vl)[N], double (&out)[N], double *sh)
+{
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = v[q] + vl[q];
+    block_sum<N>(out, sh);
+}
 template <int N>
 __device__ inline void block_sum_acc(const double (&v)[N], double (&out)[N], double *sh)
 {

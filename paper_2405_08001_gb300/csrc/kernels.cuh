@@ -335,19 +335,179 @@ template <typename R> __device__ inline void load_tet_in(const Dev<R> &D, int e,
     }
 }
 
+// Small symmetric 3x3 helpers of the FP32 corotated path.
+__device__ inline void sym_inv3f(const float X[3][3], float Xi[3][3])
+{
+    const float c00 = X[1][1] * X[2][2] - X[1][2] * X[1][2], c01 = X[0][2] * X[1][2] - X[0][1] * X[2][2];
+    const float c02 = X[0][1] * X[1][2] - X[0][2] * X[1][1], c11 = X[0][0] * X[2][2] - X[0][2] * X[0][2];
+    const float c12 = X[0][1] * X[0][2] - X[0][0] * X[1][2], c22 = X[0][0] * X[1][1] - X[0][1] * X[0][1];
+    const float id = 1.0f / (X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02);
+    Xi[0][0] = c00 * id; Xi[1][1] = c11 * id; Xi[2][2] = c22 * id;
+    Xi[0][1] = Xi[1][0] = c01 * id;
+    Xi[0][2] = Xi[2][0] = c02 * id;
+    Xi[1][2] = Xi[2][1] = c12 * id;
+}
+__device__ inline float quad3f(const float M[3][3], float a0, float a1, float a2)
+{
+    return a0 * (M[0][0] * a0 + M[0][1] * a1 + M[0][2] * a2) + a1 * (M[1][0] * a0 + M[1][1] * a1 + M[1][2] * a2) +
+           a2 * (M[2][0] * a0 + M[2][1] * a1 + M[2][2] * a2);
+}
+
+// The corotated densities' FP32 terms of one tet, computed out of line (arguments and result by value) so that
+// their temporaries stay out of the register budget of the passes that run the Neo-Hookean path.
+struct CorotIn {
+    float A[3][3], F[3][3], cf[3][3], w[3][3];   // C - I, F, cof(F), rows of Dm^-1
+    float J, Jm1, mu, lam, hv;
+    int fcr;                                      // 1: FCR (the lambda (J - 1)^2 / 2 term), 0: ARAP
+};
+struct CorotOut {
+    float P[3][3];    // first Piola-Kirchhoff stress times h^2 V
+    float dv[4][3];   // h^2 V Psi_1 d2I1 on the diagonal, per vertex and component
+    float rec[16];    // p^T H p record: R (9, row-major), Dq (6: 00 01 02 11 12 22), J - 1
+    float Psi33;
+};
+
+// U - I = V = sqrt(I + A) - I of the stretch from the metric change A = C - I (symmetric), by Newton's iteration
+// for the principal square root, X <- (X + X^-1 (I + A)) / 2, written for V from V = A / 2 (which bounds the root
+// from above, so the iteration decreases monotonically): V <- V + (I + V)^-1 (A - 2 V - V^2) / 2, symmetrised.  The
+// residual A - 2 V - V^2 is formed from the accurate A, so V keeps its relative accuracy for small strains where the
+// I2 / I1 parts of the stress cancel.  Quadratic convergence; at most 8 steps (5 for stretches up to 10).
+__device__ inline void stretch_minus_identity(const float A[3][3], float V[3][3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) V[a][b] = 0.5f * A[a][b];
+    for (int it = 0; it < 8; ++it) {
+        float X[3][3], Xi[3][3], r[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                X[a][b] = V[a][b] + (a == b ? 1.0f : 0.0f);
+                r[a][b] = A[a][b] - 2.0f * V[a][b] - (V[a][0] * V[0][b] + V[a][1] * V[1][b] + V[a][2] * V[2][b]);
+            }
+        sym_inv3f(X, Xi);
+        float dmax = 0.0f, vmax = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b) {
+                const float d = 0.25f * (Xi[a][0] * r[0][b] + Xi[a][1] * r[1][b] + Xi[a][2] * r[2][b] +
+                                         r[a][0] * Xi[0][b] + r[a][1] * Xi[1][b] + r[a][2] * Xi[2][b]);
+                V[a][b] += d;
+                V[b][a] = V[a][b];
+                dmax = fmaxf(dmax, fabsf(d));
+                vmax = fmaxf(vmax, fabsf(V[a][b]));
+            }
+        if (dmax <= 1e-7f * vmax) break;
+    }
+}
+
+// FCR, ARAP in the FP32 form (Psi_1 = -2 mu, 2 Psi_2 = 2 mu; FCR: Psi_3 = lambda (J - 1), Psi_33 = lambda).  With the
+// stretch U (F = R U) and V = U - I, F^T P = 2 mu U (U - I) + Psi_3 J I = 2 mu (V + V^2) + lambda J (J - 1) I, so
+// P = F^-T M as for the other densities.  R = F (I + V)^-1; the twist modes of d2I1(F)[dF, dF] = a^T (tr(U) I -
+// U)^-1 a (a = axial(R^T dF - dF^T R); derivation in material.cuh) with tr(U) I - U = N = (2 + tr V) I - V; the
+// diagonal takes a = w x rho (rho = R^T e_c), p^T H p the difference Dq = I/2 - N^-1 = N^-1 (tr V I - V) / 2, which
+// is small near a rotation and formed here without cancellation.
+static __device__ __noinline__ CorotOut corot_terms(CorotIn ci)
+{
+    CorotOut co;
+    float V[3][3];
+    stretch_minus_identity(ci.A, V);
+    co.Psi33 = ci.fcr ? ci.lam : 0.0f;
+    const float pj = ci.fcr ? ci.lam * ci.J * ci.Jm1 : 0.0f;
+    float M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            M[a][b] = 2.0f * ci.mu * (V[a][b] + V[a][0] * V[0][b] + V[a][1] * V[1][b] + V[a][2] * V[2][b]) +
+                      (a == b ? pj : 0.0f);
+    const float sj = ci.hv / ci.J;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) co.P[a][b] = sj * (ci.cf[a][0] * M[0][b] + ci.cf[a][1] * M[1][b] + ci.cf[a][2] * M[2][b]);
+    float X[3][3], Xi[3][3], N[3][3], Ni[3][3], W[3][3], Rm[3][3], Dq[3][3];
+    const float tv = V[0][0] + V[1][1] + V[2][2];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            X[a][b] = V[a][b] + (a == b ? 1.0f : 0.0f);
+            N[a][b] = (a == b ? 2.0f + tv : 0.0f) - V[a][b];
+            W[a][b] = (a == b ? tv : 0.0f) - V[a][b];
+        }
+    sym_inv3f(X, Xi);
+    sym_inv3f(N, Ni);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Rm[a][b] = ci.F[a][0] * Xi[0][b] + ci.F[a][1] * Xi[1][b] + ci.F[a][2] * Xi[2][b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            Dq[a][b] = Dq[b][a] = 0.25f * (Ni[a][0] * W[0][b] + Ni[a][1] * W[1][b] + Ni[a][2] * W[2][b] +
+                                           W[a][0] * Ni[0][b] + W[a][1] * Ni[1][b] + W[a][2] * Ni[2][b]);
+    const float ps1 = -2.0f * ci.mu * ci.hv;   // h^2 V Psi_1
+    for (int i = 0; i < 4; ++i) {
+        float w[3];
+        for (int b = 0; b < 3; ++b) w[b] = i == 0 ? -(ci.w[0][b] + ci.w[1][b] + ci.w[2][b]) : ci.w[i - 1][b];
+        for (int a = 0; a < 3; ++a) {
+            const float r0 = Rm[a][0], r1 = Rm[a][1], r2 = Rm[a][2];
+            co.dv[i][a] = ps1 * quad3f(Ni, w[1] * r2 - w[2] * r1, w[2] * r0 - w[0] * r2, w[0] * r1 - w[1] * r0);
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) co.rec[3 * a + b] = Rm[a][b];
+    co.rec[9] = Dq[0][0]; co.rec[10] = Dq[0][1]; co.rec[11] = Dq[0][2];
+    co.rec[12] = Dq[1][1]; co.rec[13] = Dq[1][2]; co.rec[14] = Dq[2][2];
+    co.rec[15] = ci.Jm1;
+    return co;
+}
+
+// p^T H p of one tet of a corotated density in the FP32 form, from the record of its gradient pass:
+//   2 mu (|dF|^2 - a^T N^-1 a) = 2 mu (|sym K|^2 + a^T Dq a),  K = R^T dF,  a = axial(K - K^T)
+// (|skew K|^2 = |a|^2 / 2): a direction that rotates the tet gives sym K = 0 and the small Dq, so the terms that
+// cancel for it never meet in float; FCR adds lambda (cof(F) : dF)^2 + lambda (J - 1) d2det(F)[dF, dF].
+struct CorotPIn {
+    float rec[16];
+    float dF[3][3], F[3][3], cf[3][3];
+    float mu, lam;
+    int fcr;
+};
+static __device__ __noinline__ float corot_pHp(CorotPIn ci)
+{
+    float K[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            K[a][b] = ci.rec[a] * ci.dF[0][b] + ci.rec[3 + a] * ci.dF[1][b] + ci.rec[6 + a] * ci.dF[2][b];
+    float s2 = 0.0f;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) { const float sk = 0.5f * (K[a][b] + K[b][a]); s2 += sk * sk; }
+    const float Dq[3][3] = {{ci.rec[9], ci.rec[10], ci.rec[11]}, {ci.rec[10], ci.rec[12], ci.rec[13]},
+                            {ci.rec[11], ci.rec[13], ci.rec[14]}};
+    float q = 2.0f * ci.mu * (s2 + quad3f(Dq, K[2][1] - K[1][2], K[0][2] - K[2][0], K[1][0] - K[0][1]));
+    if (ci.fcr) {
+        float g3 = 0.0f;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) g3 += ci.cf[a][b] * ci.dF[a][b];
+        const v3<float> f0 = mkv(ci.F[0][0], ci.F[1][0], ci.F[2][0]), f1 = mkv(ci.F[0][1], ci.F[1][1], ci.F[2][1]),
+                        f2 = mkv(ci.F[0][2], ci.F[1][2], ci.F[2][2]);
+        const v3<float> d0 = mkv(ci.dF[0][0], ci.dF[1][0], ci.dF[2][0]), d1 = mkv(ci.dF[0][1], ci.dF[1][1], ci.dF[2][1]),
+                        d2 = mkv(ci.dF[0][2], ci.dF[1][2], ci.dF[2][2]);
+        const float h3 = 2.0f * (dot(d0, cross(d1, f2)) + dot(d0, cross(f1, d2)) + dot(f0, cross(d1, d2)));
+        q += ci.lam * (g3 * g3 + ci.rec[15] * h3);
+    }
+    return q;
+}
+
 // First Piola-Kirchhoff stress of the FP32 form, evaluated from the metric change so that it stays accurate for
 // small strains under any rotation.  With C = F^T F and a density of I2 and I3 (Sec. 3.1: NH or SNH) written in C,
 //   P = F^-T (mu (C - I) + (mu + Psi_3 J) I),   C - I = Dm^-T (Ds^T Ds - Dm^T Dm) Dm^-1,
 // which equals mu F + Psi_3 cof(F) (the I2/I3 form) exactly; mu + Psi_3 J is lambda log J for NH.  The metric
 // change G = Ds^T Ds - Dm^T Dm is accumulated in float-float from the float-float current positions and the tet's
-// float-float rest metric, and C - I = W^T G W is formed with compensated products, so that rounding never acts on
-// the parts that cancel.  J - 1 = (det Ds - det Dm) / det Dm comes from det Ds in float-float and the tet's
+// float-float rest metric, and G W is formed with compensated products, so that rounding never acts on the parts
+// that cancel.  J - 1 = (det Ds - det Dm) / det Dm comes from det Ds in float-float and the tet's
 // float-float det Dm: under large shear a nearly incompressible tet keeps J near 1 while the entries of C - I are
 // of order one, and det C - 1 expanded in those entries cancels (lambda log J then carried about 1e-5 of the
 // stress).  F^-T = cof(F) / J.  Returns false (and flags the error) when det F <= 0.  Also returns Psi_33 for the
 // diagonal.
+template <bool CO>
 __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float> &in, TetF<float> &T, float P[3][3],
-                                         float &Psi33, int e)
+                                         float &Psi33, int e, CorotOut *cr = nullptr)
 {
     const int4 tv = in.tv;
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
@@ -385,11 +545,11 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
         for (int c = 0; c < 3; ++c) T.w[r][c] = in.w[r][c];
     tet_F_from<float>(dsf, T);
     if (!(T.J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
-    // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc), both products compensated (Dot2): their terms are
-    // up to cond(Dm)^2 times larger than A and cancel, which in plain float costs about 1e-6 of the stress on
-    // strongly sheared tets
-    ffl GW[3][3];
-    float A[3][3];
+    // A = C - I = W^T G W with W = Dm^-1 (T.w[r][c] = W_rc): G W with compensated (Dot2) products from the
+    // float-float G, rounded once, then W^T (G W) in float.  The terms are up to cond(Dm)^2 times larger than A and
+    // cancel; in plain float from a rounded G that cost about 1e-6 of the stress on strongly sheared tets
+    // (compensating the second product as well gained nothing measurable)
+    float GW[3][3], A[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -397,17 +557,12 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
             ffacc acc;
 #pragma unroll
             for (int j = 0; j < 3; ++j) acc.add_prod_f(G[i][j], T.w[j][b]);
-            GW[i][b] = acc.ff();
+            GW[i][b] = acc.value();
         }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = a; b < 3; ++b) {
-            ffacc acc;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) acc.add_prod_f(GW[i][b], T.w[i][a]);
-            A[a][b] = A[b][a] = acc.value();
-        }
+        for (int b = a; b < 3; ++b) A[a][b] = A[b][a] = T.w[0][a] * GW[0][b] + T.w[1][a] * GW[1][b] + T.w[2][a] * GW[2][b];
     // J - 1 from det Ds (float-float; the edge vectors ds[a][c] = component a of edge c) and det Dm
     float Jm1;
     {
@@ -426,6 +581,29 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
     if (!(J > 0.0f)) { flag_error(D.ctrl, ERR_INVERTED); return false; }
     const float detC = J * J;
     const float mu = D.mu * in.es, lam = D.lam * in.es;
+    if (CO && (D.model == MAT_FCR || D.model == MAT_ARAP)) {
+        CorotIn ci;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) { ci.A[a][b] = A[a][b]; ci.F[a][b] = T.F[a][b]; ci.cf[a][b] = T.cf[a][b]; ci.w[a][b] = T.w[a][b]; }
+        ci.J = J; ci.Jm1 = Jm1; ci.mu = mu; ci.lam = lam; ci.hv = in.hv; ci.fcr = D.model == MAT_FCR;
+        const CorotOut co = corot_terms(ci);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) P[a][b] = co.P[a][b];
+        Psi33 = co.Psi33;
+        if (cr) *cr = co;
+        if (e >= 0) {   // R, Dq and J - 1 for the p^T H p pass
+            const size_t n = (size_t)D.nt;
+            D.tS[e] = make_float4(co.rec[0], co.rec[1], co.rec[2], co.rec[3]);
+            D.tS[n + e] = make_float4(co.rec[4], co.rec[5], co.rec[6], co.rec[7]);
+            D.tS[2 * n + e] = make_float4(co.rec[8], co.rec[9], co.rec[10], co.rec[11]);
+            D.tS[3 * n + e] = make_float4(co.rec[12], co.rec[13], co.rec[14], co.rec[15]);
+        }
+        return true;
+    }
     // mJ = mu + Psi_3 J: lambda log J (NH), (J - 1)(lambda J - mu) (SNH)
     // k1 = J (Psi_33 J + Psi_3) / 4, k2 = -Psi_3 J / 2: the coefficients of p^T H p in C (tet_pHp_vec)
     float mJ, k1, k2;
@@ -481,7 +659,7 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
 // term has a zero diagonal, so diag_i[a] = h^2 V (2 Psi_2 |w_i|^2 + Psi_33 (cof(F) w_i)_a^2 + Psi_1 d2I1 entry)).  The contributions go to the
 // per-(tet, corner) buffer (segmented scatter), to the block's shared accumulators sacc ([6][SCATTER_MAXU],
 // indexed by the chunk-local vertex; block scatter) or straight to the global accumulators.
-template <typename R>
+template <typename R, bool CO = false>
 __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4][3], R dv[4][3], int e = -1)
 {
     const int4 tv = in.tv;
@@ -490,9 +668,22 @@ __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4
     const R sc = in.hv;
     const R mu = D.mu * in.es, lam = D.lam * in.es;
     R c2 = mu;        // 2 Psi_2
-    R Psi1 = R(0);    // the I1 term (FCR, ARAP; FP64 form)
+    R Psi1 = R(0);    // the I1 term (FCR, ARAP)
     if constexpr (sizeof(R) == 4) {
-        if (!tet_stress_metric(D, in, T, P, Psi33, e)) return false;
+        if constexpr (CO) {
+            CorotOut cr;
+            if (!tet_stress_metric<true>(D, in, T, P, Psi33, e, &cr)) return false;
+            if (D.model == MAT_FCR || D.model == MAT_ARAP) {   // Psi_1 d2I1 on the diagonal
+                c2 = R(2) * mu;
+                Psi1 = R(-2) * mu;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dv[i][a] = cr.dv[i][a];
+            }
+        } else {
+            if (!tet_stress_metric<false>(D, in, T, P, Psi33, e)) return false;
+        }
     } else {
         R ds[3][3];
         tet_ds<R>(D, tv, ds);
@@ -555,12 +746,12 @@ __device__ inline bool tet_grad_eval(const Dev<R> &D, const TetIn<R> &in, R gv[4
     return true;
 }
 
-template <typename R>
+template <typename R, bool CO = false>
 __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> &in, R *sacc = nullptr)
 {
     const int4 tv = in.tv;
     R gv[4][3], dv[4][3];
-    if (!tet_grad_eval<R>(D, in, gv, dv, e)) return;
+    if (!tet_grad_eval<R, CO>(D, in, gv, dv, e)) return;
     if (D.segmented) {
         const int q0 = 4 * e;
         const int n4 = 4 * D.nt;
@@ -596,7 +787,7 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
 // The tets of chunk ch (SCATTER_CHUNK consecutive tets, one per thread of the block): gradient and diagonal,
 // block-scattered when the chunk's distinct vertices fit the shared accumulators.  Called by all threads of a
 // block with a block-uniform ch.
-template <typename R>
+template <typename R, bool CO = false>
 __device__ inline void tet_grad_chunk(const Dev<R> &D, int ch, int par, R *sacc)
 {
     const int e = ch * SCATTER_CHUNK + (int)threadIdx.x;
@@ -612,7 +803,7 @@ __device__ inline void tet_grad_chunk(const Dev<R> &D, int ch, int par, R *sacc)
     if (e < D.nt) {
         TetIn<R> in;
         load_tet_in<R>(D, e, in);
-        tet_grad<R>(D, e, par, in, blk ? sacc : nullptr);
+        tet_grad<R, CO>(D, e, par, in, blk ? sacc : nullptr);
     }
     if (blk) {
         __syncthreads();
@@ -743,7 +934,7 @@ __device__ inline void pair_grad(const Dev<R> &D, int ci, int par)
 }
 
 // Gradient pass: blocks [0, ntb) own tets, the rest loop over the candidates.
-template <typename R>
+template <typename R, bool CO = false>
 __global__ void __launch_bounds__(EB) k_grad(Dev<R> D, int par, int ntb)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -753,7 +944,7 @@ __global__ void __launch_bounds__(EB) k_grad(Dev<R> D, int par, int ntb)
     }
     if ((int)blockIdx.x < ntb) {
         __shared__ R sacc[6 * SCATTER_MAXU];
-        tet_grad_chunk<R>(D, blockIdx.x, par, sacc);
+        tet_grad_chunk<R, CO>(D, blockIdx.x, par, sacc);
     } else {
         const int nc = min(D.ctrl->n_cand, D.cand_cap);
         const int stride = (gridDim.x - ntb) * blockDim.x;
@@ -807,37 +998,72 @@ template <typename R> __device__ inline typename V4<R>::T dir_of(const Dev<R> &D
     return dir_from<R>(g, ldcg4(D.p + i), b, nzb);
 }
 
+// adds a b to the float-float (h, l) exactly up to the final rounding of l: FMA TwoProd, then TwoSum of the head
+__device__ inline void ff_add_prod(float &h, float &l, float a, float b)
+{
+    const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(h, p), bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+// adds a b c the same way (a b formed exactly first, its tail times c added to l)
+__device__ inline void ff_add_prod3(float &h, float &l, float a, float b, float c)
+{
+    const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);
+    ff_add_prod(h, l, p, c);
+    l = __fmaf_rn(e, c, l);
+}
+
+// The beta pass's sums for one vertex (Sec. 4.1-4.2) -- PR+: {g P y, g P g, g . p0}; DK: {g P y, y P y, y . p0,
+// p0 . g, g P g}, with y = g - g0 -- as heads th and tails tl, and its preconditioned gradient P g.  In the FP32 form
+// every product is formed exactly (FMA TwoProd) and summed in float-float: the PR and DK numerators cancel, and
+// rounded float products carried about 1e-5 of beta into the direction.  m is the vertex mass (Jacobi floor).
+template <typename R>
+__device__ inline void beta_terms(const R gv[3], const R dv[3], const R g0[3], const R p0[3], R m, int rule, R th[5],
+                                  R tl[5], R pg[3])
+{
+#pragma unroll
+    for (int q = 0; q < 5; ++q) { th[q] = R(0); tl[q] = R(0); }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R P = precond<R>(dv[a], m);
+        const R g = gv[a], y = g - g0[a];
+        pg[a] = g * P;
+        if constexpr (sizeof(R) == 4) {
+            if (rule == 0) {
+                ff_add_prod3(th[0], tl[0], g, P, y); ff_add_prod3(th[1], tl[1], g, P, g); ff_add_prod(th[2], tl[2], g, p0[a]);
+            } else {
+                ff_add_prod3(th[0], tl[0], g, P, y); ff_add_prod3(th[1], tl[1], y, P, y); ff_add_prod(th[2], tl[2], y, p0[a]);
+                ff_add_prod(th[3], tl[3], p0[a], g); ff_add_prod3(th[4], tl[4], g, P, g);
+            }
+        } else {
+            if (rule == 0) {
+                th[0] += pg[a] * y; th[1] += pg[a] * g; th[2] += g * p0[a];
+            } else {
+                th[0] += pg[a] * y; th[1] += y * P * y; th[2] += y * p0[a]; th[3] += p0[a] * g; th[4] += pg[a] * g;
+            }
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(VB) k_dots(Dev<R> D, int par)
 {
     __shared__ double sh[32 * 5];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     // PR+: {g P (g - g0), g P g, g . p0, 0, 0};  DK: {g P y, y P y, y . p0, p0 . g, g P g}
-    R s[5] = {0, 0, 0, 0, 0};
+    R s[5] = {0, 0, 0, 0, 0}, sl[5] = {0, 0, 0, 0, 0};
     if (i < D.nv) {
         const typename V4<R>::T G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i), P0 = ldcg4(D.p + i);
         if (Dg.w > R(0)) {
             const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const R P = precond<R>(dv[a], Dg.w);
-                const R g = gv[a], y = g - g0[a];
-                if (D.beta_rule == 0) {
-                    s[0] += g * P * y;
-                    s[1] += g * P * g;
-                    s[2] += g * p0[a];
-                } else {
-                    s[0] += g * P * y;
-                    s[1] += y * P * y;
-                    s[2] += y * p0[a];
-                    s[3] += p0[a] * g;
-                    s[4] += g * P * g;
-                }
-            }
+            R pg[3];
+            beta_terms<R>(gv, dv, g0, p0, Dg.w, D.beta_rule, s, sl, pg);
         }
     }
     double sd[5];
-    block_sum_acc<5>(s, sd, sh);
+    block_sum_acc<5>(s, sl, sd, sh);
     if (publish_partials<5>(sd, D.part, &D.ctrl->ticket[TK_DOTS])) {
         double t[5];
         finish_sums<5>(t, D.part, sh);
@@ -932,7 +1158,7 @@ __global__ void __launch_bounds__(VB) k_dir(Dev<R> D, int par)
 
 // h^2 V [2 Psi_2 |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF] + Psi_1 d2I1(F)[dF, dF]] (Sec. 3.1 with
 // H2 = 2I, H3 the det Hessian, H1 the Hessian of tr(S)) for the direction values P0..P3 of the tet's vertices.
-template <typename R>
+template <typename R, bool CO = false>
 __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const typename V4<R>::T &P0,
                                 const typename V4<R>::T &P1, const typename V4<R>::T &P2, const typename V4<R>::T &P3)
 {
@@ -958,6 +1184,21 @@ __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const ty
         const size_t n = (size_t)D.nt;
         const float4 q0 = __ldcg(D.tS + e), q1 = __ldcg(D.tS + n + e), q2 = __ldcg(D.tS + 2 * n + e);
         const float4 q3 = __ldcg(D.tS + 3 * n + e);
+        if (CO && (D.model == MAT_FCR || D.model == MAT_ARAP)) {
+            CorotPIn ci;
+            const float rq[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w,
+                                  q3.x, q3.y, q3.z, q3.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) ci.rec[k] = rq[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) { ci.dF[a][b] = dF[a][b]; ci.F[a][b] = T.F[a][b]; ci.cf[a][b] = T.cf[a][b]; }
+            R mu, lam;
+            tet_material<R>(D, e, mu, lam);
+            ci.mu = mu; ci.lam = lam; ci.fcr = D.model == MAT_FCR;
+            return D.hv[e] * corot_pHp(ci);
+        }
         const float S00 = q0.x, S01 = q0.y, S02 = q0.z, S11 = q0.w, S12 = q1.x, S22 = q1.y;
         const float C00 = q1.z, C01 = q1.w, C02 = q2.x, C11 = q2.y, C12 = q2.z, C22 = q2.w;
         const float k1 = q3.x, k2 = q3.y;
@@ -1016,11 +1257,11 @@ __device__ inline R tet_pHp_vec(const Dev<R> &D, int e, const int4 &tv, const ty
     return D.hv[e] * q;
 }
 
-template <typename R>
+template <typename R, bool CO = false>
 __device__ inline R tet_pHp(const Dev<R> &D, int e)
 {
     const int4 tv = D.tet[e];
-    return tet_pHp_vec<R>(D, e, tv, ldcg4(D.p + tv.x), ldcg4(D.p + tv.y), ldcg4(D.p + tv.z), ldcg4(D.p + tv.w));
+    return tet_pHp_vec<R, CO>(D, e, tv, ldcg4(D.p + tv.x), ldcg4(D.p + tv.y), ldcg4(D.p + tv.z), ldcg4(D.p + tv.w));
 }
 
 // Eqs. 12-13 with the recorded A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d, for direction values P0..P3, in
@@ -1087,7 +1328,7 @@ __device__ inline void finish_step(const Dev<R> &D, double pHp)
     c->k = k + 1;
 }
 
-template <typename R>
+template <typename R, bool CO = false>
 __global__ void __launch_bounds__(EB) k_pHp(Dev<R> D, int ntb)
 {
     __shared__ double sh[32];
@@ -1095,7 +1336,7 @@ __global__ void __launch_bounds__(EB) k_pHp(Dev<R> D, int ntb)
     if ((int)blockIdx.x < ntb) {
         R s[1] = {R(0)};
         const int e = blockIdx.x * blockDim.x + threadIdx.x;
-        if (e < D.nt) s[0] = tet_pHp<R>(D, e);
+        if (e < D.nt) s[0] = tet_pHp<R, CO>(D, e);
         block_sum_acc<1>(s, sd, sh);
     } else {
         const int na = D.ctrl->n_active;

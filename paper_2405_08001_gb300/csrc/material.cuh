@@ -7,12 +7,14 @@
 // None has Psi_11 or Psi_22 terms, so P = Psi_1 R + 2 Psi_2 F + Psi_3 cof(F) and
 //   dF : d2Psi/dF2 : dF = 2 Psi_2 |dF|^2 + Psi_33 (cof(F) : dF)^2 + Psi_3 d2det(F)[dF, dF] + Psi_1 d2I1(F)[dF, dF].
 //
-// The I1 terms (FCR, ARAP; FP64 form) need no singular value decomposition.  The rotation R comes from the scaled
+// The I1 terms (FCR, ARAP) need no singular value decomposition.  In the FP64 form the rotation R comes from the scaled
 // Newton iteration X <- (g X + X^-T / g) / 2, g = |det X|^(-1/3) (Higham, 1986), started at F (det F > 0), and
 // S = R^T F.  Differentiating F = R S with R^T dR = [w]x skew and dS symmetric gives 2 skew(R^T dF) = [(tr(S) I -
 // S) w]x, so with a = axial(R^T dF - dF^T R):
 //   d2I1(F)[dF, dF] = dF : dR[dF] = a^T (tr(S) I - S)^-1 a,
-// and for the diagonal (dF = e_c w^T, w a vertex's weight vector, rho = R^T e_c) a = w x rho.
+// and for the diagonal (dF = e_c w^T, w a vertex's weight vector, rho = R^T e_c) a = w x rho.  The FP32 form takes
+// U - I = sqrt(I + (C - I)) - I from the accurate metric change by a Newton square root instead (kernels.cuh,
+// corot_terms), so that the stress keeps its relative accuracy near a rotation.
 #pragma once
 
 namespace pncg {

@@ -22,7 +22,10 @@
 
 namespace pncg {
 
-constexpr int PB = 256;                       // threads per block of the persistent kernel
+// The block size PB (threads per block) and the blocks per SM of the persistent kernel are template parameters:
+// the library instantiates a few shapes (persist_shapes) and can pick one per workload by timing (the block-shape
+// autotuner, sim_options.block_shape = -1).
+constexpr int MAXG = 1024;   // most blocks a persistent launch may have (the host caps its grid at this)
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // a barrier wait gives up after 4 s
 
 // Arrival counter of the grid barriers, zeroed before each launch.  Every block passes the same sequence of
@@ -106,6 +109,7 @@ template <> struct Acc<double> {
     __device__ inline void add(double x) { v += x; }
     __device__ inline void add_d(double x) { v += x; }
     __device__ inline void add(const Acc &o) { v += o.v; }
+    __device__ inline void add_ff(double h, double l) { v += h + l; }
     __device__ inline Acc shfl_down(int o) const { Acc r; r.v = __shfl_down_sync(0xffffffffu, v, o); return r; }
     __device__ inline Acc shfl_up(int o) const { Acc r; r.v = __shfl_up_sync(0xffffffffu, v, o); return r; }
     __device__ inline double value() const { return v; }
@@ -126,6 +130,13 @@ template <> struct Acc<float> {
         const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(o.h, bp));
         h = s;
         l = __fadd_rn(__fadd_rn(l, o.l), e);
+    }
+    __device__ inline void add_ff(float oh, float ol)   // a float-float term
+    {
+        Acc o;
+        o.h = oh;
+        o.l = ol;
+        add(o);
     }
     __device__ inline void add_d(double x)   // a double term: its float head and the rounding remainder
     {
@@ -185,7 +196,7 @@ __device__ inline Share share_of(int n)
     return {b0, min(n, b0 + per)};
 }
 
-template <typename R> struct PShared {
+template <typename R, int PB> struct PShared {
     Acc<R> t[NQ][PB];
     R mx[PB];
     double res[NQ + 1];   // reduced results: sums, then the max
@@ -197,8 +208,8 @@ template <typename R> struct PShared {
 
 // Block part of a grid reduction: N sums (and, with MX, a max of non-negative values) of the block's threads,
 // written as the block's partials (quantity q at part[q * gridDim.x + block], the max in slot N).
-template <typename R, int N, bool MX>
-__device__ inline void block_publish(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R> &sh)
+template <typename R, int PB, int N, bool MX>
+__device__ inline void block_publish(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R, PB> &sh)
 {
     static_assert(N <= NQ && N + (MX ? 1 : 0) <= PB / 32, "one warp per quantity");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -225,9 +236,8 @@ __device__ inline void block_publish(Acc<R> (&a)[N], R mx, typename PartT<R>::T 
 // L2), then the block reduces them transposed like block_publish (warp q sums quantity q, warp N takes the max, in
 // block order within each lane's stride); the results land in sh.res (sums in double), and thread 0 reads the
 // fetched scalars.  Every block computes bitwise the same results.  Ends with a CTA barrier.
-constexpr int MAXG = 2 * PB;   // most blocks a persistent launch may have (the host caps its grid at this)
-template <typename R, int N, bool MX>
-__device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R> &sh, const Fetch *f)
+template <typename R, int PB, int N, bool MX>
+__device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R, PB> &sh, const Fetch *f)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = gridDim.x;
@@ -235,10 +245,10 @@ __device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R>
         if (f->pi) sh.fi = (volatile const int &)*f->pi;
         if (f->pe) sh.fe = (volatile const uint32_t &)*f->pe;
     }
-    Acc<R> v[N][MAXG / PB];
+    Acc<R> v[N][(MAXG + PB - 1) / PB];
     R m = R(0);
 #pragma unroll
-    for (int j = 0; j < MAXG / PB; ++j) {
+    for (int j = 0; j < (MAXG + PB - 1) / PB; ++j) {
         const int b = threadIdx.x + j * PB;
         if (b < G) {
 #pragma unroll
@@ -250,7 +260,7 @@ __device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R>
     for (int q = 0; q < N; ++q) {
         Acc<R> s = v[q][0];
 #pragma unroll
-        for (int j = 1; j < MAXG / PB; ++j) s.add(v[q][j]);
+        for (int j = 1; j < (MAXG + PB - 1) / PB; ++j) s.add(v[q][j]);
         sh.t[q][threadIdx.x] = s;
     }
     if (MX) sh.mx[threadIdx.x] = m;
@@ -272,19 +282,19 @@ __device__ inline void grid_collect(const typename PartT<R>::T *part, PShared<R>
 }
 
 // Grid-wide sums of N accumulators (and a max): block part, barrier, collection into sh.res.
-template <typename R, int N, bool MX>
-__device__ inline void grid_reduce(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R> &sh, Bar &br,
+template <typename R, int PB, int N, bool MX>
+__device__ inline void grid_reduce(Acc<R> (&a)[N], R mx, typename PartT<R>::T *part, PShared<R, PB> &sh, Bar &br,
                                    Ctrl *c, const Fetch *f = nullptr)
 {
-    block_publish<R, N, MX>(a, mx, part, sh);
+    block_publish<R, PB, N, MX>(a, mx, part, sh);
     grid_barrier(br, c);
-    grid_collect<R, N, MX>(part, sh, f);
+    grid_collect<R, PB, N, MX>(part, sh, f);
 }
 
 // Grid-wide max of non-negative values of the element type (exact); one grid barrier.  `part` holds gridDim.x
 // values of type R.  Returned in every thread.
-template <typename R>
-__device__ inline R grid_max(R v, R *part, PShared<R> &sh, Bar &br, Ctrl *c)
+template <typename R, int PB>
+__device__ inline R grid_max(R v, R *part, PShared<R, PB> &sh, Bar &br, Ctrl *c)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     sh.mx[threadIdx.x] = v;
@@ -299,7 +309,7 @@ __device__ inline R grid_max(R v, R *part, PShared<R> &sh, Bar &br, Ctrl *c)
     grid_barrier(br, c);
     R m = R(0);
 #pragma unroll
-    for (int j = 0; j < MAXG / PB; ++j) {
+    for (int j = 0; j < (MAXG + PB - 1) / PB; ++j) {
         const int b = threadIdx.x + j * PB;
         if (b < (int)gridDim.x) m = fmax(m, __ldcg(part + b));
     }
@@ -388,13 +398,14 @@ namespace pncg {
 
 // ------------------------------------------------------------------------------------------------ the kernel
 
-template <typename R>
-__global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, PersistArgs A)
+template <typename R, int PB, int MINB, bool CO = false>
+__global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, PersistArgs A)
 {
     typedef typename V4<R>::T R4;
     typedef typename PartT<R>::T PT;
-    __shared__ __align__(16) unsigned char sh_raw[sizeof(PShared<R>)];   // raw storage: Acc has initialisers
-    PShared<R> &sh = *reinterpret_cast<PShared<R> *>(sh_raw);
+    static_assert(PB % 32 == 0 && PB / 32 >= NQ + 1, "one warp per reduced quantity");
+    __shared__ __align__(16) unsigned char sh_raw[sizeof(PShared<R, PB>)];   // raw storage: Acc has initialisers
+    PShared<R, PB> &sh = *reinterpret_cast<PShared<R, PB> *>(sh_raw);
     __shared__ int sh_i;
     // one buffer for several phases: the gradient's block-scatter accumulators, the candidate build's chunk
     // offsets, then the warps' query batches
@@ -402,7 +413,8 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                                  sizeof(BPQWarp) * (PB / 32));
     __shared__ __align__(16) unsigned char sbuf[SBUF];
     static_assert(SBUF >= 2 * MAX_SCENES * sizeof(double), "the batched form keeps per-scene beta and alpha here");
-    static_assert(PB == SCATTER_CHUNK, "a block's tet loop covers one scatter chunk");
+    // the block-aggregated scatter (options.scatter = block) covers one chunk of SCATTER_CHUNK tets per block: only
+    // the shape with PB == SCATTER_CHUNK runs it (the host keeps that shape for it)
     Ctrl *c = D.ctrl;
     RedBufs rb;
     rb.base = A.part;
@@ -452,7 +464,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 md = fmax(md, (R)disp2<R>(D, i, X));
             }
         }
-        const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
+        const R m = grid_max<R, PB>(md, rb.max_region<PT, R>(), sh, br, c);
         if (!skip_step && (double)m >= disp_lim * disp_lim) rebuild = 1;
         gPg_prev = 0.0;
         dE0 = 0.0;
@@ -490,7 +502,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 B.bhi[j] = hi;
                 ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
             }
-            const float ext = (float)grid_max<R>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
+            const float ext = (float)grid_max<R, PB>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
             if (lead) c->cell_bits = __float_as_uint(ext);
             st.mark(1);   // K_BP_BOXES
             const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
@@ -603,10 +615,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
         }
         {
             const Share cs = share_of(min(ncand, D.cand_cap));
-            if (D.scatter_block) {
+            if (PB == SCATTER_CHUNK && D.scatter_block) {
                 const int nch = (D.nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
                 for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
-                    tet_grad_chunk<R>(D, ch, par, reinterpret_cast<R *>(sbuf));
+                    tet_grad_chunk<R, CO>(D, ch, par, reinterpret_cast<R *>(sbuf));
                 for (int ci = cs.b0 + (int)threadIdx.x; ci < cs.b1; ci += PB) pair_grad<R>(D, ci, par);
             } else {
                 // the block's share of the tets, then candidates 32 at a time per warp from a grid-wide cursor: the
@@ -616,7 +628,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 for (int q = threadIdx.x; q < nts; q += PB) {
                     TetIn<R> in;
                     load_tet_in<R>(D, ts.b0 + q, in);
-                    tet_grad<R>(D, ts.b0 + q, par, in);
+                    tet_grad<R, CO>(D, ts.b0 + q, par, in);
                 }
                 if (lead) c->ticket[TK_PAIRS + ((k + 1) & 1)] = 0u;   // the next iteration's cursor
                 unsigned int *cur = &c->ticket[TK_PAIRS + (k & 1)];
@@ -652,7 +664,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             st.mark(7);   // K_GATHER
         }
         if (D.nseg > 1) {   // batched scenes: per-scene beta, alpha (batched.cuh)
-            if (batched_tail<R>(D, c, sh, sbuf, br, st, rb, k, par, sred, disp_lim)) rebuild = 1;
+            if (batched_tail<R, PB, CO>(D, c, sh, sbuf, br, st, rb, k, par, sred, disp_lim)) rebuild = 1;
             continue;
         }
         // ------------------------------------------------------------ a4: beta (and P g for the direction)
@@ -669,20 +681,10 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
                 if (Dg.w > R(0)) {
                     const R gv[3] = {G.x, G.y, G.z}, dv[3] = {Dg.x, Dg.y, Dg.z}, g0[3] = {G0.x, G0.y, G0.z}, p0[3] = {P0.x, P0.y, P0.z};
-                    R t5[5] = {0, 0, 0, 0, 0}, pg[3];
+                    R th[5], tl[5], pg[3];
+                    beta_terms<R>(gv, dv, g0, p0, Dg.w, D.beta_rule, th, tl, pg);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const R P = precond<R>(dv[a], Dg.w);
-                        const R g = gv[a], y = g - g0[a];
-                        pg[a] = g * P;
-                        if (D.beta_rule == 0) {
-                            t5[0] += pg[a] * y; t5[1] += pg[a] * g; t5[2] += g * p0[a];
-                        } else {
-                            t5[0] += pg[a] * y; t5[1] += y * P * y; t5[2] += y * p0[a]; t5[3] += p0[a] * g; t5[4] += pg[a] * g;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) s5[q].add(t5[q]);
+                    for (int q = 0; q < 5; ++q) s5[q].add_ff(th[q], tl[q]);
                     PG = mk4<R>(pg[0], pg[1], pg[2], R(0));
                 } else if (P0.x != R(0) || P0.y != R(0) || P0.z != R(0)) {
                     D.p[i] = PG;   // a kinematic vertex never moves along p
@@ -693,7 +695,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             }
             Fetch f;
             f.pi = &c->n_active;
-            grid_reduce<R, 5, false>(s5, R(0), rb.sum_region<PT>(), sh, br, c, &f);
+            grid_reduce<R, PB, 5, false>(s5, R(0), rb.sum_region<PT>(), sh, br, c, &f);
             st.mark(8);   // K_DOTS
             // beta and the restart test: scalar FP64 work, done by one thread and broadcast
             if (threadIdx.x == 0) {
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 if (q < nts) {
                     const int e = ts.b0 + q;
                     const int4 tv = D.tet[e];
-                    s3[2].add(tet_pHp_vec<R>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
+                    s3[2].add(tet_pHp_vec<R, CO>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
                                              dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
                 } else {
                     Active<R> ap;
@@ -772,7 +774,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
             Fetch f;
             f.pe = &c->err;
             PT *part = rb.sum_region<PT>();
-            block_publish<R, 3, true>(s3, pm, part, sh);
+            block_publish<R, PB, 3, true>(s3, pm, part, sh);
             grid_barrier(br, c);
             // the update's loads of this thread's own vertex go out before the partial collection and the step rule
             if (ov < vs.b1) {
@@ -781,7 +783,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 uXT = ldcg4(D.xtil + ov);
                 uXB = disp_ref<R>(D, ov);
             }
-            grid_collect<R, 3, true>(part, sh, &f);
+            grid_collect<R, PB, 3, true>(part, sh, &f);
             st.mark(10);  // K_PHP (direction included)
             // the step rule (Sec. 4.3) and the predicted decrease: scalar FP64 work, done by one thread
             if (threadIdx.x == 0) {
@@ -857,7 +859,7 @@ __global__ void __launch_bounds__(PB, 2) k_persistent(Dev<R> D, BPDev B, Persist
                 }
             }
             if (lead) c->n_active = 0;
-            const R m = grid_max<R>(md, rb.max_region<PT, R>(), sh, br, c);
+            const R m = grid_max<R, PB>(md, rb.max_region<PT, R>(), sh, br, c);
             st.mark(11);  // K_UPDATE
             if ((double)m >= disp_lim * disp_lim) rebuild = 1;
         }

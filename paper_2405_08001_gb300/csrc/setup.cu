@@ -116,15 +116,11 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
     }
     if (opt.iters <= 0 || opt.beta < 0 || opt.beta > 1 || opt.pnorm < 0 || opt.pnorm > 1 || opt.precision < 0 ||
         opt.precision > 1 || opt.scatter < 0 || opt.scatter > 2 || opt.persistent < 0 || opt.persistent > 2 ||
-        opt.split_objects < 0 || opt.split_objects > 1) {
+        opt.split_objects < 0 || opt.split_objects > 1 || opt.block_shape < -1 || opt.block_shape > 3) {
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }
     if (mat->model < SIM_MAT_NH || mat->model > SIM_MAT_ARAP) { err = "unknown material model"; return SIM_ERR_INVALID_ARG; }
-    if ((mat->model == SIM_MAT_FCR || mat->model == SIM_MAT_ARAP) && opt.precision == SIM_FP32_MIXED) {
-        err = "the corotated densities (FCR, ARAP) run in the FP64 form";
-        return SIM_ERR_INVALID_ARG;
-    }
     const int nv = mesh->n_verts, nt = mesh->n_tets;
     m.nv = nv; m.nt = nt; m.h = dt; m.dhat = dhat; m.kappa = kappa; m.opt = opt;
     m.model = mat->model;

@@ -8,7 +8,7 @@
 
 #include "broadphase.cuh"
 #include "kernels.cuh"
-#include "persistent.cuh"
+#include "persist_shapes.cuh"
 #include "adjoint.cuh"
 #include "sim.h"
 
@@ -98,14 +98,14 @@ template <typename R> __global__ void __launch_bounds__(VB) k_eval_vert_pHp(Dev<
     }
 }
 // p^T H p (tets + active pairs) only, for sim_eval_pHp: ctrl->pHp = sum + pHp_vert
-template <typename R> __global__ void __launch_bounds__(EB) k_eval_pHp(Dev<R> D, int ntb)
+template <typename R, bool CO = false> __global__ void __launch_bounds__(EB) k_eval_pHp(Dev<R> D, int ntb)
 {
     __shared__ double sh[32];
     double sdd[1] = {0.0};
     if ((int)blockIdx.x < ntb) {
         R s[1] = {R(0)};
         const int e = blockIdx.x * blockDim.x + threadIdx.x;
-        if (e < D.nt) s[0] = tet_pHp<R>(D, e);
+        if (e < D.nt) s[0] = tet_pHp<R, CO>(D, e);
         block_sum_acc<1>(s, sdd, sh);
     } else {
         const int na = D.ctrl->n_active;
@@ -162,7 +162,7 @@ public:
         for (int k = 0; k < n; ++k) {
             sim_status st = stage_targets(targets ? targets + (size_t)k * 3 * M.nfix : nullptr);
             if (st != SIM_OK) return st;
-            if (tune_phase > 0 && tune_phase < 3 && steps_run >= 1) {
+            if (tune_next >= 0 && steps_run >= 1) {
                 st = tuned_step();
                 if (st != SIM_OK) return st;
                 ++steps_run;
@@ -179,17 +179,32 @@ public:
         return sync_and_check();
     }
 
-    // Launch-form autotuning (options.persistent = 2): one time step in each form, timed on the GPU with events on
-    // the solver's stream; the faster form is kept.  Both steps are ordinary time steps of the simulation.
+    // Autotuning: the candidates are block shapes of the persistent form (options.block_shape = -1) and, with
+    // options.persistent = 2, the per-phase form; from the second time step on each candidate runs TUNE_REPS time
+    // steps, interleaved (c0, c1, .., c0, c1, ..), each timed on the GPU with events on the solver's stream, and the
+    // candidate with the fastest step is kept.  Every tuned step is an ordinary time step of the simulation.
+    static constexpr int TUNE_REPS = 2;
     void drop_graph()
     {
         if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
         if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     }
+    // candidate c: a shape index >= 0 (persistent form) or -1 (one kernel per phase)
+    void apply_config(int c)
+    {
+        const bool want_persist = c >= 0;
+        const int want_shape = c >= 0 ? c : shape;
+        if (persist != want_persist || shape != want_shape) {
+            persist = want_persist;
+            shape = want_shape;
+            pgrid = shape_grid[shape];
+            drop_graph();
+        }
+    }
     sim_status tuned_step()
     {
-        const bool want_persist = tune_phase == 1;
-        if (persist != want_persist) { persist = want_persist; drop_graph(); }
+        const int nc = (int)tune_cfg.size(), cand = tune_next % nc;
+        apply_config(tune_cfg[cand]);
         if (M.opt.use_graph && !gexec) {
             sim_status st = capture();
             if (st != SIM_OK) return st;
@@ -206,13 +221,16 @@ public:
         }
         CK(cudaEventRecord(tune_ev[1], s));
         CK(cudaEventSynchronize(tune_ev[1]));
-        CK(cudaEventElapsedTime(&tune_ms[tune_phase - 1], tune_ev[0], tune_ev[1]));
-        if (tune_phase == 1) {
-            tune_phase = 2;
-        } else {
-            tune_phase = 3;
-            const bool best = tune_ms[0] <= tune_ms[1];
-            if (persist != best) { persist = best; drop_graph(); }
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]));
+        if ((int)tune_ms.size() < nc) tune_ms.assign(nc, 3.0e38f);
+        tune_ms[cand] = std::min(tune_ms[cand], ms);
+        if (++tune_next == TUNE_REPS * nc) {
+            int best = 0;
+            for (int i = 1; i < nc; ++i)
+                if (tune_ms[i] < tune_ms[best]) best = i;
+            apply_config(tune_cfg[best]);
+            tune_next = -1;
         }
         return SIM_OK;
     }
@@ -269,6 +287,8 @@ public:
             st->dE0 = hctrl->dE0;
             st->dE_last = hctrl->dE;
             st->launch_form = persist ? 1 : 0;
+            st->block_threads = persist ? PSHAPE_PB[shape] : 0;
+            st->blocks_per_sm = persist ? pgrid / nsm : 0;
             st->n_scenes = M.nseg;
             st->n_near_fp64 = hctrl->n_near64;
         }
@@ -386,7 +406,8 @@ public:
         CK(cudaMemcpyAsync(stage, p, 24 * (size_t)M.nv, cudaMemcpyDefault, s));
         k_packR<R4, R><<<nb, 256, 0, s>>>(stage, D.p, M.nv);
         k_eval_vert_pHp<R><<<nvb, VB, 0, s>>>(D, 0);
-        k_eval_pHp<R><<<ntb + npb, EB, 0, s>>>(D, ntb);
+        if (corot) k_eval_pHp<R, true><<<ntb + npb, EB, 0, s>>>(D, ntb);
+        else k_eval_pHp<R><<<ntb + npb, EB, 0, s>>>(D, ntb);
         CK(cudaMemcpyAsync(D.p, psave, sizeof(R4) * (size_t)M.nv, cudaMemcpyDeviceToDevice, s));
         eval_restore();
         r = sync_and_check();
@@ -493,11 +514,11 @@ public:
             mark(K_BP_SCAN); bp_scan<<<3 * B.H / BP_SCAN_N, BP_SCAN_T, 0, s>>>(B);
             mark(K_BP_FILL); bp_fill<<<bpb_prims, BP_B, 0, s>>>(B);
             mark(K_BP_QUERY); bp_query<<<bpb_query, BP_B, 0, s>>>(B);
-            mark(K_GRAD); k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
+            mark(K_GRAD); launch_grad_kernel(par);
             if (D.segmented) { mark(K_GATHER); k_gather<R><<<nvb, VB, 0, s>>>(D, par); }
             mark(K_DOTS); k_dots<R><<<nvb, VB, 0, s>>>(D, par);
             mark(K_DIR); k_dir<R><<<nvb, VB, 0, s>>>(D, par);
-            mark(K_PHP); k_pHp<R><<<ntb + npb, EB, 0, s>>>(D, ntb);
+            mark(K_PHP); launch_pHp_kernel();
             mark(K_UPDATE); k_update<R><<<nvb, VB, 0, s>>>(D, par);
         }
         mark(K_FINISH); launch_finish();
@@ -728,8 +749,12 @@ private:
     std::vector<cudaEvent_t> prof_ev;
     // persistent form
     bool persist = false;
-    int tune_phase = 0;          // autotuning: 1 = next tuned step runs persistent, 2 = per phase, 3 = done
-    float tune_ms[2] = {0.0f, 0.0f};
+    bool corot = false;                // FP32 form with a corotated density (FCR, ARAP): its own kernel instantiations
+    int shape = 0;                     // block shape of the persistent form (persist_shapes.cuh)
+    int shape_grid[N_PSHAPES] = {};    // its grid (blocks), 0 = the shape cannot be launched
+    std::vector<int> tune_cfg;         // autotuning candidates: shape index, or -1 = per-phase kernels
+    std::vector<float> tune_ms;
+    int tune_next = -1;                // the next candidate to time (-1: no tuning, or done)
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     long long steps_run = 0;
     int pgrid = 0;
@@ -783,16 +808,32 @@ private:
     sim_status setup_persistent()
     {
         persist = false;
+        corot = sizeof(R) == 4 && (M.model == MAT_FCR || M.model == MAT_ARAP);
         if (!M.opt.persistent) return SIM_OK;
         if (((3 * B.H) >> B.cshift_p) > BP_MAX_CHUNKS) return SIM_OK;   // chunk offsets live in shared memory
         int coop = 0;
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (!coop) return SIM_OK;
-        int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<R>, PB, 0));
-        if (per_sm <= 0) return SIM_OK;
-        per_sm = std::min(per_sm, 4);
-        pgrid = std::min(per_sm * nsm, MAXG);
+        // every shape's grid: as many blocks per SM as it is built for and the occupancy allows
+        int gmax = 0;
+        for (int sh = 0; sh < N_PSHAPES; ++sh) {
+            int per_sm = 0;
+            if (corot && sh > 0) { shape_grid[sh] = 0; continue; }   // the corotated FP32 kernel: shape 0 only
+            if constexpr (sizeof(R) == 4) {
+                if (corot) CK(persist_occupancy_corot(&per_sm));
+                else CK(persist_occupancy_shape<R>(sh, &per_sm));
+            } else {
+                CK(persist_occupancy_shape<R>(sh, &per_sm));
+            }
+            per_sm = std::min(per_sm, PSHAPE_MINB[sh]);
+            shape_grid[sh] = per_sm > 0 ? std::min(per_sm * nsm, MAXG) : 0;
+            gmax = std::max(gmax, shape_grid[sh]);
+        }
+        const bool block_scatter = M.opt.scatter == SIM_SCATTER_BLOCK;   // runs in shape 0 only
+        shape = (block_scatter || M.opt.block_shape < 0) ? 0 : M.opt.block_shape;
+        if (shape_grid[shape] <= 0) shape = 0;
+        if (shape_grid[shape] <= 0) return SIM_OK;
+        pgrid = shape_grid[shape];
         unsigned int *sync;
         AL2(sync, 32);                    // the barrier arrival counter on a 128-byte line of its own
         bar_count = sync;
@@ -801,12 +842,21 @@ private:
         AL2(pnx, (size_t)M.nv);
         D.pg = pg;
         D.pnext = pnx;
-        const size_t bytes = 16 * (size_t)pgrid * sizeof(typename PartT<R>::T) + 2 * (size_t)pgrid * sizeof(R);
+        const size_t bytes = 16 * (size_t)gmax * sizeof(typename PartT<R>::T) + 2 * (size_t)gmax * sizeof(R);
         char *pp;
         AL2(pp, bytes);
         ppart = pp;
         persist = true;
-        tune_phase = (M.opt.persistent == 2 && M.nseg == 1) ? 1 : 0;
+        tune_cfg.clear();
+        if (M.opt.block_shape < 0 && !block_scatter) {
+            for (int sh = 0; sh < N_PSHAPES; ++sh) if (shape_grid[sh] > 0) tune_cfg.push_back(sh);
+        } else {
+            tune_cfg.push_back(shape);
+        }
+        if (M.opt.persistent == 2 && M.nseg == 1) tune_cfg.push_back(-1);
+        tune_next = tune_cfg.size() > 1 ? 0 : -1;
+        if (tune_next < 0) tune_cfg.clear();
+        tune_ms.clear();
         return SIM_OK;
     }
 
@@ -1137,7 +1187,7 @@ private:
     }
     void launch_grad(int par)
     {
-        k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
+        launch_grad_kernel(par);
         if (D.segmented) k_gather<R><<<nvb, VB, 0, s>>>(D, par);
     }
     void launch_iteration(int par)
@@ -1146,10 +1196,21 @@ private:
         launch_grad(par);
         k_dots<R><<<nvb, VB, 0, s>>>(D, par);
         k_dir<R><<<nvb, VB, 0, s>>>(D, par);
-        k_pHp<R><<<ntb + npb, EB, 0, s>>>(D, ntb);
+        launch_pHp_kernel();
         k_update<R><<<nvb, VB, 0, s>>>(D, par);
     }
     void launch_finish() { k_finish<R><<<nvb, VB, 0, s>>>(D); }
+    // the element kernels: the FP32 corotated densities run their own instantiations
+    void launch_grad_kernel(int par)
+    {
+        if (corot) k_grad<R, true><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
+        else k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
+    }
+    void launch_pHp_kernel()
+    {
+        if (corot) k_pHp<R, true><<<ntb + npb, EB, 0, s>>>(D, ntb);
+        else k_pHp<R><<<ntb + npb, EB, 0, s>>>(D, ntb);
+    }
     cudaError_t launch_persistent(int do_predict, int k0, int n_iters, int do_finish, unsigned long long *stamps = nullptr,
                                   int *kinds = nullptr, int max_stamps = 0, unsigned long long *arrive = nullptr,
                                   unsigned long long *depart = nullptr, int *bar_kind = nullptr, int max_bar = 0)
@@ -1167,8 +1228,10 @@ private:
         A.part = ppart;
         A.stamps = stamps; A.stamp_kind = kinds; A.max_stamps = max_stamps;
         A.arrive = arrive; A.depart = depart; A.bar_kind = bar_kind; A.max_bar = max_bar;
-        void *args[] = {(void *)&D, (void *)&B, (void *)&A};
-        return cudaLaunchCooperativeKernel((const void *)k_persistent<R>, dim3(pgrid), dim3(PB), args, 0, s);
+        if constexpr (sizeof(R) == 4) {
+            if (corot) return persist_launch_corot(D, B, A, pgrid, s);
+        }
+        return persist_launch_shape<R>(shape, D, B, A, pgrid, s);
     }
     sim_status launch_step()
     {

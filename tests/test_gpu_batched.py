@@ -78,9 +78,11 @@ def batched_lockstep(B, O, sim, sc, iters, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batched_lockstep_per_scene(B, O, prec):
+@pytest.mark.parametrize("shape", [0, 1])
+def test_batched_lockstep_per_scene(B, O, prec, shape):
+    """Per-scene lock-step in the default block shape (256 x 2) and in 512 x 1."""
     sc = small_batch()
-    sim = B.Sim(sc, precision=prec)
+    sim = B.Sim(sc, precision=prec, block_shape=shape)
     sim.step(2)     # the scenes reach the plane: per-scene alpha caps differ
     worst = batched_lockstep(B, O, sim, sc, sc.iters, prec)
     for k, v in worst.items():

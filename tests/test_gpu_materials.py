@@ -1,8 +1,9 @@
-"""GPU parity of the other energy densities (Sec. 3.1 invariants; sim_material.model): stable Neo-Hookean in both
-forms, fixed corotated and as-rigid-as-possible in the FP64 form, against the oracle of the same model.  The
-library forms the I1 terms from a Newton polar iteration and the axial form of d2 tr(S); the oracle from the
-twist modes of an SVD, so the two derivations check each other.  Evaluation at a rotated, sheared and noisy state
-with contacts, then lock-step iterations of a contact step, at the single-scene tolerances."""
+"""GPU parity of the other energy densities (Sec. 3.1 invariants; sim_material.model): stable Neo-Hookean, fixed
+corotated and as-rigid-as-possible, each in both forms, against the oracle of the same model.  The library forms
+the I1 terms from a Newton polar iteration (FP64) or a Newton square root of C = F^T F from the metric change
+(FP32) and the axial form of d2 tr(S); the oracle from the twist modes of an SVD, so the derivations check each
+other.  Evaluation at a rotated, sheared and noisy state with contacts, then lock-step iterations of a contact
+step, at the single-scene tolerances."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ from paper_2405_08001_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-10, 1: 1e-5}
-CASES = [(1, 0), (1, 1), (2, 0), (3, 0)]   # (model, precision): SNH both forms, FCR and ARAP in FP64
+CASES = [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)]   # (model, precision): SNH, FCR, ARAP, both forms
 
 
 @pytest.fixture(scope="module")
@@ -103,11 +104,8 @@ def test_lockstep_contact_step(B, O, model, prec):
 
 
 def test_unsupported_combinations_are_rejected(B):
+    """An unknown density is refused; the adjoint (sim_eval_hvp, sim_adjoint_step) supports Neo-Hookean only."""
     sc = S.two_blocks(0)
-    for model in (2, 3):
-        with pytest.raises(B.SimError) as ei:
-            B.Sim(sc, precision=1, model=model)
-        assert ei.value.status == B.SIM_ERR_INVALID_ARG
     with pytest.raises(B.SimError) as ei:
         B.Sim(sc, precision=0, model=4)
     assert ei.value.status == B.SIM_ERR_INVALID_ARG
@@ -115,4 +113,32 @@ def test_unsupported_combinations_are_rejected(B):
     with pytest.raises(B.SimError) as ei:
         B.sim_eval_hvp(sim.h, sc.x0, np.ones_like(sc.x0))
     assert ei.value.status == B.SIM_ERR_INVALID_ARG
+    sim.close()
+
+
+@pytest.mark.parametrize("model", [2, 3])
+def test_corotated_fp32_at_large_twist(B, O, model):
+    """FCR and ARAP in the FP32 form on a strongly twisted bar (cap layers turned by +-60 degrees relative to the
+    rest, large shear): gradient, diagonal and p^T H p against the oracle, entry by entry."""
+    sc = S.twisted_bar(nx=4, ny=4, nz=12)
+    o = O.Oracle.from_scene(sc, model=model)
+    z = sc.rest_x[:, 2] / sc.rest_x[:, 2].max()
+    th = (2.0 * z - 1.0) * np.pi / 3.0
+    c = np.array([0.05, 0.05, 0.0])
+    d = sc.rest_x - c
+    x = np.stack([d[:, 0] * np.cos(th) - d[:, 1] * np.sin(th), d[:, 0] * np.sin(th) + d[:, 1] * np.cos(th),
+                  d[:, 2]], axis=1) + c
+    x += 1e-5 * np.random.default_rng(9).normal(size=x.shape)
+    xt = x + 1e-4 * np.random.default_rng(10).normal(size=x.shape)
+    sim = B.Sim(sc, precision=1, model=model)
+    g, dg = B.sim_eval_gradient(sim.h, x, xt)
+    go, do, _ = o.grad_diag(x, xt)
+    assert rel(g, go) < TOL[1] and rel(dg, do) < TOL[1], (rel(g, go), rel(dg, do))
+    for k, v in grad_errors(o, x, xt, g, go, dg, do).items():
+        assert v < TOL[1], (k, v)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        p = rng.normal(size=x.shape)
+        ref = o.pHp(x, p)
+        assert abs(B.sim_eval_pHp(sim.h, x, p) - ref) / abs(ref) < TOL[1]
     sim.close()
