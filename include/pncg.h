@@ -48,7 +48,7 @@ typedef enum {
 enum { SIM_FP64 = 0, SIM_FP32_MIXED = 1 };                 /* sim_options.precision */
 enum { SIM_BETA_PR_PLUS = 0, SIM_BETA_DK = 1 };            /* sim_options.beta */
 enum { SIM_PNORM_VERTEX2 = 0, SIM_PNORM_COMPONENT_INF = 1 }; /* sim_options.pnorm */
-enum { SIM_SCATTER_ATOMIC = 0, SIM_SCATTER_SEGMENTED = 1, SIM_SCATTER_BLOCK = 2 }; /* sim_options.scatter */
+enum { SIM_SCATTER_ATOMIC = 0, SIM_SCATTER_SEGMENTED = 1, SIM_SCATTER_BLOCK = 2, SIM_SCATTER_COLOR = 3 }; /* sim_options.scatter */
 
 /* Tetrahedral mesh and initial state (Sec. 3: x holds all vertex positions of the tet meshes). */
 typedef struct {
@@ -103,8 +103,11 @@ typedef struct {
     int32_t scatter;      /* gradient / diagonal scatter of the tets: SIM_SCATTER_ATOMIC (default: one global
                              atomic add per tet corner), SIM_SCATTER_BLOCK (each block of 256 consecutive tets
                              sums its contributions per distinct vertex in shared memory and adds them to the
-                             global accumulators once) or SIM_SCATTER_SEGMENTED (per-vertex gather over a
-                             vertex-to-(tet, corner) CSR list, deterministic) */
+                             global accumulators once), SIM_SCATTER_SEGMENTED (per-vertex gather over a
+                             vertex-to-(tet, corner) CSR list, deterministic) or SIM_SCATTER_COLOR (the tets
+                             greedily coloured so that no two of a colour share a vertex, one kernel per colour
+                             adding without atomics; deterministic; one kernel per phase only: in the persistent
+                             form every colour would be a grid barrier) */
     double excl_factor;   /* rest-pose exclusion radius in units of dhat (Sec. 5.1: 1.5; default 1.5; 0 = off) */
     void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = a stream owned by the library */
     int32_t use_graph;    /* 1 (default) = each time step is replayed from a captured CUDA graph */
@@ -123,7 +126,15 @@ typedef struct {
                              along p_o (p with every other object's entries zero) by alpha_o = min(dhat / (2 max_o
                              |p_v|), -g^T p_o / p_o^T H p_o); a pair between objects a and b adds to p_a^T H p_a
                              and to p_b^T H p_b, each with the other object's entries of p zero.  Needs the
-                             persistent form, like batched scenes. */
+                             persistent form, like batched scenes.
+                             2 = as 1, and every object is further divided into its collision and non-collision
+                             parts at the start of each time step (Sec. 5.2, the long-noodles example): the vertices
+                             of the pairs with d < dhat at x_0 (after the prediction and the kinematic targets) and
+                             those within dhat of the plane form the object's collision part, the rest its
+                             non-collision part; the parts stay fixed for the time step and iterate as the groups
+                             above (a tet or pair spanning groups adds to each group's p^T H p with the other groups'
+                             entries of p zero).  Group g = 2 object + (1 for the collision part); a group without
+                             vertices takes no step.  Works without scene_of_vert (one object, two groups). */
     int32_t block_shape;  /* block shape of the persistent form: 0 (default) = 256 threads x 2 blocks per SM,
                              1 = 512 x 1, 2 = 256 x 3, 3 = 256 x 1 (the compiler fits the registers per thread to
                              the shape: 128, 128, 85, 255); -1 = autotuned: from the second time step on, each shape
@@ -149,6 +160,8 @@ typedef struct {
                               distance fell below 1e-3 dhat, where the barrier terms are evaluated in double */
     int32_t block_threads; /* persistent form: threads per block and blocks per SM of the shape in use (0 in the */
     int32_t blocks_per_sm; /*   per-phase form) */
+    int32_t n_colors;      /* scatter SIM_SCATTER_COLOR: colours of the tet colouring (gradient kernels per
+                              iteration); 0 with the other scatters */
 } sim_stats;
 
 /* Scalars of the most recent iteration (Algorithm 1). */
@@ -369,6 +382,13 @@ sim_status sim_adjoint_step(sim_handle h, const double *x1, const double *ax1, c
  * the sim_iter_scalars of sim_get_iterate).  Synchronises.
  */
 sim_status sim_get_scene_scalars(sim_handle h, double *out, int32_t max_scenes, int32_t *n_scenes);
+
+/*
+ * The group of every vertex in the current time step: with split_objects = 2 the part label 2 object + (1 when
+ * the vertex is in its object's collision part; set by the step's first iteration), otherwise scene_of_vert (0
+ * without it).  The rows of sim_get_scene_scalars follow these labels.  group: host [n_verts].  Synchronises.
+ */
+sim_status sim_get_groups(sim_handle h, int32_t *group);
 
 #ifdef __cplusplus
 }

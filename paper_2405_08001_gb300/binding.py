@@ -20,7 +20,7 @@ SIM_FP64, SIM_FP32_MIXED = 0, 1
 SIM_BETA_PR_PLUS, SIM_BETA_DK = 0, 1
 SIM_MAT_NH, SIM_MAT_SNH, SIM_MAT_FCR, SIM_MAT_ARAP = 0, 1, 2, 3
 SIM_PNORM_VERTEX2, SIM_PNORM_COMPONENT_INF = 0, 1
-SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED, SIM_SCATTER_BLOCK = 0, 1, 2
+SIM_SCATTER_ATOMIC, SIM_SCATTER_SEGMENTED, SIM_SCATTER_BLOCK, SIM_SCATTER_COLOR = 0, 1, 2, 3
 TRACE_COLUMNS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "n_active", "capped")
 
 
@@ -48,7 +48,8 @@ class sim_stats(C.Structure):
                 ("n_active", C.c_int32), ("n_rebuilds", C.c_int32), ("n_capped", C.c_int32),
                 ("n_surface_tris", C.c_int32), ("n_surface_edges", C.c_int32), ("n_surface_verts", C.c_int32),
                 ("dE0", C.c_double), ("dE_last", C.c_double), ("launch_form", C.c_int32), ("n_scenes", C.c_int32),
-                ("n_near_fp64", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("n_near_fp64", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("n_colors", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,6 +72,9 @@ class SimError(RuntimeError):
 
 
 _lib = None
+
+
+ABI_VERSION = 4
 
 
 def load():
@@ -106,6 +110,7 @@ def load():
         "sim_profile_step": (C.c_int, [P, P, P, P, I32]),
         "sim_profile_barriers": (C.c_int, [P, P, P, P, P, I32, P, P]),
         "sim_get_scene_scalars": (C.c_int, [P, P, I32, P]),
+        "sim_get_groups": (C.c_int, [P, P]),
         "sim_eval_hvp": (C.c_int, [P, P, P, P]),
         "sim_adjoint_step": (C.c_int, [P, P, P, P, P, P, P, D, I32, P, P]),
         "sim_kernel_count": (I32, []),
@@ -121,6 +126,8 @@ def load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    if lib.sim_abi_version() != ABI_VERSION:   # the structures below describe this version's layouts
+        raise ImportError(f"{LIB_PATH} has ABI version {lib.sim_abi_version()}, this binding {ABI_VERSION}: rebuild it")
     _lib = lib
     return lib
 
@@ -379,6 +386,14 @@ def sim_adjoint_step(h, x1, ax1, av1, dE=None, tol=1e-10, max_iters=2000, ax0=No
 
 SCENE_SCALAR_COLS = ("beta", "gp", "pHp", "pmax", "alpha", "dE", "dE0", "converged", "iters_done", "restarted",
                      "capped")
+
+
+def sim_get_groups(h):
+    """The group label of every vertex in the current time step (int32 [n_verts])."""
+    nv = sim_get_sizes(h)["n_verts"]
+    out = np.zeros(nv, np.int32)
+    _check(load().sim_get_groups(h, out.ctypes.data), h)
+    return out
 
 
 def sim_get_scene_scalars(h, max_scenes=1024):

@@ -5,9 +5,14 @@
 // of one scene: the candidate pass also pairs primitives of two objects, and such a pair's p^T H p term is split
 // between the two objects (each with the other's entries of p zero).
 //
-// Per-scene sums: the lanes of a warp take consecutive vertices (tets), so their scene ids are non-decreasing; a
-// segmented warp scan adds up each run of equal ids and the run's last lane adds it to the scene's accumulator
-// with a double atomic.  Accumulators are used round robin over three buffers: reduction r accumulates into buffer
+// With parts (split_objects = 2) every object is divided into its collision and non-collision parts for the time
+// step: group 2 o + 1 holds object o's vertices in contact at x_0 (plane: marked by the prediction; pairs: marked
+// from the active set of iteration 0, before its beta phase), group 2 o the rest.  A tet or pair whose vertices lie
+// in several groups adds to each of them with the other groups' entries of p zero.
+//
+// Per-scene sums: the lanes of a warp take consecutive vertices (tets), so their scene ids are non-decreasing (with
+// parts, runs of equal ids); a segmented warp scan adds up each run of equal ids and the run's last lane adds it to
+// the scene's accumulator with a double atomic.  Accumulators are used round robin over three buffers: reduction r accumulates into buffer
 // r % 3 and zeroes buffer (r + 1) % 3 for the next one, which every block last read before the barrier of
 // reduction r - 1.  After the barrier every block computes all scenes' scalars itself (identical values) into
 // shared memory; block 0 also writes them to the per-scene state.
@@ -24,19 +29,48 @@ template <typename R> __device__ inline double max_value(unsigned long long b);
 template <> __device__ inline double max_value<float>(unsigned long long b) { return (double)__uint_as_float((unsigned int)b); }
 template <> __device__ inline double max_value<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
 
-// Segmented sum over the warp's lanes (equal keys contiguous; key < 0 = no item): the last lane of each run adds
-// the run's N sums to acc[key * 8 + q0 + q].
+// The group of vertex i: its scene (object), or with parts its object's collision or non-collision part.
+template <typename R> __device__ inline int group_of(const Dev<R> &D, int i)
+{
+    return D.cmark ? 2 * D.vscene[i] + D.cmark[i] : D.vscene[i];
+}
+
+// The distinct groups of a tet's or pair's four vertices (k[0..3]): returns their number n and u[0..n).
+__device__ inline int distinct4(const int k[4], int u[4])
+{
+    int n = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        bool seen = false;
+#pragma unroll
+        for (int r = 0; r < q; ++r) seen |= k[r] == k[q];
+        if (!seen) u[n++] = k[q];
+    }
+    return n;
+}
+
+// First lane of the run of equal keys that lane `lane` belongs to (runs need not be sorted: with parts a group's
+// vertices can come back after another group's).
+__device__ inline int run_start(int key, int lane)
+{
+    const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned int heads = __ballot_sync(0xffffffffu, lane == 0 || kp != key);
+    return 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+}
+
+// Segmented sum over the warp's lanes (key < 0 = no item): the last lane of each run of equal keys adds the run's
+// N sums to acc[key * 8 + q0 + q].
 template <typename R, int N>
 __device__ inline void seg_warp_sum(Acc<R> (&a)[N], int key, double *acc, int q0)
 {
     const int lane = threadIdx.x & 31;
+    const int start = run_start(key, lane);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int ku = __shfl_up_sync(0xffffffffu, key, o);
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             const Acc<R> u = a[q].shfl_up(o);
-            if (lane >= o && ku == key) a[q].add(u);
+            if (lane - o >= start) a[q].add(u);
         }
     }
     const int kn = __shfl_down_sync(0xffffffffu, key, 1);
@@ -51,11 +85,11 @@ template <typename R>
 __device__ inline void seg_warp_max(R m, int key, unsigned long long *mx)
 {
     const int lane = threadIdx.x & 31;
+    const int start = run_start(key, lane);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int ku = __shfl_up_sync(0xffffffffu, key, o);
         const R mu = __shfl_up_sync(0xffffffffu, m, o);
-        if (lane >= o && ku == key) m = fmax(m, mu);
+        if (lane - o >= start) m = fmax(m, mu);
     }
     const int kn = __shfl_down_sync(0xffffffffu, key, 1);
     if (key >= 0 && (lane == 31 || kn != key)) atomicMax(mx + key, max_bits<R>(m));
@@ -99,6 +133,17 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
     double *sbeta = reinterpret_cast<double *>(sbuf);
     double *salpha = sbeta + MAX_SCENES;
 
+    // ------------------------------------------------------------ parts: the collision parts of the time step
+    if (D.cmark && k == 0) {
+        br.phase = 8;   // K_DOTS
+        const int na0 = min((volatile const int &)c->n_active, D.cand_cap);
+        for (int kk = tid; kk < na0; kk += nthr) {
+            const int4 v = __ldcg(&D.act[kk].v);
+            D.cmark[v.x] = 1; D.cmark[v.y] = 1; D.cmark[v.z] = 1; D.cmark[v.w] = 1;
+        }
+        grid_barrier(br, c);
+    }
+
     // ------------------------------------------------------------ beta (per scene) and P g
     br.phase = 8;   // K_DOTS
     {
@@ -109,7 +154,7 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
             Acc<R> a5[5];
             int key = -1;
             if (i < D.nv) {
-                key = D.vscene[i];
+                key = group_of(D, i);
                 const R4 G = ldcg4(D.g[par] + i), Dg = ldcg4(D.dg[par] + i), G0 = ldcg4(D.g[par ^ 1] + i);
                 const R4 P0 = ldcg4(D.p + i);
                 R4 PG = mk4<R>(R(0), R(0), R(0), R(0));
@@ -163,11 +208,12 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
         seg_zero_next(D.sacc, D.smax, ns, sred, tid, nthr);
         for (int base = tid - lane; base < D.nv; base += nthr) {
             const int i = base + lane;
-            Acc<R> a2[2];
+            Acc<R> a2[3];   // g^T p, p^T M p, vertices (a group without vertices takes no step)
             R pmv = R(0);
             int key = -1;
             if (i < D.nv) {
-                key = D.vscene[i];
+                key = group_of(D, i);
+                a2[2].add(R(1));
                 const double bd = sbeta[key];
                 const R4 Dg = ldcg4(D.dg[par] + i);
                 R4 Pn = mk4<R>(R(0), R(0), R(0), R(0));
@@ -186,7 +232,7 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
                 }
                 D.pnext[i] = Pn;
             }
-            seg_warp_sum<R, 2>(a2, key, acc, 0);
+            seg_warp_sum<R, 3>(a2, key, acc, 0);
             seg_warp_max<R>(pmv, key, mx);
         }
         for (int base = tid - lane; base < D.nt; base += nthr) {
@@ -195,14 +241,29 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
             int key = -1;
             if (e < D.nt) {
                 const int4 tv = D.tet[e];
-                key = D.vscene[tv.x];
-                const double bd = sbeta[key];
-                const R b = R(bd);
-                const bool nzb = bd != 0.0;
-                a1[0].add(tet_pHp_vec<R, CO>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
-                                         dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
+                const int vv[4] = {tv.x, tv.y, tv.z, tv.w};
+                int ks[4];
+                R4 pv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {   // each vertex takes the direction of its own group
+                    ks[q] = group_of(D, vv[q]);
+                    const double bd = sbeta[ks[q]];
+                    pv[q] = dir_of<R>(D, vv[q], R(bd), bd != 0.0);
+                }
+                if (ks[1] == ks[0] && ks[2] == ks[0] && ks[3] == ks[0]) {
+                    key = ks[0];
+                    a1[0].add(tet_pHp_vec<R, CO>(D, e, tv, pv[0], pv[1], pv[2], pv[3]));
+                } else {   // a tet on the border of two parts: one term per group, the others' p zero
+                    const R4 z = mk4<R>(R(0), R(0), R(0), R(0));
+                    int u[4];
+                    const int nu = distinct4(ks, u);
+                    for (int j = 0; j < nu; ++j)
+                        atomicAdd(acc + (size_t)u[j] * 8 + 3,
+                                  (double)tet_pHp_vec<R, CO>(D, e, tv, ks[0] == u[j] ? pv[0] : z, ks[1] == u[j] ? pv[1] : z,
+                                                             ks[2] == u[j] ? pv[2] : z, ks[3] == u[j] ? pv[3] : z));
+                }
             }
-            seg_warp_sum<R, 1>(a1, key, acc, 2);
+            seg_warp_sum<R, 1>(a1, key, acc, 4);
         }
         for (int kk = tid; kk < na; kk += nthr) {   // active pairs come in no order: one atomic each
             Active<R> ap;
@@ -211,26 +272,23 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
             int ks[4];
             R4 pv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {   // each vertex takes the direction of its own scene (object)
-                ks[q] = D.vscene[vv[q]];
+            for (int q = 0; q < 4; ++q) {   // each vertex takes the direction of its own group
+                ks[q] = group_of(D, vv[q]);
                 const double bd = sbeta[ks[q]];
                 pv[q] = dir_of<R>(D, vv[q], R(bd), bd != 0.0);
             }
-            // both primitives of a pair lie in one object each: v.x in the first (the point, or edge a), v.w in the
-            // second.  A pair between two objects (split objects only) adds to each object's p^T H p with the
-            // other object's entries of p zero.
-            const int ka = ks[0], kb = ks[3];
-            if (ka == kb) {
-                atomicAdd(acc + (size_t)ka * 8 + 2, pair_pHp_vec<R>(ap, pv[0], pv[1], pv[2], pv[3]));
+            // a pair whose vertices lie in several groups (objects, or parts) adds to each group's p^T H p with
+            // the other groups' entries of p zero
+            int u[4];
+            const int nu = distinct4(ks, u);
+            if (nu == 1) {
+                atomicAdd(acc + (size_t)u[0] * 8 + 3, pair_pHp_vec<R>(ap, pv[0], pv[1], pv[2], pv[3]));
             } else {
                 const R4 z = mk4<R>(R(0), R(0), R(0), R(0));
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int key = side ? kb : ka;
-                    atomicAdd(acc + (size_t)key * 8 + 2,
-                              pair_pHp_vec<R>(ap, ks[0] == key ? pv[0] : z, ks[1] == key ? pv[1] : z,
-                                              ks[2] == key ? pv[2] : z, ks[3] == key ? pv[3] : z));
-                }
+                for (int j = 0; j < nu; ++j)
+                    atomicAdd(acc + (size_t)u[j] * 8 + 3,
+                              pair_pHp_vec<R>(ap, ks[0] == u[j] ? pv[0] : z, ks[1] == u[j] ? pv[1] : z,
+                                              ks[2] == u[j] ? pv[2] : z, ks[3] == u[j] ? pv[3] : z));
             }
         }
         grid_barrier(br, c);
@@ -240,13 +298,15 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
         int ncap = 0;
         for (int s = threadIdx.x; s < ns; s += blockDim.x) {
             const double gp = __ldcg(acc + (size_t)s * 8), pMp = __ldcg(acc + (size_t)s * 8 + 1);
-            const double pHp = __ldcg(acc + (size_t)s * 8 + 2) + pMp;
+            const bool empty = __ldcg(acc + (size_t)s * 8 + 2) == 0.0;
+            const double pHp = __ldcg(acc + (size_t)s * 8 + 4) + __ldcg(acc + (size_t)s * 8 + 3) + pMp;
             const double pmax = max_value<R>(__ldcg(mx + s));
             const double au = pmax > 0.0 ? D.dhat / (2.0 * pmax) : 0.0;
             const double ab = -gp / pHp;
             double a;
             int capped;
-            if (!(pHp > 0.0) || !isfinite(ab)) { a = au; capped = 1; }
+            if (empty) { a = 0.0; capped = 0; }
+            else if (!(pHp > 0.0) || !isfinite(ab)) { a = au; capped = 1; }
             else if (ab < au) { a = ab; capped = 0; }
             else { a = au; capped = 1; }
             const double dE = -a * gp - 0.5 * a * a * pHp;
@@ -255,8 +315,8 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
             const int cprev = k > 0 ? __ldcg(&D.seg[s].converged[rp]) : 0;
             double e0 = k > 0 ? __ldcg(&D.seg[s].dE0[rp]) : 0.0;
             if (bad || cprev) a = 0.0;
-            int cv = cprev;
-            if (!cprev && !bad) {
+            int cv = cprev | (empty ? 1 : 0);
+            if (!cv && !bad) {
                 if (k == 0) e0 = dE;
                 if (D.eps > 0.0 && dE < D.eps * e0) cv = 1;
             }
@@ -286,12 +346,18 @@ __device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh,
     for (int i = tid; i < D.nv; i += nthr) {
         double4_32a X = ldcg4(D.x + i);
         const R4 P = ldcg4(D.pnext + i);
-        const double a = salpha[D.vscene[i]];
-        X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
-        put_x<R>(D, i, X);
+        const double a = salpha[group_of(D, i)];
+        if constexpr (sizeof(R) == 4) {
+            const ffl as = ff_split(a);
+            const float4 xh = update_vertex<R>(D, i, X, P, a, as.h, as.l, X, par ^ 1);
+            const float4 b = ldcg4(D.xbh + i);
+            const float dx = xh.x - b.x, dy = xh.y - b.y, dz = xh.z - b.z;
+            md = fmax(md, dx * dx + dy * dy + dz * dz);
+        } else {
+            update_vertex<R>(D, i, X, P, a, 0.0f, 0.0f, ldcg4(D.xtil + i), par ^ 1);
+            md = fmax(md, (R)disp2<R>(D, i, X));
+        }
         D.p[i] = P;
-        init_vertex<R>(D, i, X, ldcg4(D.xtil + i), par ^ 1);
-        md = fmax(md, (R)disp2<R>(D, i, X));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) c->n_active = 0;
     const R m = grid_max<R, PB>(md, rb.max_region<PT, R>(), sh, br, c);

@@ -28,7 +28,7 @@ const char *const kProfiledNames[N_PROFILED] = {"k_predict", "bp_boxes", "bp_cou
 
 extern "C" {
 
-int32_t sim_abi_version(void) { return 3; }
+int32_t sim_abi_version(void) { return 4; }
 
 const char *sim_status_string(sim_status s)
 {
@@ -227,6 +227,12 @@ sim_status sim_adjoint_step(sim_handle h, const double *x1, const double *ax1, c
 {
     if (guard(h)) return SIM_ERR_INVALID_ARG;
     return h->impl->adjoint_step(x1, ax1, av1, ax0, av0, dE, tol, max_iters, iters, residual);
+}
+
+sim_status sim_get_groups(sim_handle h, int32_t *group)
+{
+    if (guard(h) || !group) return SIM_ERR_INVALID_ARG;
+    return h->impl->get_groups(group);
 }
 
 sim_status sim_get_scene_scalars(sim_handle h, double *out, int32_t max_scenes, int32_t *n_scenes)

@@ -34,6 +34,18 @@ __device__ inline ffl ff_sub(float ah, float al, float bh, float bl)
 
 __device__ inline float ff_val(ffl a) { return __fadd_rn(a.h, a.l); }
 
+// (h + l) += (ah + al) p: the head product exact (FMA TwoProd), its tail and al p joined to the error of the TwoSum
+// of the heads, then renormalised (about 2^-46 relative accuracy)
+__device__ inline void ff_axpy(float &h, float &l, float ah, float al, float p)
+{
+    const float q = __fmul_rn(ah, p);
+    float e = __fmaf_rn(al, p, __fmaf_rn(ah, p, -q));
+    const float s = __fadd_rn(h, q), bb = __fsub_rn(s, h);
+    e = __fadd_rn(e, __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(q, bb)), l));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
 // Compensated accumulator: s + c carries sum_k sign_k x_k y_k for float-float x, y.
 struct ffacc {
     float s = 0.0f, c = 0.0f;

@@ -23,6 +23,7 @@ template <typename R> struct Dev {
     double4_32a *x, *xt, *xtil, *v, *xb;   // xtil.w = mass (free vertex) or -1 (kinematic)
     float4 *xh, *xl;                   // FP32 form: float-float copy of x (hi, lo); null in the FP64 form
     float4 *xbh;                       // FP32 form: xh at the last candidate build (displacement check)
+    float4 *xth, *xtl;                 // FP32 form: float-float copy of xtil (hi with w = xtil.w, lo)
     const float *G0;                   // FP32 form: [14][nt] rest metric Dm^T Dm of each tet as float-float (six
                                        // heads, six tails), then det Dm as float-float
                                        // (hi of entries 00 01 02 11 12 22, then lo)
@@ -60,10 +61,14 @@ template <typename R> struct Dev {
     const int *cv_off, *cv;
     const ushort4 *tloc;
     int scatter_block;
+    // colouring: tets sorted by colour (no two tets of a colour share a vertex); one kernel per colour
+    const int *color_tets;
+    int colored;
     // batching: nseg independent scenes (1 = none), the scene of each vertex, per-scene state and the per-scene
     // reduction accumulators ([3][nseg][8] sums, [3][nseg] maxima as bits; used round robin)
     int nseg;
     const int *vscene;
+    int *cmark;                        // parts (split_objects = 2): 1 for the vertices of the step's collision parts
     SegCtl *seg;
     double *sacc;
     unsigned long long *smax;
@@ -85,6 +90,16 @@ template <> __device__ inline void atomic_add4<double>(double4_32a *p, double a,
 }
 
 __device__ inline void flag_error(Ctrl *c, uint32_t bits) { atomicOr(&c->err, bits); }
+
+// Writes the FP32 form's float-float copy of x~ (vertex i; its w carries the mass slot of xtil.w).
+template <typename R> __device__ inline void put_xt(const Dev<R> &D, int i, const double4_32a &XT)
+{
+    if constexpr (sizeof(R) == 4) {
+        const ffl a = ff_split(XT.x), b = ff_split(XT.y), c = ff_split(XT.z);
+        D.xth[i] = make_float4(a.h, b.h, c.h, (float)XT.w);
+        D.xtl[i] = make_float4(a.l, b.l, c.l, 0.0f);
+    }
+}
 
 // Writes vertex i's position (and, in the FP32 form, its float-float copy, whose head it returns).
 template <typename R> __device__ inline float4 put_x(const Dev<R> &D, int i, const double4_32a &X)
@@ -167,6 +182,77 @@ __device__ inline void init_vertex(const Dev<R> &D, int i, const double4_32a &X,
     D.dg[par][i] = mk4<R>(R(dx), R(dy), R(dz), R(m));
 }
 
+// init_vertex of the FP32 form after a position update, from the float-float copies of x (H + L, just written)
+// and of x~: no FP64 arithmetic, except for a vertex whose float distance to the plane lies within dhat (plus that
+// estimate's error bound), whose plane barrier is evaluated from the double position X as in init_vertex.
+__device__ inline void init_vertex_ff(const Dev<float> &D, int i, const float4 &H, const float4 &L,
+                                      const double4_32a &X, int par)
+{
+    const float4 TH = ldcg4(D.xth + i), TL = ldcg4(D.xtl + i);
+    const float m = TH.w, mm = m > 0.0f ? m : 0.0f;
+    float gx = mm * ff_val(ff_sub(H.x, L.x, TH.x, TL.x)), gy = mm * ff_val(ff_sub(H.y, L.y, TH.y, TL.y)),
+          gz = mm * ff_val(ff_sub(H.z, L.z, TH.z, TL.z));
+    float dx = mm, dy = mm, dz = mm, curv = 0.0f;
+    if (D.has_plane) {
+        // n . x - o in float from the heads: the dropped tails, the rounded n and o and the three roundings of the
+        // FMAs are each at most 2^-24 of a value no larger than |x|_1 + |o| (n normalised), about 4e-7 of it in
+        // all; the bound below leaves more than a factor of two
+        const float n0 = (float)D.pn[0], n1 = (float)D.pn[1], n2 = (float)D.pn[2], o = (float)D.po;
+        const float df = __fmaf_rn(n0, H.x, __fmaf_rn(n1, H.y, __fmaf_rn(n2, H.z, -o)));
+        const float bound = 1e-6f * (fabsf(H.x) + fabsf(H.y) + fabsf(H.z) + fabsf(o));
+        if (df < (float)D.dhat + bound) {
+            const double d = D.pn[0] * X.x + D.pn[1] * X.y + D.pn[2] * X.z - D.po;
+            if (d < D.dhat) {
+                if (!(d > 0.0)) {
+                    flag_error(D.ctrl, ERR_PENETRATION);
+                } else {
+                    float k1, k2;
+                    if (d < 1e-3 * D.dhat) {
+                        double b1, b2;
+                        barrier_d12<double>(d, D.dhat, b1, b2);
+                        k1 = (float)(D.kappa * b1); k2 = (float)(D.kappa * b2);
+                    } else {
+                        float b1, b2;
+                        barrier_d12r<float>((float)d, (float)(d - D.dhat), (float)D.dhat, b1, b2);
+                        k1 = (float)D.kappa * b1; k2 = (float)D.kappa * b2;
+                    }
+                    gx += k1 * n0; gy += k1 * n1; gz += k1 * n2;
+                    dx += k2 * n0 * n0; dy += k2 * n1 * n1; dz += k2 * n2 * n2;
+                    curv = k2;
+                }
+            }
+        }
+    }
+    D.g[par][i] = make_float4(gx, gy, gz, curv);
+    D.dg[par][i] = make_float4(dx, dy, dz, m);
+}
+
+// x += a p for vertex i (X in and out; a split as ah + al for the FP32 form) and the initialisation of the
+// accumulators of parity par at the new x.  The FP32 form advances its float-float copy by float-float arithmetic (ff_axpy) beside
+// the double state, so that the double update itself is its only FP64 work (FP64 issue is scarce on this GPU), and
+// returns the new float head (the displacement check reads it).
+template <typename R>
+__device__ inline float4 update_vertex(const Dev<R> &D, int i, double4_32a &X, const typename V4<R>::T &P, double a,
+                                       float ah, float al, const double4_32a &XT, int par)
+{
+    X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
+    if constexpr (sizeof(R) == 4) {
+        D.x[i] = X;
+        float4 H = ldcg4(D.xh + i), L = ldcg4(D.xl + i);
+        ff_axpy(H.x, L.x, ah, al, P.x);
+        ff_axpy(H.y, L.y, ah, al, P.y);
+        ff_axpy(H.z, L.z, ah, al, P.z);
+        D.xh[i] = H;
+        D.xl[i] = L;
+        init_vertex_ff(D, i, H, L, X, par);
+        return H;
+    } else {
+        put_x<R>(D, i, X);
+        init_vertex<R>(D, i, X, XT, par);
+        return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+}
+
 __device__ inline double dist2(const double4_32a &a, const double4_32a &b)
 {
     double x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
@@ -222,6 +308,7 @@ __global__ void __launch_bounds__(VB) k_predict(Dev<R> D)
                               X.z + h * V.z + h2 * D.grav[2], D.mass[i]);
         }
         D.xtil[i] = XT;
+        put_xt<R>(D, i, XT);
         init_vertex<R>(D, i, X, XT, 0);
         md2 = disp2<R>(D, i, X);
     }
@@ -777,11 +864,51 @@ __device__ inline void tet_grad(const Dev<R> &D, int e, int par, const TetIn<R> 
         return;
     }
     const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+    if (D.colored) {   // no other tet of this launch's colour touches these vertices: plain read-modify-write
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            typename V4<R>::T G = D.g[par][vid[i]], Dg = D.dg[par][vid[i]];
+            G.x += gv[i][0]; G.y += gv[i][1]; G.z += gv[i][2];
+            Dg.x += dv[i][0]; Dg.y += dv[i][1]; Dg.z += dv[i][2];
+            D.g[par][vid[i]] = G;
+            D.dg[par][vid[i]] = Dg;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         atomic_add4<R>(&D.g[par][vid[i]], gv[i][0], gv[i][1], gv[i][2]);
         atomic_add4<R>(&D.dg[par][vid[i]], dv[i][0], dv[i][1], dv[i][2]);
     }
+}
+
+// Colouring scatter: the tets of one colour (positions t0 .. t0 + n of the colour order), one thread each.  Dc is
+// D with the per-tet inputs (tet, Dm, hv, escale, G0) in colour order, so that the loads of a colour stay
+// coalesced; the record of the p^T H p pass is written at the tet's own index color_tets[q].
+template <typename R, bool CO = false>
+__global__ void __launch_bounds__(EB) k_grad_color(Dev<R> D, Dev<R> Dc, int par, int t0, int n)
+{
+    const int q = t0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (q >= t0 + n) return;
+    TetIn<R> in;
+    load_tet_in<R>(Dc, q, in);
+    tet_grad<R, CO>(D, D.color_tets[q], par, in);
+}
+
+// The colour-ordered copies of the per-tet inputs (once, at setup): position q holds tet color_tets[q].
+template <typename R>
+__global__ void k_color_gather(Dev<R> D, int4 *tet, R *Dm, R *hv, R *es, float *G0)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= D.nt) return;
+    const size_t n = (size_t)D.nt;
+    const int e = D.color_tets[q];
+    tet[q] = D.tet[e];
+    for (int k = 0; k < 9; ++k) Dm[k * n + q] = D.Dm[k * n + e];
+    hv[q] = D.hv[e];
+    if (es) es[q] = D.escale[e];
+    if (G0)
+        for (int k = 0; k < 14; ++k) G0[k * n + q] = D.G0[k * n + e];
 }
 
 // The tets of chunk ch (SCATTER_CHUNK consecutive tets, one per thread of the block): gradient and diagonal,
@@ -856,6 +983,18 @@ __device__ inline ffn pair_geom_ffn(const Dev<float> &D, bool ee, const int4 &v,
 {
     if (!ee) return pt_coeffs<ffn>(rel_ffn(D, v.x, v.y), rel_ffn(D, v.z, v.y), rel_ffn(D, v.w, v.y), c, t);
     return ee_coeffs<ffn>(rel_ffn(D, v.x, v.z), rel_ffn(D, v.y, v.z), rel_ffn(D, v.w, v.z), c, t);
+}
+
+// The FP32 form's float filter of a candidate (the first test of pair_grad): whether its float distance is below
+// dhat (1 + 1e-4), i.e. whether pair_grad goes on to the float-float geometry.
+__device__ inline bool pair_passes_filter(const Dev<float> &D, int ci)
+{
+    const int4 q = ldcg4(D.cand + ci);
+    const bool ee = q.x < 0;
+    const int4 v = make_int4(ee ? -1 - q.x : q.x, q.y, q.z, q.w);
+    float c[4];
+    v3<float> t;
+    return pair_geom_ff(D, ee, v, c, t) < float(D.dhat) * 1.0001f;
 }
 
 // Barrier gradient and diagonal of one candidate (Eqs. 8-11) when d < dhat; records the pair for p^T H p.
@@ -1363,12 +1502,18 @@ __global__ void __launch_bounds__(VB) k_update(Dev<R> D, int par)
     const double a = D.ctrl->alpha;
     double md2 = 0.0;
     if (i < D.nv) {
-        double4_32a X = ldcg4(D.x + i);
         const typename V4<R>::T P = ldcg4(D.p + i);
-        X.x += a * double(P.x); X.y += a * double(P.y); X.z += a * double(P.z);
-        put_x<R>(D, i, X);
-        init_vertex<R>(D, i, X, ldcg4(D.xtil + i), par ^ 1);
-        md2 = disp2<R>(D, i, X);
+        double4_32a X = ldcg4(D.x + i);
+        if constexpr (sizeof(R) == 4) {
+            const ffl as = ff_split(a);
+            const float4 xh = update_vertex<R>(D, i, X, P, a, as.h, as.l, X, par ^ 1);
+            const float4 b = D.xbh[i];
+            const float x = xh.x - b.x, y = xh.y - b.y, z = xh.z - b.z;
+            md2 = (double)(x * x + y * y + z * z);
+        } else {
+            update_vertex<R>(D, i, X, P, a, 0.0f, 0.0f, ldcg4(D.xtil + i), par ^ 1);
+            md2 = disp2<R>(D, i, X);
+        }
     }
     double mx = block_max(md2, sh);
     double v1[1] = {mx};

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
                                  sizeof(BPQWarp) * (PB / 32));
     __shared__ __align__(16) unsigned char sbuf[SBUF];
     static_assert(SBUF >= 2 * MAX_SCENES * sizeof(double), "the batched form keeps per-scene beta and alpha here");
+    static_assert(SBUF >= (PB / 32) * 64 * sizeof(int), "the gradient pass queues candidates here, 64 per warp");
     // the block-aggregated scatter (options.scatter = block) covers one chunk of SCATTER_CHUNK tets per block: only
     // the shape with PB == SCATTER_CHUNK runs it (the host keeps that shape for it)
     Ctrl *c = D.ctrl;
@@ -460,7 +461,9 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
                                           X.z + h * V.z + h2 * D.grav[2], D.mass[i]);
                 }
                 D.xtil[i] = XT;
+                put_xt<R>(D, i, XT);
                 init_vertex<R>(D, i, X, XT, 0);
+                if (D.cmark) D.cmark[i] = D.g[0][i].w != R(0) ? 1 : 0;   // within dhat of the plane at x_0
                 md = fmax(md, (R)disp2<R>(D, i, X));
             }
         }
@@ -633,12 +636,41 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
                 if (lead) c->ticket[TK_PAIRS + ((k + 1) & 1)] = 0u;   // the next iteration's cursor
                 unsigned int *cur = &c->ticket[TK_PAIRS + (k & 1)];
                 const int nc = min(ncand, D.cand_cap), lane = threadIdx.x & 31;
-                for (;;) {
-                    int b0 = 0;
-                    if (lane == 0) b0 = (int)atomicAdd(cur, 32u);
-                    b0 = __shfl_sync(0xffffffffu, b0, 0);
-                    if (b0 >= nc) break;
-                    if (b0 + lane < nc) pair_grad<R>(D, b0 + lane, par);
+                if constexpr (sizeof(R) == 4) {
+                    // the float filter first; the candidates that pass it queue in shared memory (per warp) and
+                    // take the float-float geometry 32 at a time, so that the long path runs with full warps (the
+                    // passing ones are a fraction of each batch: a warp otherwise ran it once per batch)
+                    int *wq = reinterpret_cast<int *>(sbuf) + (threadIdx.x >> 5) * 64;
+                    int qn = 0;
+                    const unsigned int below = (1u << lane) - 1u;
+                    for (;;) {
+                        int b0 = 0;
+                        if (lane == 0) b0 = (int)atomicAdd(cur, 32u);
+                        b0 = __shfl_sync(0xffffffffu, b0, 0);
+                        if (b0 >= nc) break;
+                        const int ci = b0 + lane;
+                        const bool pass = ci < nc && pair_passes_filter(D, ci);
+                        const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+                        if (pass) wq[qn + __popc(bal & below)] = ci;
+                        qn += __popc(bal);
+                        __syncwarp();
+                        if (qn >= 32) {
+                            const int cj = wq[qn - 32 + lane];
+                            __syncwarp();
+                            qn -= 32;
+                            pair_grad<R>(D, cj, par);
+                        }
+                    }
+                    if (lane < qn) pair_grad<R>(D, wq[lane], par);
+                    __syncwarp();
+                } else {
+                    for (;;) {
+                        int b0 = 0;
+                        if (lane == 0) b0 = (int)atomicAdd(cur, 32u);
+                        b0 = __shfl_sync(0xffffffffu, b0, 0);
+                        if (b0 >= nc) break;
+                        if (b0 + lane < nc) pair_grad<R>(D, b0 + lane, par);
+                    }
                 }
             }
         }
@@ -758,10 +790,12 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
             // vertex pass above is short)
             const Share as = share_of(na);
             const int nts = ts.b1 - ts.b0, nit = nts + (as.b1 - as.b0);
+            int4 tvn = (int)threadIdx.x < nts ? D.tet[ts.b0 + threadIdx.x] : make_int4(0, 0, 0, 0);   // one tet ahead
             for (int q = threadIdx.x; q < nit; q += PB) {
                 if (q < nts) {
                     const int e = ts.b0 + q;
-                    const int4 tv = D.tet[e];
+                    const int4 tv = tvn;
+                    if (q + PB < nts) tvn = D.tet[e + PB];
                     s3[2].add(tet_pHp_vec<R, CO>(D, e, tv, dir_of<R>(D, tv.x, b, nzb), dir_of<R>(D, tv.y, b, nzb),
                                              dir_of<R>(D, tv.z, b, nzb), dir_of<R>(D, tv.w, b, nzb)));
                 } else {
@@ -780,7 +814,7 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
             if (ov < vs.b1) {
                 uX = ldcg4(D.x + ov);
                 uP = ldcg4(D.pnext + ov);
-                uXT = ldcg4(D.xtil + ov);
+                if constexpr (sizeof(R) == 8) uXT = ldcg4(D.xtil + ov);
                 uXB = disp_ref<R>(D, ov);
             }
             grid_collect<R, PB, 3, true>(part, sh, &f);
@@ -841,16 +875,18 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
         br.phase = 11;   // K_UPDATE
         {
             R md = R(0);
+            const ffl as = ff_split(alpha);
             for (int i = ov; i < vs.b1; i += PB) {
                 double4_32a X, XT;
                 R4 P;
                 typename DispRef<R>::T XB;
                 if (i == ov) { X = uX; P = uP; XT = uXT; XB = uXB; }
-                else { X = ldcg4(D.x + i); P = ldcg4(D.pnext + i); XT = ldcg4(D.xtil + i); XB = disp_ref<R>(D, i); }
-                X.x += alpha * double(P.x); X.y += alpha * double(P.y); X.z += alpha * double(P.z);
-                const float4 xh = put_x<R>(D, i, X);
+                else {
+                    X = ldcg4(D.x + i); P = ldcg4(D.pnext + i); XB = disp_ref<R>(D, i);
+                    if constexpr (sizeof(R) == 8) XT = ldcg4(D.xtil + i);
+                }
+                const float4 xh = update_vertex<R>(D, i, X, P, alpha, as.h, as.l, XT, par ^ 1);
                 D.p[i] = P;
-                init_vertex<R>(D, i, X, XT, par ^ 1);
                 if constexpr (sizeof(R) == 4) {   // the float head just written, as disp2 forms it
                     const float dx = xh.x - XB.x, dy = xh.y - XB.y, dz = xh.z - XB.z;
                     md = fmax(md, dx * dx + dy * dy + dz * dz);

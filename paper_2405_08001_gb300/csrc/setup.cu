@@ -115,8 +115,8 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         return SIM_ERR_INVALID_ARG;
     }
     if (opt.iters <= 0 || opt.beta < 0 || opt.beta > 1 || opt.pnorm < 0 || opt.pnorm > 1 || opt.precision < 0 ||
-        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 2 || opt.persistent < 0 || opt.persistent > 2 ||
-        opt.split_objects < 0 || opt.split_objects > 1 || opt.block_shape < -1 || opt.block_shape > 3) {
+        opt.precision > 1 || opt.scatter < 0 || opt.scatter > 3 || opt.persistent < 0 || opt.persistent > 2 ||
+        opt.split_objects < 0 || opt.split_objects > 2 || opt.block_shape < -1 || opt.block_shape > 3) {
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }
@@ -268,6 +268,13 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
         }
         if (m.nseg > 1) m.vscene.assign(sc, sc + nv);
     }
+    // collision / non-collision parts: two groups per object (vscene keeps the objects)
+    m.nobj = m.nseg;
+    if (opt.split_objects == 2) {
+        if (m.vscene.empty()) m.vscene.assign(nv, 0);
+        m.nseg = 2 * m.nobj;
+        if (m.nseg > MAX_SCENES) { err = "at most " + std::to_string(MAX_SCENES / 2) + " objects with parts"; return SIM_ERR_INVALID_ARG; }
+    }
     // block-scatter tables
     const int nchunk = (nt + SCATTER_CHUNK - 1) / SCATTER_CHUNK;
     m.cv_off.assign(nchunk + 1, 0);
@@ -283,6 +290,32 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
             m.tloc[q] = (unsigned short)(std::lower_bound(ids.begin(), ids.end(), m.tet[q]) - ids.begin());
         m.cv.insert(m.cv.end(), ids.begin(), ids.end());
         m.cv_off[c + 1] = (int)m.cv.size();
+    }
+    // colouring scatter: first-fit greedy colouring of the tets (the colours a vertex's tets already have are a
+    // bit mask per vertex), then the tets grouped by colour
+    m.color_off.clear();
+    m.color_tets.clear();
+    if (opt.scatter == SIM_SCATTER_COLOR) {
+        if (m.nseg > 1) { err = "the colouring scatter runs one kernel per phase: not with batched scenes"; return SIM_ERR_INVALID_ARG; }
+        std::vector<unsigned long long> used(nv, 0ull);
+        std::vector<int> col(nt);
+        int ncol = 0;
+        for (int e = 0; e < nt; ++e) {
+            const int *v = &m.tet[4 * (size_t)e];
+            const unsigned long long busy = used[v[0]] | used[v[1]] | used[v[2]] | used[v[3]];
+            if (busy == ~0ull) { err = "the colouring scatter needs more than 64 colours"; return SIM_ERR_INVALID_ARG; }
+            int c = 0;
+            while (busy >> c & 1ull) ++c;
+            col[e] = c;
+            ncol = std::max(ncol, c + 1);
+            for (int i = 0; i < 4; ++i) used[v[i]] |= 1ull << c;
+        }
+        m.color_off.assign(ncol + 1, 0);
+        for (int e = 0; e < nt; ++e) ++m.color_off[col[e] + 1];
+        for (int c = 0; c < ncol; ++c) m.color_off[c + 1] += m.color_off[c];
+        std::vector<int> pos(m.color_off.begin(), m.color_off.end() - 1);
+        m.color_tets.resize(nt);
+        for (int e = 0; e < nt; ++e) m.color_tets[pos[col[e]]++] = e;
     }
     return SIM_OK;
 }

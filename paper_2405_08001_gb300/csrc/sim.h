@@ -37,9 +37,13 @@ struct HostMesh {
     // the chunk-local index of each corner
     std::vector<int> cv_off, cv;           // [nchunk + 1], [sum of distinct counts]
     std::vector<unsigned short> tloc;      // [nt][4]
+    // colouring scatter: tets grouped by colour (first-fit greedy in tet order), colour c at [color_off[c],
+    // color_off[c + 1])
+    std::vector<int> color_off, color_tets;
     // batching: independent scenes (nseg == 1 without scene_of_vert)
     int nseg = 1;
-    std::vector<int> vscene;               // [nv] scene of each vertex (empty when nseg == 1)
+    std::vector<int> vscene;               // [nv] scene (object) of each vertex (empty when nseg == 1)
+    int nobj = 1;                          // objects (scenes); nseg = 2 nobj groups with split_objects = 2
 };
 
 
@@ -70,6 +74,7 @@ public:
     virtual sim_status get_trace(double *buf, int32_t max_iters, int32_t *n) = 0;
     virtual sim_status profile_step(const double *targets, float *ms, int32_t *launches, int n_kernels) = 0;
     virtual sim_status get_scene_scalars(double *out, int32_t max_scenes, int32_t *n_scenes) = 0;
+    virtual sim_status get_groups(int32_t *group) = 0;
     virtual sim_status eval_hvp(const double *x, const double *v, double *out) = 0;
     virtual sim_status adjoint_step(const double *x1, const double *ax1, const double *av1, double *ax0, double *av0,
                                     double *dE, double tol, int32_t max_iters, int32_t *iters, double *residual) = 0;

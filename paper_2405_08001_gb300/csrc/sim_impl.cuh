@@ -63,11 +63,14 @@ template <typename R> __global__ void k_reinit(Dev<R> D, int par)
     if (i >= D.nv) return;
     init_vertex<R>(D, i, D.x[i], D.xtil[i], par);
 }
-// refreshes the FP32 form's float-float position copy after the host wrote x
+// refreshes the FP32 form's float-float copies of x and x~ after the host wrote either
 template <typename R> __global__ void k_refresh_ff(Dev<R> D)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < D.nv) put_x<R>(D, i, D.x[i]);
+    if (i < D.nv) {
+        put_x<R>(D, i, D.x[i]);
+        put_xt<R>(D, i, D.xtil[i]);
+    }
 }
 // xtil.w = mass for every vertex (unmasked evaluation)
 static __global__ void k_set_mass_w(double4_32a *xt, const double *mass, int n)
@@ -291,6 +294,7 @@ public:
             st->blocks_per_sm = persist ? pgrid / nsm : 0;
             st->n_scenes = M.nseg;
             st->n_near_fp64 = hctrl->n_near64;
+            st->n_colors = M.color_off.empty() ? 0 : (int)M.color_off.size() - 1;
         }
         return r;
     }
@@ -361,6 +365,7 @@ public:
         if (xt) { r = in3(xt, D.xtil); if (r) return r; }
         const int nb = (M.nv + 255) / 256;
         k_set_mass_w<<<nb, 256, 0, s>>>(D.xtil, D.mass, M.nv);
+        refresh_ff();
         k_reinit<R><<<nb, 256, 0, s>>>(D, 0);
         force_rebuild();
         zero_active();
@@ -608,6 +613,20 @@ public:
         return sync_and_check();
     }
 
+    sim_status get_groups(int32_t *group) override
+    {
+        CK(cudaSetDevice(dev));
+        sim_status r = sync_and_check();
+        const int nv = M.nv;
+        for (int i = 0; i < nv; ++i) group[i] = M.vscene.empty() ? 0 : M.vscene[i];
+        if (D.cmark) {
+            std::vector<int> mark(nv);
+            CK(cudaMemcpy(mark.data(), D.cmark, sizeof(int) * nv, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < nv; ++i) group[i] = 2 * group[i] + mark[i];
+        }
+        return r;
+    }
+
     sim_status get_scene_scalars(double *out, int32_t max_scenes, int32_t *n_scenes) override
     {
         CK(cudaSetDevice(dev));
@@ -746,6 +765,10 @@ private:
     R4 *psave = nullptr;
     int cap = 0, k_host = 0;
     int nvb = 1, ntb = 1, ncb = 1, npb = 1, bpb_boxes = 1, bpb_prims = 1, bpb_query = 1;
+    // colouring scatter: the per-tet inputs in colour order
+    int4 *c_tet = nullptr;
+    R *c_Dm = nullptr, *c_hv = nullptr, *c_es = nullptr;
+    float *c_G0 = nullptr;
     std::vector<cudaEvent_t> prof_ev;
     // persistent form
     bool persist = false;
@@ -810,6 +833,7 @@ private:
         persist = false;
         corot = sizeof(R) == 4 && (M.model == MAT_FCR || M.model == MAT_ARAP);
         if (!M.opt.persistent) return SIM_OK;
+        if (M.opt.scatter == SIM_SCATTER_COLOR) return SIM_OK;         // one kernel per colour: per-phase form
         if (((3 * B.H) >> B.cshift_p) > BP_MAX_CHUNKS) return SIM_OK;   // chunk offsets live in shared memory
         int coop = 0;
         CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -884,12 +908,13 @@ private:
         AL(D.x, nv); AL(D.xt, nv); AL(D.xtil, nv); AL(D.v, nv); AL(D.xb, nv);
         AL(D.g[0], nv); AL(D.g[1], nv); AL(D.dg[0], nv); AL(D.dg[1], nv); AL(D.p, nv);
         D.xh = D.xl = nullptr;
+        D.xth = D.xtl = nullptr;
         D.G0 = nullptr;
         D.tS = nullptr;
         D.xbh = nullptr;
         D.pg = D.pnext = nullptr;
         if (sizeof(R) == 4) {
-            AL(D.xh, nv); AL(D.xl, nv); AL(D.xbh, nv);
+            AL(D.xh, nv); AL(D.xl, nv); AL(D.xbh, nv); AL(D.xth, nv); AL(D.xtl, nv);
             float *g0;
             AL(g0, 14 * (size_t)nt);
             D.G0 = g0;
@@ -921,8 +946,17 @@ private:
         D.beta_rule = M.opt.beta; D.pnorm = M.opt.pnorm; D.iters = M.opt.iters;
         D.segmented = M.opt.scatter == SIM_SCATTER_SEGMENTED;
         D.scatter_block = M.opt.scatter == SIM_SCATTER_BLOCK;
+        D.colored = M.opt.scatter == SIM_SCATTER_COLOR;
+        D.color_tets = nullptr;
+        if (D.colored) {
+            int *ct; AL(ct, (size_t)nt); D.color_tets = ct;
+            AL(c_tet, nt); AL(c_Dm, 9 * (size_t)nt); AL(c_hv, nt);
+            if (!M.escale.empty()) AL(c_es, nt);
+            if (sizeof(R) == 4) AL(c_G0, 14 * (size_t)nt);
+        }
         D.nseg = M.nseg;
-        D.vscene = nullptr; D.seg = nullptr; D.sacc = nullptr; D.smax = nullptr;
+        D.vscene = nullptr; D.seg = nullptr; D.sacc = nullptr; D.smax = nullptr; D.cmark = nullptr;
+        if (M.opt.split_objects == 2) AL(D.cmark, (size_t)nv);
         if (M.nseg > 1) {
             int *vs; AL(vs, (size_t)nv); D.vscene = vs;
             AL(D.seg, (size_t)M.nseg);
@@ -1043,6 +1077,7 @@ private:
             if (!M.cv.empty() && (st = up(D.cv, M.cv.data(), sizeof(int) * M.cv.size()))) return st;
             if ((st = up(D.tloc, M.tloc.data(), sizeof(unsigned short) * 4 * (size_t)nt))) return st;
         }
+        if (D.colored && (st = up((int *)D.color_tets, M.color_tets.data(), sizeof(int) * nt))) return st;
         if (D.segmented) {
             if ((st = up(D.v2c_off, M.v2c_off.data(), sizeof(int) * (nv + 1)))) return st;
             if ((st = up(D.v2c, M.v2c.data(), sizeof(int) * 4 * nt))) return st;
@@ -1078,6 +1113,10 @@ private:
                 g0[(size_t)13 * nt + e] = (float)(det - (double)dh);
             }
             if ((st = up(D.G0, g0.data(), sizeof(float) * 14 * (size_t)nt))) return st;
+        }
+        if (D.colored) {
+            k_color_gather<R><<<(nt + 255) / 256, 256, 0, s>>>(D, c_tet, c_Dm, c_hv, c_es, c_G0);
+            CK(cudaGetLastError());
         }
         refresh_ff();
         std::memset(hctrl, 0, sizeof(Ctrl));
@@ -1124,7 +1163,7 @@ private:
     {
         CK(cudaMemcpyAsync(stage, src, 24 * (size_t)M.nv, cudaMemcpyDefault, s));
         k_pack4<<<(M.nv + 255) / 256, 256, 0, s>>>(stage, dst, M.nv, dst == D.xtil ? 1 : 0);
-        if (dst == D.x) refresh_ff();
+        if (dst == D.x || dst == D.xtil) refresh_ff();
         CK(cudaGetLastError());
         return SIM_OK;
     }
@@ -1203,8 +1242,19 @@ private:
     // the element kernels: the FP32 corotated densities run their own instantiations
     void launch_grad_kernel(int par)
     {
-        if (corot) k_grad<R, true><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
-        else k_grad<R><<<ntb + ncb, EB, 0, s>>>(D, par, ntb);
+        // colouring scatter: the candidates alone (no tet blocks), then one kernel per colour
+        const int nt_blocks = D.colored ? 0 : ntb;
+        if (corot) k_grad<R, true><<<nt_blocks + ncb, EB, 0, s>>>(D, par, nt_blocks);
+        else k_grad<R><<<nt_blocks + ncb, EB, 0, s>>>(D, par, nt_blocks);
+        if (D.colored) {
+            Dev<R> Dc = D;
+            Dc.tet = c_tet; Dc.Dm = c_Dm; Dc.hv = c_hv; Dc.escale = c_es; Dc.G0 = c_G0;
+            for (size_t c = 0; c + 1 < M.color_off.size(); ++c) {
+                const int t0 = M.color_off[c], n = M.color_off[c + 1] - t0;
+                if (corot) k_grad_color<R, true><<<(n + EB - 1) / EB, EB, 0, s>>>(D, Dc, par, t0, n);
+                else k_grad_color<R><<<(n + EB - 1) / EB, EB, 0, s>>>(D, Dc, par, t0, n);
+            }
+        }
     }
     void launch_pHp_kernel()
     {

@@ -9,7 +9,7 @@ runs the steps (no barrier recording): a fixed, countable sequence of launches f
 `ncu -k regex:k_persistent -s W -c 1` captures the first step after W warm-up steps.
 
     python -m paper_2405_08001_gb300.phase_profile [--scene twisted_bar|cube_drop|large_pile|contact_stack|batched]
-        [--precision fp32|fp64] [--warmup W] [--steps K] [--phases] [--plain]
+        [--precision fp32|fp64] [--warmup W] [--steps K] [--phases] [--plain] [--block-shape S] [--scatter C]
 """
 import argparse
 import collections
@@ -53,6 +53,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--phases", action="store_true", help="one kernel per phase instead of the persistent step")
     ap.add_argument("--plain", action="store_true", help="only run the steps (for an external profiler)")
+    ap.add_argument("--block-shape", type=int, default=0, help="sim_options.block_shape (0-3; -1 = autotuned)")
+    ap.add_argument("--scatter", type=int, default=0, help="sim_options.scatter (0 atomic, 1 segmented, 2 block, 3 colour)")
     args = ap.parse_args()
     build.build()
     B.load()
@@ -60,18 +62,26 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     prec = B.SIM_FP32_MIXED if args.precision == "fp32" else B.SIM_FP64
-    sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else 1)
+    sim = B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, persistent=0 if args.phases else 1,
+                block_shape=args.block_shape, scatter=args.scatter)
     n = args.warmup + args.steps
     tg = sc.all_targets(n)
     for s in range(args.warmup):
         B.sim_step(sim.h, 1, None if tg is None else tg[s])
     if args.plain or args.phases:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
         for s in range(args.warmup, n):
             B.sim_step(sim.h, 1, None if tg is None else tg[s])
+        e1.record(stream)
+        torch.cuda.synchronize()
         _, _, st = B.sim_get_state(sim.h, want_x=False, want_v=False)
         sim.close()
-        print(f"{args.scene} {args.precision}: {n} steps; last step: {st['n_candidates']} candidates, "
-              f"{st['n_active']} active pairs, {st['n_rebuilds']} candidate builds")
+        print(f"{args.scene} {args.precision}: {n} steps, {e0.elapsed_time(e1) / max(1, args.steps):.3f} ms per step "
+              f"after the warm-up (CUDA events); last step: {st['n_candidates']} candidates, "
+              f"{st['n_active']} active pairs, {st['n_rebuilds']} candidate builds; block shape "
+              f"{st['block_threads']} x {st['blocks_per_sm']}; scatter {args.scatter}, {st['n_colors']} colours")
         return
     acc = collections.defaultdict(list)
     nblocks = 0
@@ -84,9 +94,9 @@ def main():
             acc[k].append(v)
     _, _, st = B.sim_get_state(sim.h, want_x=False, want_v=False)
     sim.close()
-    print(f"{args.scene} {args.precision}: {args.steps} steps after {args.warmup} warm-up steps, {nblocks} blocks; "
-          f"{st['n_candidates']} candidates, {st['n_active']} active pairs; times in microseconds, per phase "
-          f"instance")
+    print(f"{args.scene} {args.precision}: {args.steps} steps after {args.warmup} warm-up steps, {nblocks} blocks of "
+          f"{st['block_threads']} threads; {st['n_candidates']} candidates, {st['n_active']} active pairs; times in "
+          f"microseconds, per phase instance")
     print(f"{'phase':12s} {'per step':>8s} {'span':>8s} {'median':>8s} {'max':>8s} {'release':>8s} {'late':>8s}")
     print(f"step span (first barrier's release to the last arrival): {np.mean(spans) / 1e3:.1f} us")
     for k, parts in acc.items():

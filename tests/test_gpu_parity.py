@@ -218,10 +218,12 @@ def test_lockstep_cube_drop_with_plane_contact(B, O, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("seed", [0, 2])
-def test_lockstep_two_blocks_pt_ee(B, O, prec, seed):
+@pytest.mark.parametrize("seed,scatter", [(0, 0), (2, 0), (0, 3), (2, 1)])
+def test_lockstep_two_blocks_pt_ee(B, O, prec, seed, scatter):
+    """Lock-step on two blocks in point-triangle and edge-edge contact, with the default (atomic) scatter and with
+    the colouring and segmented ones."""
     sc = S.two_blocks(seed)
-    sim = B.Sim(sc, precision=prec)
+    sim = B.Sim(sc, precision=prec, scatter=scatter)
     o = O.Oracle.from_scene(sc)
     worst = lockstep(B, O, o, sim, sc, sc.iters, prec)
     for k in CHECKED:
@@ -381,15 +383,17 @@ def test_graph_replay_equals_eager_and_segmented_is_deterministic(B, prec):
     out = {}
     for name, use_graph, scatter in (("graph", 1, B.SIM_SCATTER_SEGMENTED), ("eager", 0, B.SIM_SCATTER_SEGMENTED),
                                      ("again", 1, B.SIM_SCATTER_SEGMENTED), ("atomic", 1, B.SIM_SCATTER_ATOMIC),
-                                     ("block", 1, B.SIM_SCATTER_BLOCK)):
+                                     ("block", 1, B.SIM_SCATTER_BLOCK), ("color", 1, B.SIM_SCATTER_COLOR),
+                                     ("color_eager", 0, B.SIM_SCATTER_COLOR)):
         sim = B.Sim(sc, precision=prec, use_graph=use_graph, scatter=scatter)
         sim.step(3)
         out[name] = sim.state()[0]
         sim.close()
     assert np.array_equal(out["graph"], out["eager"])
     assert np.array_equal(out["graph"], out["again"])
+    assert np.array_equal(out["color"], out["color_eager"])   # the colouring scatter adds in a fixed order too
     # 150 iterations amplify the order-dependent rounding of the atomic scatters (about 1e3 times)
-    for name in ("atomic", "block"):
+    for name in ("atomic", "block", "color"):
         assert rel(out[name] - sc.x0, out["graph"] - sc.x0) < (1e-9 if prec == 0 else 1e-3), name
 
 
