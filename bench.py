@@ -196,7 +196,7 @@ def recorded_traffic(kernel: str, prec_name: str, phases: bool = False, scene: s
         return None
 
 
-SHAPES = {(256, 2): 0, (512, 1): 1, (256, 3): 2, (256, 1): 3}   # sim_options.block_shape of (threads, blocks/SM)
+SHAPES = {(256, 2): 0, (512, 1): 1, (256, 3): 2, (256, 1): 3, (384, 1): 4}   # sim_options.block_shape of (threads, blocks/SM)
 
 
 def shape_of(st):

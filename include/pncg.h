@@ -136,8 +136,8 @@ typedef struct {
                              entries of p zero).  Group g = 2 object + (1 for the collision part); a group without
                              vertices takes no step.  Works without scene_of_vert (one object, two groups). */
     int32_t block_shape;  /* block shape of the persistent form: 0 (default) = 256 threads x 2 blocks per SM,
-                             1 = 512 x 1, 2 = 256 x 3, 3 = 256 x 1 (the compiler fits the registers per thread to
-                             the shape: 128, 128, 85, 255); -1 = autotuned: from the second time step on, each shape
+                             1 = 512 x 1, 2 = 256 x 3, 3 = 256 x 1, 4 = 384 x 1 (the compiler fits the registers
+                             per thread to the shape: 128, 128, 85, 255, 168); -1 = autotuned: from the second time step on, each shape
                              runs two time steps (interleaved), timed on the GPU (those steps synchronise), and the
                              shape of the fastest step runs from then on (sim_stats.block_threads, blocks_per_sm).
                              With persistent = 2 the per-phase form is timed as one more candidate.

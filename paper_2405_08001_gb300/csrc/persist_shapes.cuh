@@ -8,11 +8,11 @@
 
 namespace pncg {
 
-constexpr int N_PSHAPES = 4;
+constexpr int N_PSHAPES = 5;
 // shape s: PSHAPE_PB[s] threads per block, at most PSHAPE_MINB[s] blocks per SM (the launch bound the compiler
-// fits the registers to: 128 per thread at 2 x 256, 85 at 3 x 256, 255 at 1 x 256; 128 at 1 x 512)
-constexpr int PSHAPE_PB[N_PSHAPES] = {256, 512, 256, 256};
-constexpr int PSHAPE_MINB[N_PSHAPES] = {2, 1, 3, 1};
+// fits the registers to: 128 per thread at 2 x 256, 85 at 3 x 256, 255 at 1 x 256; 128 at 1 x 512, 168 at 1 x 384)
+constexpr int PSHAPE_PB[N_PSHAPES] = {256, 512, 256, 256, 384};
+constexpr int PSHAPE_MINB[N_PSHAPES] = {2, 1, 3, 1, 1};
 
 // launch of shape S (cooperative, grid blocks, PSHAPE_PB[S] threads) and its occupancy (blocks per SM)
 template <typename R, int S> cudaError_t persist_launch(const Dev<R> &D, const BPDev &B, const PersistArgs &A, int grid,
@@ -24,7 +24,9 @@ template <typename R, int S> cudaError_t persist_occupancy(int *per_sm);
                                                  cudaStream_t);                                                \
     template <> cudaError_t persist_occupancy<R, S>(int *);
 PNCG_PERSIST_DECL(float, 0) PNCG_PERSIST_DECL(float, 1) PNCG_PERSIST_DECL(float, 2) PNCG_PERSIST_DECL(float, 3)
+PNCG_PERSIST_DECL(float, 4)
 PNCG_PERSIST_DECL(double, 0) PNCG_PERSIST_DECL(double, 1) PNCG_PERSIST_DECL(double, 2) PNCG_PERSIST_DECL(double, 3)
+PNCG_PERSIST_DECL(double, 4)
 #undef PNCG_PERSIST_DECL
 
 // the definitions, one shape per translation unit
@@ -59,6 +61,7 @@ inline cudaError_t persist_launch_shape(int shape, const Dev<R> &D, const BPDev 
     case 1: return persist_launch<R, 1>(D, B, A, grid, s);
     case 2: return persist_launch<R, 2>(D, B, A, grid, s);
     case 3: return persist_launch<R, 3>(D, B, A, grid, s);
+    case 4: return persist_launch<R, 4>(D, B, A, grid, s);
     default: return persist_launch<R, 0>(D, B, A, grid, s);
     }
 }
@@ -68,6 +71,7 @@ template <typename R> inline cudaError_t persist_occupancy_shape(int shape, int 
     case 1: return persist_occupancy<R, 1>(per_sm);
     case 2: return persist_occupancy<R, 2>(per_sm);
     case 3: return persist_occupancy<R, 3>(per_sm);
+    case 4: return persist_occupancy<R, 4>(per_sm);
     default: return persist_occupancy<R, 0>(per_sm);
     }
 }

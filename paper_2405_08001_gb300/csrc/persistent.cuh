@@ -560,10 +560,10 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
             {
                 const int per = (nchunk + PB - 1) / PB;   // chunks per thread (nchunk <= BP_MAX_CHUNKS)
                 const int c0 = threadIdx.x * per;
-                unsigned int loc[BP_MAX_CHUNKS / PB];
+                unsigned int loc[(BP_MAX_CHUNKS + PB - 1) / PB];
                 unsigned int tsum = 0;
 #pragma unroll
-                for (int q = 0; q < BP_MAX_CHUNKS / PB; ++q) {
+                for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
                     loc[q] = (q < per && c0 + q < nchunk) ? __ldcg(B.ctot + c0 + q) : 0u;
                     tsum += loc[q];
                 }
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, Pers
                 unsigned int run = inc - tsum;
                 for (int w = 0; w < warp; ++w) run += wtot[w];
 #pragma unroll
-                for (int q = 0; q < BP_MAX_CHUNKS / PB; ++q) {
+                for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
                     if (q < per && c0 + q < nchunk) choff[c0 + q] = run;
                     run += loc[q];
                 }

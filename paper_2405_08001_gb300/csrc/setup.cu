@@ -116,7 +116,7 @@ sim_status build_host_mesh(const sim_mesh *mesh, const sim_material *mat, double
     }
     if (opt.iters <= 0 || opt.beta < 0 || opt.beta > 1 || opt.pnorm < 0 || opt.pnorm > 1 || opt.precision < 0 ||
         opt.precision > 1 || opt.scatter < 0 || opt.scatter > 3 || opt.persistent < 0 || opt.persistent > 2 ||
-        opt.split_objects < 0 || opt.split_objects > 2 || opt.block_shape < -1 || opt.block_shape > 3) {
+        opt.split_objects < 0 || opt.split_objects > 2 || opt.block_shape < -1 || opt.block_shape > 4) {
         err = "invalid options";
         return SIM_ERR_INVALID_ARG;
     }

@@ -53,7 +53,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--phases", action="store_true", help="one kernel per phase instead of the persistent step")
     ap.add_argument("--plain", action="store_true", help="only run the steps (for an external profiler)")
-    ap.add_argument("--block-shape", type=int, default=0, help="sim_options.block_shape (0-3; -1 = autotuned)")
+    ap.add_argument("--block-shape", type=int, default=0, help="sim_options.block_shape (0-4; -1 = autotuned)")
     ap.add_argument("--scatter", type=int, default=0, help="sim_options.scatter (0 atomic, 1 segmented, 2 block, 3 colour)")
     args = ap.parse_args()
     build.build()

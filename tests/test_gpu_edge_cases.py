@@ -59,7 +59,8 @@ def test_invalid_inputs_are_rejected(B):
         with pytest.raises(B.SimError) as ei:
             _create(B, x, t, **kw)
         assert ei.value.status == B.SIM_ERR_INVALID_ARG, name
-    for field, value in (("iters", 0), ("beta", 2), ("precision", 3), ("split_objects", 2), ("persistent", 3)):
+    for field, value in (("iters", 0), ("beta", 2), ("precision", 3), ("split_objects", 3), ("persistent", 3),
+                         ("block_shape", 5), ("scatter", 4)):
         o = B.options_for(sc)
         setattr(o, field, value)
         with pytest.raises(B.SimError) as ei:
