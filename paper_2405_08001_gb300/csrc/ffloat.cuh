@@ -46,9 +46,28 @@ __device__ inline void ff_axpy(float &h, float &l, float ah, float al, float p)
     l = __fsub_rn(e, __fsub_rn(h, s));
 }
 
-// Compensated accumulator: s + c carries sum_k sign_k x_k y_k for float-float x, y.
+// Compensated accumulator: s + c carries sum_k sign_k x_k y_k for float-float x, y.  The first term can start it
+// (prod, prod_f): the TwoSum of a term into a zero sum is exact and only costs instructions.
 struct ffacc {
     float s = 0.0f, c = 0.0f;
+    // x y for float-float x, y: the FMA TwoProd of the heads, the cross terms into the compensation
+    __device__ static inline ffacc prod(ffl x, ffl y)
+    {
+        ffacc a;
+        a.s = __fmul_rn(x.h, y.h);
+        float e = __fmaf_rn(x.h, y.h, -a.s);
+        e = __fmaf_rn(x.h, y.l, e);
+        a.c = __fmaf_rn(x.l, y.h, e);
+        return a;
+    }
+    // x y for a float-float x and a float y
+    __device__ static inline ffacc prod_f(ffl x, float y)
+    {
+        ffacc a;
+        a.s = __fmul_rn(x.h, y);
+        a.c = __fmaf_rn(x.l, y, __fmaf_rn(x.h, y, -a.s));
+        return a;
+    }
     __device__ inline void add_prod(ffl x, ffl y, float sign)
     {
         float p = __fmul_rn(x.h, y.h);

@@ -615,9 +615,9 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
 #pragma unroll
         for (int j = i; j < 3; ++j) {
             const int q = (i == 0 ? j : (i == 1 ? 2 + j : 5));   // 00 01 02 11 12 22
-            ffacc acc;
+            ffacc acc = ffacc::prod(ds[0][i], ds[0][j]);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc.add_prod(ds[a][i], ds[a][j], 1.0f);
+            for (int a = 1; a < 3; ++a) acc.add_prod(ds[a][i], ds[a][j], 1.0f);
             acc.sub_ff(g0h[q], g0l[q]);
             G[i][j] = G[j][i] = acc.ff();
         }
@@ -641,9 +641,9 @@ __device__ inline bool tet_stress_metric(const Dev<float> &D, const TetIn<float>
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            ffacc acc;
+            ffacc acc = ffacc::prod_f(G[i][0], T.w[0][b]);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) acc.add_prod_f(G[i][j], T.w[j][b]);
+            for (int j = 1; j < 3; ++j) acc.add_prod_f(G[i][j], T.w[j][b]);
             GW[i][b] = acc.value();
         }
 #pragma unroll
