@@ -294,8 +294,8 @@ def side_workload(B, torch, S, stream, flush, sc, name, desc, unit_scale, unit, 
 
 
 def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shapes, repeat=3):
-    """FP32-mixed against plain FP64 at equal final-energy accuracy on one time step (the comparison the method's
-    FP32 form is judged by).
+    """FP32-mixed against plain FP64 at equal final-energy accuracy on one time step (the fair comparison of the two
+    precision forms: equal iteration counts would credit the FP32 form with steps that reach less).
 
     From a saved state the step is taken once per form with max(ks) iterations through the persistent kernel, one
     iteration batch at a time (sim_iterate), and the energy after K iterations is read for every K in `ks`; the
