@@ -309,3 +309,46 @@ def test_differentiation_config_twenty_converged_steps(B):
     hv = 1e-3 * np.abs(v0).max()
     fd = (loss(v0 + hv * uv) - loss(v0 - hv * uv)) / (2 * hv)
     assert abs(float(np.vdot(gv, uv)) - fd) <= 1e-3 * abs(fd), (float(np.vdot(gv, uv)), fd)
+
+
+def test_fp32_adjoint_steps_match_the_oracle_adjoint(B, O):
+    """The FP32 form's reverse steps against the oracle's (FP64) adjoint steps along the 3-cell drop's run (its
+    states from the FP64 form).  A linear solve turns an operator error of relative size eps into a solution error
+    of at most cond(H) eps, and each reverse step starts from the previous one's result: the bound after k reverse
+    steps is 10 k cond(H) eps, with cond(H) from the oracle's dense Hessian at the state (its columns are H e_j) and
+    eps the FP32 Hessian-vector kernel's measured error there, max over random v of |H v - H_oracle v| / (|H| |v|)."""
+    sc = drop_scene()
+    rng = np.random.default_rng(23)
+    sim64 = B.Sim(sc, precision=0)
+    xs = [sc.x0.copy()]
+    for t in range(sc.steps):
+        sim64.step(1)
+        xs.append(sim64.state()[0])
+    sim64.close()
+    sim = B.Sim(sc, precision=1)
+    o = O.Oracle.from_scene(sc)
+    ax = rng.normal(size=sc.x0.shape)
+    av = rng.normal(size=sc.x0.shape)
+    axo, avo = ax.copy(), av.copy()
+    dE, dEo = np.zeros(sc.n_tets), np.zeros(sc.n_tets)
+    n = 3 * sc.n_verts
+    for k, t in enumerate(range(sc.steps, 0, -1), start=1):
+        H = np.zeros((n, n))
+        for j in range(n):
+            e = np.zeros(n)
+            e[j] = 1.0
+            H[:, j] = o.hvp(xs[t], e.reshape(-1, 3)).ravel()
+        ev = np.abs(np.linalg.eigvalsh(0.5 * (H + H.T)))
+        cond = ev.max() / ev.min()
+        eps = 0.0
+        for _ in range(4):
+            v = rng.normal(size=sc.x0.shape)
+            hv = B.sim_eval_hvp(sim.h, xs[t], v)
+            eps = max(eps, np.linalg.norm(hv - o.hvp(xs[t], v)) / (ev.max() * np.linalg.norm(v)))
+        ax, av, it, res = B.sim_adjoint_step(sim.h, xs[t], ax, av, dE=dE, tol=1e-9, max_iters=20000)
+        axo, avo, ito, reso = o.adjoint_step(xs[t], axo, avo, dE=dEo, tol=1e-13, max_iters=20000)
+        bound = 10 * k * cond * eps
+        for a, b in ((ax, axo), (av, avo), (dE, dEo)):
+            err = np.linalg.norm(a - b) / np.linalg.norm(b)
+            assert err <= bound, (t, err, cond, eps)
+    sim.close()
