@@ -387,7 +387,9 @@ def test_graph_replay_equals_eager_and_segmented_is_deterministic(B, prec):
                                      ("color_eager", 0, B.SIM_SCATTER_COLOR)):
         sim = B.Sim(sc, precision=prec, use_graph=use_graph, scatter=scatter)
         sim.step(3)
-        out[name] = sim.state()[0]
+        x, _, st = sim.state()
+        out[name] = x
+        assert (st["n_colors"] > 0) == (scatter == B.SIM_SCATTER_COLOR), (name, st["n_colors"])
         sim.close()
     assert np.array_equal(out["graph"], out["eager"])
     assert np.array_equal(out["graph"], out["again"])

@@ -87,6 +87,7 @@ def split_lockstep(B, O, sim, sc, iters, rule):
 def test_split_objects_lockstep(B, O, seed, rule, prec):
     sc = S.objects(seed)
     sim = B.Sim(sc, precision=prec, split_objects=1, beta=rule)
+    assert np.array_equal(B.sim_get_groups(sim.h), sc.scene_of_vert)   # the groups are the objects
     worst, cross = split_lockstep(B, O, sim, sc, sc.iters, rule)
     for k, v in worst.items():
         assert v < TOL[prec], (k, {kk: f"{vv:.3e}" for kk, vv in worst.items()})
