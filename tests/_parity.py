@@ -75,3 +75,21 @@ def update_entry(x1, x, alpha, p1):
     ref = alpha * np.asarray(p1)
     floor = 4 * np.spacing(np.abs(np.asarray(x1))) + 4 * np.spacing(np.abs(np.asarray(x)))
     return entrywise(np.asarray(x1) - np.asarray(x), ref, np.abs(ref), floor)
+
+
+def pHp_pair_scale(O, o, x, p, dhat, kappa):
+    """The magnitude of the barrier terms of p^T H p at x (Eqs. 12-13): the sum over the active pairs of
+    |A (c.p . t)^2| + |B |c.p|^2|, A = kappa (b''/d^2 - b'/d^3), B = kappa b'/d, with c.p = sum_i c_i p_i.  The two
+    terms have opposite signs (b' < 0) and the pairs' sum can cancel, so a float evaluation's rounding is relative to
+    this, not to the net p^T H p."""
+    idx, _, _ = o.active_pairs(x)
+    s = 0.0
+    for row in idx:
+        t, vv = int(row[0]), [int(v) for v in row[1:]]
+        d, c, tt = O.pair_geometry(t, x[vv])
+        b = O.barrier_fn(d, dhat)
+        cp = (c[:, None] * p[vv]).sum(axis=0)
+        A = kappa * (b[2] / d ** 2 - b[1] / d ** 3)
+        B = kappa * b[1] / d
+        s += abs(A) * float(cp @ tt) ** 2 + abs(B) * float(cp @ cp)
+    return s

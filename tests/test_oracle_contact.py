@@ -241,3 +241,30 @@ def test_rest_pose_exclusion(oracle_mod):
     assert len(idx) > 0
     half = X.shape[0]
     assert np.all((idx[:, 1] < half) != (idx[:, 3] < half))   # every active pair spans the two objects
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pair_scale_of_pHp_bounds_the_barrier_part(oracle_mod, seed):
+    """The magnitude the parity tests measure a group's p^T H p error against (tests/_parity.py pHp_pair_scale): it
+    bounds the barrier part of the oracle's p^T H p (the difference to the same scene without contact stiffness),
+    is quadratic in p, and vanishes for a rigid translation (sum_i c_i = 0), which leaves the barrier part at zero."""
+    import dataclasses
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _parity import pHp_pair_scale
+    O = oracle_mod
+    sc = S.two_blocks(seed)
+    o = O.Oracle.from_scene(sc)
+    o0 = O.Oracle.from_scene(dataclasses.replace(sc, kappa=0.0))
+    x = sc.x0
+    assert len(o.active_pairs(x)[0]) > 0
+    rng = np.random.default_rng(seed)
+    p = rng.normal(size=x.shape)
+    barrier = o.pHp(x, p) - o0.pHp(x, p)
+    s = pHp_pair_scale(O, o, x, p, sc.dhat, sc.kappa)
+    assert s >= abs(barrier) * (1 - 1e-12) and s > 0
+    assert abs(pHp_pair_scale(O, o, x, 2 * p, sc.dhat, sc.kappa) - 4 * s) <= 1e-12 * s
+    shift = np.tile(rng.normal(size=3), (sc.n_verts, 1))
+    assert pHp_pair_scale(O, o, x, shift, sc.dhat, sc.kappa) <= 1e-12 * s
+    assert abs(o.pHp(x, shift) - o0.pHp(x, shift)) <= 1e-9 * abs(o.pHp(x, shift))
