@@ -641,6 +641,8 @@ def run_ours(args):
                        "launch": "one kernel per phase" if args.phases else "one persistent cooperative kernel per step",
                        "block_shape": shape32_rep},
             "time_steps_per_s": round(K / (total_ms / 1e3), 2),
+            "step_ms": {"median": round(statistics.median(t32), 4), "min": round(min(t32), 4),
+                        "max": round(max(t32), 4), "note": "this rank's timed steps, one CUDA-event pair each"},
             "fp64_plain": {"value": round(v64, 2), "unit": UNIT, "ms_per_step": round(ms64, 4), "steps": K64,
                            "launch": "persistent" if st64["launch_form"] == 1 else "one kernel per phase",
                            "block_shape": shape64_rep,
