@@ -40,13 +40,13 @@ def small_batch(seed=5, n_scenes=6):
     return sc
 
 
-def batched_lockstep(B, O, sim, sc, iters, prec):
+def batched_lockstep(B, O, sim, sc, iters, prec, model=0):
     """Lock-step iterations of one time step: after every GPU iteration each scene's gradient, preconditioner,
     direction, p^T H p, max |p_v|, step and update are compared with the oracle of that scene from the GPU's own
     inputs (as in the single-scene protocol), as relative 2-norms, entry by entry and over contact vertices.
     Returns the worst errors over scenes and iterations."""
     ranges = sc.scene_ranges()
-    oracles = [O.Oracle.from_scene(sc.subscene(s)) for s in range(len(ranges))]
+    oracles = [O.Oracle.from_scene(sc.subscene(s), model=model) for s in range(len(ranges))]
     B.sim_begin_step(sim.h, None)
     keys = ("g", "P", "p", "pHp", "pmax", "alpha", "dx", "g_entry", "P_entry", "g_contact", "P_contact", "p_entry",
             "dx_entry")
@@ -89,6 +89,19 @@ def test_batched_lockstep_per_scene(B, O, prec, shape):
         assert v < TOL[prec], (k, {kk: f"{vv:.3e}" for kk, vv in worst.items()})
     scal = B.sim_get_scene_scalars(sim.h)
     assert len(scal["alpha"]) == sc.n_scenes
+    sim.close()
+
+
+@pytest.mark.parametrize("model,prec", [(1, 1), (2, 1), (3, 1), (2, 0)])
+def test_batched_lockstep_other_densities(B, O, model, prec):
+    """Per-scene lock-step with the other energy densities (SNH, FCR, ARAP; the FP32 corotated ones run their own
+    kernel instantiation) in the batched form."""
+    sc = small_batch(seed=7)
+    sim = B.Sim(sc, precision=prec, model=model)
+    sim.step(2)
+    worst = batched_lockstep(B, O, sim, sc, sc.iters, prec, model=model)
+    for k, v in worst.items():
+        assert v < TOL[prec], (k, {kk: f"{vv:.3e}" for kk, vv in worst.items()})
     sim.close()
 
 
