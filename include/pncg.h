@@ -137,9 +137,10 @@ typedef struct {
                              vertices takes no step.  Works without scene_of_vert (one object, two groups). */
     int32_t block_shape;  /* block shape of the persistent form: 0 (default) = 256 threads x 2 blocks per SM,
                              1 = 512 x 1, 2 = 256 x 3, 3 = 256 x 1, 4 = 384 x 1 (the compiler fits the registers
-                             per thread to the shape: 128, 128, 85, 255, 168); -1 = autotuned: from the second time step on, each shape
-                             runs two time steps (interleaved), timed on the GPU (those steps synchronise), and the
-                             shape of the fastest step runs from then on (sim_stats.block_threads, blocks_per_sm).
+                             per thread to the shape: 128, 128, 85, 255, 168); -1 = autotuned: from the second time
+                             step on, each shape runs two time steps (interleaved), timed on the GPU (those steps
+                             synchronise), and the shape of the fastest step runs from then on
+                             (sim_stats.block_threads, blocks_per_sm).
                              With persistent = 2 the per-phase form is timed as one more candidate.
                              SIM_SCATTER_BLOCK keeps shape 0. */
 } sim_options;
@@ -155,7 +156,8 @@ typedef struct {
     int32_t n_surface_tris, n_surface_edges, n_surface_verts;
     double dE0, dE_last;   /* Delta E of the first and the last iteration */
     int32_t launch_form;   /* the form time steps run in now: 1 = persistent, 0 = one kernel per phase */
-    int32_t n_scenes;      /* independent scenes (1 without scene_of_vert) */
+    int32_t n_scenes;      /* groups with their own scalars: independent scenes, objects (split_objects = 1) or
+                              object parts (split_objects = 2: two per object); 1 without scene_of_vert and parts */
     int32_t n_near_fp64;   /* FP32 form: pair evaluations of the last step (or of the last sim_eval_* call) whose
                               distance fell below 1e-3 dhat, where the barrier terms are evaluated in double */
     int32_t block_threads; /* persistent form: threads per block and blocks per SM of the shape in use (0 in the */
