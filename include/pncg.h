@@ -357,8 +357,8 @@ int32_t sim_abi_version(void);
  * Differentiation (the adjoint of a time step, read as the exact minimiser of Algorithm 1's incremental potential
  * E(x; x~, theta); the paper has no adjoint).
  *
- * sim_eval_hvp: out = H(x) v, H the Hessian of E at x as the p^T H p pass sees it (Sec. 3.1 Neo-Hookean terms,
- * the barrier with the closest points frozen, Eqs. 12-13, the half-space barrier and the lumped mass), candidates
+ * sim_eval_hvp: out = H(x) v, H the Hessian of E at x as the p^T H p pass sees it (the Sec. 3.1 split of the
+ * handle's density, the I1 term of the fixed corotated and as-rigid-as-possible densities included; the barrier with the closest points frozen, Eqs. 12-13, the half-space barrier and the lumped mass), candidates
  * and active pairs taken at x.  Rows and columns of kinematic vertices are dropped (their out entries are 0).
  * x, v, out: [n_verts][3], host or device.  The handle's state is kept.  Synchronises.
  */

@@ -1,7 +1,7 @@
 // Differentiation of a simulated trajectory by the adjoint method.  Each time step is taken as the solution of
 // grad E(x_{t+1}; x~_t, theta) = 0 (Algorithm 1's minimisation), x~_t = x_t + h v_t + h^2 g, v_{t+1} = (x_{t+1} - x_t)/h.
 // The implicit function theorem gives H dx_{t+1} = M dx~_t - (d grad E / d theta) d theta with H the Hessian of E at
-// x_{t+1} (inertia, Neo-Hookean, barrier with the closest points frozen as in Sec. 3.2, half-space barrier), so a
+// x_{t+1} (inertia, elastic density, barrier with the closest points frozen as in Sec. 3.2, half-space barrier), so a
 // reverse step solves H lambda = abar_x(t+1) + abar_v(t+1)/h and carries abar_x~ = M lambda back:
 //   abar_x(t) = M lambda - abar_v(t+1)/h,   abar_v(t) = h M lambda,   abar_E_e -= lambda_e . d g_e / d E_e.
 // H is applied matrix-free (the vector form of the p^T H p terms); the solve is Jacobi-preconditioned linear CG with
@@ -47,8 +47,10 @@ template <typename R> __device__ inline void vadd(const Dev<R> &D, double *out, 
     atomicAdd(out + 3 * i + 2, double(c));
 }
 
-// Neo-Hookean tet part: h^2 V dP(dF) W^T scattered to the corners, dP = mu dF + Psi_33 (cof F : dF) cof F +
-// Psi_3 d cof(F)[dF] (the differential of P = mu F + Psi_3 cof F); p^T (H v) equals the p^T H p form of Sec. 3.1.
+// Elastic tet part: h^2 V dP(dF) W^T scattered to the corners, dP = 2 Psi_2 dF + Psi_33 (cof F : dF) cof F +
+// Psi_3 d cof(F)[dF] + Psi_1 H1[dF] (the differential of P = Psi_1 R + 2 Psi_2 F + Psi_3 cof F; the I1 term of the
+// fixed corotated and as-rigid-as-possible densities from the polar decomposition, in double); p^T (H v) equals the
+// p^T H p form of Sec. 3.1.
 template <typename R>
 __global__ void __launch_bounds__(EB) k_hvp_tet(Dev<R> D, const double *v, double *out)
 {
@@ -70,9 +72,7 @@ __global__ void __launch_bounds__(EB) k_hvp_tet(Dev<R> D, const double *v, doubl
         for (int b = 0; b < 3; ++b) dF[a][b] = dp[a][0] * T.w[0][b] + dp[a][1] * T.w[1][b] + dp[a][2] * T.w[2][b];
     R mu, lam;
     tet_material<R>(D, e, mu, lam);
-    const R L = log(T.J);
-    const R Psi3 = (lam * L - mu) / T.J;
-    const R Psi33 = (mu + lam * (R(1) - L)) / (T.J * T.J);
+    const MatTerms<R> mt = mat_terms<R>(D.model, mu, lam, T.J);
     R g3 = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -90,7 +90,21 @@ __global__ void __launch_bounds__(EB) k_hvp_tet(Dev<R> D, const double *v, doubl
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) dP[a][b] = sc * (mu * dF[a][b] + Psi33 * g3 * T.cf[a][b] + Psi3 * dcof[a][b]);
+        for (int b = 0; b < 3; ++b) dP[a][b] = sc * (mt.c2 * dF[a][b] + mt.Psi33 * g3 * T.cf[a][b] + mt.Psi3 * dcof[a][b]);
+    if (mt.Psi1 != R(0)) {
+        double Fd[3][3], dFd[3][3], H1[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) { Fd[a][b] = double(T.F[a][b]); dFd[a][b] = double(dF[a][b]); }
+        Polar pol;
+        polar_of(Fd, pol);
+        polar_h1_vec(pol, dFd, H1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) dP[a][b] += sc * R(double(mt.Psi1) * H1[a][b]);
+    }
     R o[4][3];
 #pragma unroll
     for (int i = 1; i < 4; ++i)

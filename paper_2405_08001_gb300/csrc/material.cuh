@@ -157,6 +157,26 @@ __device__ inline double polar_h1(const Polar &P, const double dF[3][3])
     return quad_Mi(P, K[2][1] - K[1][2], K[0][2] - K[2][0], K[1][0] - K[0][1]);
 }
 
+// the operator form of polar_h1: H1[dF] = R [Mi a]x^T with a = axial(R^T dF - dF^T R), so that
+// dF : H1[dF] = a^T Mi a (a . b = (R^T dF) : B(b) for the skew B(b) with B21 = b0, B02 = b1, B10 = b2)
+__device__ inline void polar_h1_vec(const Polar &P, const double dF[3][3], double out[3][3])
+{
+    double K[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) K[a][b] = P.R[0][a] * dF[0][b] + P.R[1][a] * dF[1][b] + P.R[2][a] * dF[2][b];
+    const double a0 = K[2][1] - K[1][2], a1 = K[0][2] - K[2][0], a2 = K[1][0] - K[0][1];
+    const double b0 = P.Mi[0][0] * a0 + P.Mi[0][1] * a1 + P.Mi[0][2] * a2;
+    const double b1 = P.Mi[1][0] * a0 + P.Mi[1][1] * a1 + P.Mi[1][2] * a2;
+    const double b2 = P.Mi[2][0] * a0 + P.Mi[2][1] * a1 + P.Mi[2][2] * a2;
+    const double Bm[3][3] = {{0.0, -b2, b1}, {b2, 0.0, -b0}, {-b1, b0, 0.0}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) out[a][b] = P.R[a][0] * Bm[0][b] + P.R[a][1] * Bm[1][b] + P.R[a][2] * Bm[2][b];
+}
+
 // the diagonal entry of vertex weight vector w and component c: a = w x rho, rho = R^T e_c (row c of R)
 __device__ inline double polar_h1_diag(const Polar &P, const double w[3], int c)
 {

@@ -674,7 +674,6 @@ public:
     {
         CK(cudaSetDevice(dev));
         if (!x || !v || !out) return fail(SIM_ERR_INVALID_ARG, "x, v and out are required");
-        if (M.model != SIM_MAT_NH) return fail(SIM_ERR_INVALID_ARG, "the Hessian-vector product supports Neo-Hookean only");
         sim_status r = adj_alloc();
         if (r) return r;
         r = eval_setup(x, nullptr);
@@ -693,7 +692,6 @@ public:
         CK(cudaSetDevice(dev));
         if (!x1 || !ax1 || !av1 || !ax0 || !av0 || max_iters <= 0 || !(tol > 0))
             return fail(SIM_ERR_INVALID_ARG, "x1, the adjoints and a positive tolerance and iteration cap are required");
-        if (M.model != SIM_MAT_NH) return fail(SIM_ERR_INVALID_ARG, "the adjoint step supports Neo-Hookean only");
         sim_status r = adj_alloc();
         if (r) return r;
         r = eval_setup(x1, nullptr);   // H at x_{t+1}: candidates, active pairs and the gradient pass there

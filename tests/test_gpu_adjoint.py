@@ -57,6 +57,32 @@ def test_hvp_is_the_oracle_bilinear_form(B, O, make, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("model", [1, 2, 3])
+def test_hvp_other_densities(B, O, model, prec):
+    """The Hessian-vector kernel for the stable Neo-Hookean, fixed corotated and as-rigid-as-possible densities
+    against the oracle's H v (its I1 term from the polar decomposition), on the lowered cube at a strained state:
+    the rest shape stretched by 3 % along x and sheared, plus noise, so that S differs from I and R from a plain
+    rotation; and p . (H v) = v . (H p)."""
+    sc = lowered_cube()
+    sim = B.Sim(sc, precision=prec, model=model)
+    o = O.Oracle.from_scene(sc, model=model)
+    rng = np.random.default_rng(31 + model)
+    c = sc.x0.mean(axis=0)
+    A = np.array([[1.03, 0.02, 0.0], [0.0, 0.99, 0.015], [0.0, 0.0, 1.0]])
+    x = (sc.x0 - c) @ A.T + c + 2e-5 * rng.normal(size=sc.x0.shape)
+    tol = 1e-10 if prec == 0 else 1e-5
+    for _ in range(3):
+        v = rng.normal(size=x.shape)
+        Hv = B.sim_eval_hvp(sim.h, x, v)
+        ref = o.hvp(x, v)
+        assert np.linalg.norm(Hv - ref) <= tol * np.linalg.norm(ref)
+        p = rng.normal(size=x.shape)
+        Hp = B.sim_eval_hvp(sim.h, x, p)
+        assert abs(np.vdot(p, Hv) - np.vdot(v, Hp)) <= tol * abs(np.vdot(v, Hp))
+    sim.close()
+
+
 def drop_scene(iters=1000, steps=5):
     """A 3-cell cube 1.5 mm above the plane, falling and tipping: the barrier is active from the first step.  1000
     iterations per step converge every step to rounding (200 leave 3e-9 m, which biases central differences of
@@ -203,17 +229,18 @@ def test_differentiation_config_full_size(B, O):
     assert abs(float(gE @ uE)) < 1e-6 * np.linalg.norm(exact) * np.linalg.norm(uE) / np.sqrt(sc.n_tets)
 
 
-def test_adjoint_steps_match_the_oracle_adjoint(B, O):
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_adjoint_steps_match_the_oracle_adjoint(B, O, model):
     """Each reverse step of the library (sim_adjoint_step) against the oracle's own adjoint step (its CG on its
     Hessian-vector product, pinned on the CPU) from the same end state and adjoints, along the 3-cell drop's run:
-    dL/dx_t, dL/dv_t and the accumulated dL/dE_e."""
+    dL/dx_t, dL/dv_t and the accumulated dL/dE_e; for each of the four densities."""
     sc = drop_scene()
     rng = np.random.default_rng(21)
     E0 = np.full(sc.n_tets, 1e5) * (1.0 + 0.2 * rng.uniform(-1, 1, sc.n_tets))
     import dataclasses
     s2 = dataclasses.replace(sc, youngs=1.0, youngs_per_tet=E0)
-    sim = B.Sim(s2, precision=0)
-    o = O.Oracle.from_scene(s2)
+    sim = B.Sim(s2, precision=0, model=model)
+    o = O.Oracle.from_scene(s2, model=model)
     xs = [s2.x0.copy()]
     for t in range(s2.steps):
         sim.step(1)

@@ -103,17 +103,12 @@ def test_lockstep_contact_step(B, O, model, prec):
         assert v < TOL[prec], (kk, {q: f"{w:.3e}" for q, w in worst.items()})
 
 
-def test_unsupported_combinations_are_rejected(B):
-    """An unknown density is refused; the adjoint (sim_eval_hvp, sim_adjoint_step) supports Neo-Hookean only."""
+def test_unknown_density_is_rejected(B):
+    """An unknown density is refused."""
     sc = S.two_blocks(0)
     with pytest.raises(B.SimError) as ei:
         B.Sim(sc, precision=0, model=4)
     assert ei.value.status == B.SIM_ERR_INVALID_ARG
-    sim = B.Sim(sc, precision=0, model=1)
-    with pytest.raises(B.SimError) as ei:
-        B.sim_eval_hvp(sim.h, sc.x0, np.ones_like(sc.x0))
-    assert ei.value.status == B.SIM_ERR_INVALID_ARG
-    sim.close()
 
 
 @pytest.mark.parametrize("model", [2, 3])

@@ -33,13 +33,17 @@ def test_hvp_is_the_polarised_pHp_and_symmetric(oracle_mod, make):
         assert abs(np.vdot(v, Hv) - o.pHp(x, v)) <= 1e-12 * abs(o.pHp(x, v))
 
 
-def test_hvp_equals_differences_of_the_gradient_with_plane_contact(oracle_mod):
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_hvp_equals_differences_of_the_gradient_with_plane_contact(oracle_mod, model):
     """Inertia, elasticity and the plane barrier have exact Hessians (no closest point to freeze): H v equals the
-    central difference of the gradient along v."""
+    central difference of the gradient along v, for each density (the fixed corotated and as-rigid-as-possible ones
+    at a stretched and sheared state, where the I1 term's rotation is not the identity)."""
     sc = lowered_cube()
-    o = oracle_mod.Oracle.from_scene(sc)
+    o = oracle_mod.Oracle.from_scene(sc, model=model)
     rng = np.random.default_rng(3)
-    x = sc.x0 + 2e-5 * rng.normal(size=sc.x0.shape)
+    c = sc.x0.mean(axis=0)
+    A = np.eye(3) if model == 0 else np.array([[1.03, 0.02, 0.0], [0.0, 0.99, 0.015], [0.0, 0.0, 1.0]])
+    x = (sc.x0 - c) @ A.T + c + 2e-5 * rng.normal(size=sc.x0.shape)
     xt = sc.x0.copy()
     assert (x[:, 2] < sc.dhat).any()
     v = rng.normal(size=x.shape)
