@@ -14,7 +14,7 @@ class Simulate(torch.autograd.Function):
 
     The forward creates a handle for `scene` with the given Young's moduli and initial velocities (float64 tensors;
     the scene's other data as given), advances `steps` time steps and keeps every step's positions (the checkpoints
-    the reverse pass needs).  Each step is taken as the exact minimiser of its incremental potential, so the
+    the reverse pass needs); `options` are the handle's keyword options (scatter, model, ...).  Each step is taken as the exact minimiser of its incremental potential, so the
     forward should be converged (enough iterations, or the eps rule) for the gradients to be those of the run."""
 
     @staticmethod

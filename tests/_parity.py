@@ -70,6 +70,38 @@ def direction_entry(p1, P1, g1, beta, p0):
     return entrywise(np.asarray(p1).ravel(), ref, scale)
 
 
+def beta_scale(g1, P1, g0, P0, p0, k, rule=0):
+    """The magnitude of beta's terms (Sec. 4.1): for beta = N / D formed from sums of per-entry products, rounding of
+    relative size u in each product (the FP32 form's inputs g, P and y = g1 - g0 are float) moves beta by up to
+    u (sum |n_i| + |beta| sum |d_i|) / |D|.  PR+: N = g1 P1 y, D = g0 P0 g0.  DK: beta = gPy / yp - yPy pg / yp^2, the
+    same first-order bound over its four sums.  Zero at k = 0 (beta = 0 on both sides)."""
+    if k == 0:
+        return 0.0
+    g1, P1, g0, P0, p0 = (np.asarray(a, dtype=np.float64).ravel() for a in (g1, P1, g0, P0, p0))
+    y = g1 - g0
+    if rule == 0:
+        D = float(np.dot(g0 * P0, g0))
+        if not D > 0.0:
+            return 0.0
+        beta = max(float(np.dot(g1 * P1, y)) / D, 0.0)
+        return float(np.abs(g1 * P1 * y).sum()) / D + beta
+    S1, S2, S3, S4 = (float(np.dot(g1 * P1, y)), float(np.dot(y * P1, y)), float(np.dot(y, p0)), float(np.dot(p0, g1)))
+    if abs(S3) < 1e-30:
+        return 0.0
+    A1, A3, A4 = float(np.abs(g1 * P1 * y).sum()), float(np.abs(y * p0).sum()), float(np.abs(p0 * g1).sum())
+    return (A1 / abs(S3) + abs(S1) * A3 / S3 ** 2 + (S2 * abs(S4) + S2 * A4) / S3 ** 2 +
+            2.0 * S2 * abs(S4) * A3 / abs(S3) ** 3)
+
+
+def direction_error(p1, pd, g1, P1, g0, P0, p0, k, rule=0):
+    """|p1 - pd| / (|pd| + beta_scale |p0|): the GPU direction against the oracle's (-P1 g1 + beta p0 with the
+    oracle's beta from the same g1, P1, g0, P0, p0), relative to the direction plus what beta's rounding can move
+    it by."""
+    p1, pd, p0 = (np.asarray(a, dtype=np.float64).ravel() for a in (p1, pd, p0))
+    den = np.linalg.norm(pd) + beta_scale(g1, P1, g0, P0, p0, k, rule) * np.linalg.norm(p0)
+    return float(np.linalg.norm(p1 - pd) / max(den, 1e-300))
+
+
 def update_entry(x1, x, alpha, p1):
     """Entry-wise error of the update x1 - x against alpha p1, relative to |alpha p1| beyond 4 ulp of x."""
     ref = alpha * np.asarray(p1)

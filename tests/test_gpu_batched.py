@@ -5,7 +5,7 @@ tolerances as the single-scene tests."""
 import numpy as np
 import pytest
 
-from _parity import direction_entry, grad_errors, rel, update_entry
+from _parity import direction_entry, direction_error, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -65,7 +65,8 @@ def batched_lockstep(B, O, sim, sc, iters, prec, model=0):
             pHp_ref = o.pHp(x[sl], p1[sl])
             pm_ref = O.pmax(p1[sl])
             a_ref = O.ncg_alpha(scal["gp"][s], scal["pHp"][s], scal["pmax"][s], sc.dhat)[0]
-            e = dict(g=rel(g1[sl], go), P=rel(P1[sl], Po), p=rel(p1[sl].ravel(), pd),
+            pe = direction_error(p1[sl], pd, g1[sl], P1[sl], g[sl], P[sl], p[sl], k, 0)
+            e = dict(g=rel(g1[sl], go), P=rel(P1[sl], Po), p=pe,
                      pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref), pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref,
                      alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref), dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]))
             e.update(grad_errors(o, x[sl], xt[sl], g1[sl], go, P=P1[sl], Po=Po))

@@ -7,7 +7,7 @@ step, at the single-scene tolerances."""
 import numpy as np
 import pytest
 
-from _parity import direction_entry, grad_errors, rel, update_entry
+from _parity import direction_entry, direction_error, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -91,7 +91,8 @@ def test_lockstep_contact_step(B, O, model, prec):
         pd, beta = O.ncg_direction(g1, P1, g, P, p, k, 0)[:2]
         pHp_ref = o.pHp(x, p1)
         a_ref = O.ncg_alpha(s1["gp"], s1["pHp"], s1["pmax"], sc.dhat)[0]
-        e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
+        pe = direction_error(p1, pd, g1, P1, g, P, p, k, 0)
+        e = dict(g=rel(g1, go), P=rel(P1, Po), p=pe, pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
                  alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1),
                  p_entry=direction_entry(p1, P1, g1, s1["beta"], p), dx_entry=update_entry(x1, x, s1["alpha"], p1))
         e.update(grad_errors(o, x, xt, g1, go, P=P1, Po=Po))

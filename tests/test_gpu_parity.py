@@ -9,7 +9,7 @@ and the relative 2-norm over the entries of contact vertices alone.
 import numpy as np
 import pytest
 
-from _parity import direction_entry, entrywise, grad_errors, rel, update_entry
+from _parity import direction_entry, direction_error, entrywise, grad_errors, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -158,7 +158,8 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
     """Runs `iters` iterations of one step on the GPU; at every iteration the oracle repeats each kernel's work
     from the GPU's own inputs and the worst relative errors are returned:
       g, P  : gradient and preconditioner at the GPU's x_k (oracle's full iteration from the GPU's state)
-      p     : direction from the GPU's g_{k+1}, P_{k+1} and its g_k, P_k, p_k (beta, restart and update)
+      p     : direction from the GPU's g_{k+1}, P_{k+1} and its g_k, P_k, p_k (beta, restart and update), relative
+              to |p| plus what beta's rounding can move it by (_parity.direction_error)
       pHp   : p^T H p at x_k for the GPU's direction
       pmax  : the largest per-vertex length of the GPU's direction
       alpha : step rule from the GPU's g^T p, p^T H p and max |p_v|
@@ -182,7 +183,8 @@ def lockstep(B, O, o, sim, sc, iters, prec, targets=None):
         pHp_ref = o.pHp(x, p1)
         a_ref = O.ncg_alpha(s1["gp"], s1["pHp"], s1["pmax"], sc.dhat)[0]
         pm_ref = O.pmax(p1)
-        e = dict(g=rel(g1, go), P=rel(P1, Po), p=rel(p1.ravel(), pd), pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
+        pe = direction_error(p1, pd, g1, P1, g, P, p, k, o_rule(sc))
+        e = dict(g=rel(g1, go), P=rel(P1, Po), p=pe, pHp=abs(s1["pHp"] - pHp_ref) / abs(pHp_ref),
                  pmax=abs(s1["pmax"] - pm_ref) / pm_ref,
                  alpha=abs(s1["alpha"] - a_ref) / abs(a_ref), dx=rel(x1 - x, s1["alpha"] * p1), chain_p=rel(p1, po))
         e.update(grad_errors(o, x, xt, g1, go, P=P1, Po=Po, fixed=fixed))

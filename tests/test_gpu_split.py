@@ -5,7 +5,7 @@ precisions and with both beta rules; plus the candidate pass pairing primitives 
 import numpy as np
 import pytest
 
-from _parity import direction_entry, grad_errors, pHp_pair_scale, rel, update_entry
+from _parity import direction_entry, direction_error, grad_errors, pHp_pair_scale, rel, update_entry
 from paper_2405_08001_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -68,7 +68,8 @@ def split_lockstep(B, O, sim, sc, iters, rule):
             pHp_ref = o.pHp(x, pm)
             pm_ref = O.pmax(p1[sl])
             a_ref = O.ncg_alpha(scal["gp"][s], scal["pHp"][s], scal["pmax"][s], sc.dhat)[0]
-            es = dict(p=rel(p1[sl].ravel(), pd), pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref),
+            pe = direction_error(p1[sl], pd, g1[sl], P1[sl], g[sl], P[sl], p[sl], k, rule)
+            es = dict(p=pe, pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref),
                       pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref, alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref),
                       dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]),
                       p_entry=direction_entry(p1[sl], P1[sl], g1[sl], scal["beta"][s], p[sl]),
@@ -181,7 +182,8 @@ def parts_lockstep(B, O, sim, sc, iters, rule, obj):
             pscale = abs(pHp_ref) + pHp_pair_scale(O, o, x, pm, sc.dhat, sc.kappa)
             pm_ref = O.pmax(p1[sl])
             a_ref = O.ncg_alpha(scal["gp"][s], scal["pHp"][s], scal["pmax"][s], sc.dhat)[0]
-            es = dict(p=rel(p1[sl].ravel(), pd), pHp=abs(scal["pHp"][s] - pHp_ref) / pscale,
+            pe = direction_error(p1[sl], pd, g1[sl], P1[sl], g[sl], P[sl], p[sl], k, rule)
+            es = dict(p=pe, pHp=abs(scal["pHp"][s] - pHp_ref) / pscale,
                       pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref, alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref),
                       dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]),
                       p_entry=direction_entry(p1[sl], P1[sl], g1[sl], scal["beta"][s], p[sl]),

@@ -274,3 +274,46 @@ def test_preconditioner_floor_is_a_thousandth_of_the_mass(oracle_mod, ratio):
     o.iteration(x, sc.x0, g, P, p, 0)
     want = 1.0 / m if ratio < 1e-3 else 1.0 / diag[b0, 0]
     assert abs(P[b0, 0] / want - 1.0) < 1e-12, (P[b0, 0] * m, want * m)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_beta_scale_bounds_float_rounding_of_beta(oracle_mod, rule):
+    """The scale the GPU parity tests measure beta's error against (tests/_parity.py beta_scale): beta formed from
+    float inputs with y = g1 - g0 and every product rounded to float (as the FP32 form's reduction inputs are) differs
+    from the oracle's double beta of the same inputs by at most 4 u beta_scale (u = 2^-24; three roundings per
+    product), on inputs whose sums cancel (beta_scale up to more than 30 |beta|)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _parity import beta_scale
+    O = oracle_mod
+    rng = np.random.default_rng(7 + rule)
+    n = 3000
+    worst, ratio = 0.0, 0.0
+    for _ in range(20):
+        g0 = rng.normal(size=n).astype(np.float32)
+        g1 = (g0 * (1.0 + 1e-3 * rng.normal(size=n))).astype(np.float32)
+        P1 = rng.uniform(0.5, 2.0, n).astype(np.float32)
+        P0 = rng.uniform(0.5, 2.0, n).astype(np.float32)
+        p0 = rng.normal(size=n).astype(np.float32)
+        _, beta, _, rs = O.ncg_direction(g1, P1, g0, P0, p0, 1, rule)
+        if rs:
+            continue
+        y = (g1 - g0).astype(np.float32)
+        if rule == 0:
+            num = np.sum((g1 * P1).astype(np.float32) * y, dtype=np.float64)
+            den = np.sum((g0 * P0).astype(np.float32) * g0, dtype=np.float64)
+            bf = max(num / den, 0.0)
+        else:
+            gPy = np.sum((g1 * P1).astype(np.float32) * y, dtype=np.float64)
+            yPy = np.sum((y * P1).astype(np.float32) * y, dtype=np.float64)
+            yp = np.sum(y * p0, dtype=np.float64)
+            pg = np.sum(p0 * g1, dtype=np.float64)
+            bf = gPy / yp - (yPy / yp) * (pg / yp)
+        s = beta_scale(g1, P1, g0, P0, p0, 1, rule)
+        err = abs(bf - beta)
+        worst = max(worst, err / (4 * 2.0 ** -24 * s))
+        ratio = max(ratio, s / max(abs(beta), 1e-300))
+    assert 0.0 < worst <= 1.0, worst
+    assert beta_scale(g1, P1, g0, P0, p0, 0, rule) == 0.0
+    assert ratio > 30.0, ratio
