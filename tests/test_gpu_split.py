@@ -43,8 +43,9 @@ def _offsets(sc):
 
 def split_lockstep(B, O, sim, sc, iters, rule):
     """After every GPU iteration: the gradient and preconditioner against the oracle's, and per object the
-    direction, p_o^T H p_o (the oracle's pHp of the GPU's p with the other objects' entries zero), max |p_v|, the
-    step and the update, as relative 2-norms, entry by entry and over contact vertices.  Returns the worst errors."""
+    direction, p_o^T H p_o (the oracle's pHp of the GPU's p with the other objects' entries zero, relative to its
+    size plus that of its barrier terms, _parity.pHp_pair_scale), max |p_v|, the step and the update, as relative
+    2-norms, entry by entry and over contact vertices.  Returns the worst errors."""
     off = _offsets(sc)
     o = O.Oracle.from_scene(sc, beta_rule=rule)
     B.sim_begin_step(sim.h, None)
@@ -66,10 +67,12 @@ def split_lockstep(B, O, sim, sc, iters, rule):
             pm = np.zeros_like(p1)
             pm[sl] = p1[sl]
             pHp_ref = o.pHp(x, pm)
+            # objects pressed together: p_o^T H p_o holds barrier terms of both signs, rounding is relative to them
+            pscale = abs(pHp_ref) + pHp_pair_scale(O, o, x, pm, sc.dhat, sc.kappa)
             pm_ref = O.pmax(p1[sl])
             a_ref = O.ncg_alpha(scal["gp"][s], scal["pHp"][s], scal["pmax"][s], sc.dhat)[0]
             pe = direction_error(p1[sl], pd, g1[sl], P1[sl], g[sl], P[sl], p[sl], k, rule)
-            es = dict(p=pe, pHp=abs(scal["pHp"][s] - pHp_ref) / abs(pHp_ref),
+            es = dict(p=pe, pHp=abs(scal["pHp"][s] - pHp_ref) / pscale,
                       pmax=abs(scal["pmax"][s] - pm_ref) / pm_ref, alpha=abs(scal["alpha"][s] - a_ref) / abs(a_ref),
                       dx=rel(x1[sl] - x[sl], scal["alpha"][s] * p1[sl]),
                       p_entry=direction_entry(p1[sl], P1[sl], g1[sl], scal["beta"][s], p[sl]),
