@@ -68,11 +68,15 @@ def test_hvp_drops_kinematic_rows_and_columns(oracle_mod):
     assert abs(np.vdot(vm, Hv) - o.pHp(x, vm)) <= 1e-12 * abs(o.pHp(x, vm))
 
 
-def test_adjoint_solve_equals_a_dense_solve(oracle_mod):
+@pytest.mark.parametrize("model", [0, 2])
+def test_adjoint_solve_equals_a_dense_solve(oracle_mod, model):
     """The CG solve of the adjoint step against numpy's dense solve of the Hessian assembled column by column from
-    H v: the adjoint velocity h M lambda must match."""
+    H v: the adjoint velocity h M lambda must match (Neo-Hookean and fixed corotated).  In norm within the linear
+    solve's a-priori bound, 10 cond(H) times CG's relative residual (cond about 4e8 here: mass-dominated modes at
+    7e-4, barrier modes at 3e5, H indefinite through the frozen-c barrier); entry by entry to 1e-7 (measured
+    1e-8)."""
     sc = S.two_blocks(0, n=2)
-    o = oracle_mod.Oracle.from_scene(sc)
+    o = oracle_mod.Oracle.from_scene(sc, model=model)
     rng = np.random.default_rng(5)
     x1 = sc.x0 + 1e-5 * rng.normal(size=sc.x0.shape)
     n = 3 * sc.n_verts
@@ -86,8 +90,11 @@ def test_adjoint_solve_equals_a_dense_solve(oracle_mod):
     ax0, av0, it, res = o.adjoint_step(x1, ax1, av1, tol=1e-13, max_iters=10000)
     m = o.mass()[:, None]
     assert res < 1e-12
-    np.testing.assert_allclose(av0, sc.dt * m * lam, rtol=1e-8, atol=1e-12 * np.abs(sc.dt * m * lam).max())
-    np.testing.assert_allclose(ax0 + av1 / sc.dt, m * lam, rtol=1e-8, atol=1e-12 * np.abs(m * lam).max())
+    ev = np.abs(np.linalg.eigvalsh(0.5 * (H + H.T)))   # the frozen-c barrier can make H indefinite
+    bound = 10.0 * (ev.max() / ev.min()) * max(res, 1e-16)
+    for a, ref in ((av0, sc.dt * m * lam), (ax0 + av1 / sc.dt, m * lam)):
+        assert np.linalg.norm(a - ref) <= bound * np.linalg.norm(ref), np.linalg.norm(a - ref) / np.linalg.norm(ref)
+        np.testing.assert_allclose(a, ref, rtol=1e-7, atol=1e-12 * np.abs(ref).max())
 
 
 def drop_scene(iters=1000, steps=3):
@@ -98,9 +105,9 @@ def drop_scene(iters=1000, steps=3):
     return sc
 
 
-def forward(oracle_mod, sc, youngs, v0):
+def forward(oracle_mod, sc, youngs, v0, model=0):
     s2 = dataclasses.replace(sc, youngs=1.0, youngs_per_tet=youngs, v0=v0)
-    o = oracle_mod.Oracle.from_scene(s2)
+    o = oracle_mod.Oracle.from_scene(s2, model=model)
     x, v = s2.x0.copy(), s2.v0.copy()
     xs = [x.copy()]
     for t in range(s2.steps):
@@ -109,9 +116,11 @@ def forward(oracle_mod, sc, youngs, v0):
     return o, xs
 
 
-def test_adjoint_gradients_match_differences_of_the_converged_forward(oracle_mod):
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_adjoint_gradients_match_differences_of_the_converged_forward(oracle_mod, model):
     """The reverse pass (adjoint_step per step, from the end) gives dL/dE_e and dL/dv0 equal to central differences
-    (relative step 1e-4) of the loss of the oracle's converged forward run, L = |centroid(x_T) - target|^2."""
+    (relative step 1e-4) of the loss of the oracle's converged forward run, L = |centroid(x_T) - target|^2; for
+    each of the four densities."""
     sc = drop_scene()
     rng = np.random.default_rng(6)
     E0 = np.full(sc.n_tets, 1e5) * (1.0 + 0.2 * rng.uniform(-1, 1, sc.n_tets))
@@ -121,7 +130,7 @@ def test_adjoint_gradients_match_differences_of_the_converged_forward(oracle_mod
         d = xT.mean(axis=0) - target
         return float(d @ d)
 
-    o, xs = forward(oracle_mod, sc, E0, sc.v0)
+    o, xs = forward(oracle_mod, sc, E0, sc.v0, model)
     ax = np.tile(2.0 * (xs[-1].mean(axis=0) - target) / sc.n_verts, (sc.n_verts, 1))
     av = np.zeros_like(ax)
     dE = np.zeros(sc.n_tets)
@@ -130,11 +139,11 @@ def test_adjoint_gradients_match_differences_of_the_converged_forward(oracle_mod
         assert res < 1e-12
     for _ in range(2):
         uE = rng.normal(size=E0.shape) * E0
-        fd = (loss(forward(oracle_mod, sc, E0 + 1e-4 * uE, sc.v0)[1][-1]) -
-              loss(forward(oracle_mod, sc, E0 - 1e-4 * uE, sc.v0)[1][-1])) / 2e-4
+        fd = (loss(forward(oracle_mod, sc, E0 + 1e-4 * uE, sc.v0, model)[1][-1]) -
+              loss(forward(oracle_mod, sc, E0 - 1e-4 * uE, sc.v0, model)[1][-1])) / 2e-4
         assert abs(dE @ uE - fd) <= 1e-4 * abs(fd), (dE @ uE, fd)
         uv = rng.normal(size=sc.v0.shape)
         h = 1e-4 * np.abs(sc.v0).max()
-        fd = (loss(forward(oracle_mod, sc, E0, sc.v0 + h * uv)[1][-1]) -
-              loss(forward(oracle_mod, sc, E0, sc.v0 - h * uv)[1][-1])) / (2 * h)
+        fd = (loss(forward(oracle_mod, sc, E0, sc.v0 + h * uv, model)[1][-1]) -
+              loss(forward(oracle_mod, sc, E0, sc.v0 - h * uv, model)[1][-1])) / (2 * h)
         assert abs(np.vdot(av, uv) - fd) <= 1e-4 * abs(fd), (np.vdot(av, uv), fd)
