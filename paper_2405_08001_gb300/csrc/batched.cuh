@@ -118,11 +118,10 @@ template <typename R> __device__ inline void seg_reset(const Dev<R> &D)
 
 // Beta, direction + p^T H p, and update phases of iteration k for nseg > 1 scenes (three grid barriers, as in the
 // single-scene form).  sbuf holds the scenes' beta and alpha (2 x MAX_SCENES doubles).  Returns 1 when some vertex
-// has moved far enough since the candidate build to need a new one.  Out of line: the single-scene step does not
-// carry its registers (the kernel's parameters are grid constants, so D is not copied for the call).
+// has moved far enough since the candidate build to need a new one.
 template <typename R, int PB, bool CO>
-__device__ __noinline__ int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh, unsigned char *sbuf,
-                                        Bar &br, Stamper &st, RedBufs &rb, int k, int par, int &sred, double disp_lim)
+__device__ inline int batched_tail(const Dev<R> &D, Ctrl *c, PShared<R, PB> &sh, unsigned char *sbuf, Bar &br,
+                                   Stamper &st, RedBufs &rb, int k, int par, int &sred, double disp_lim)
 {
     typedef typename V4<R>::T R4;
     typedef typename PartT<R>::T PT;

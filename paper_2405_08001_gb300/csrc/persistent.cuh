@@ -398,145 +398,8 @@ namespace pncg {
 
 // ------------------------------------------------------------------------------------------------ the kernel
 
-// a1 inside the persistent step: the candidate build's five phases, out of line.  The build runs only when some
-// vertex has moved r/2; inlined, its temporaries raised the register pressure of the whole step and the iteration's
-// phases spilled (256 x 3: 568 bytes of spill stores against 180 with the build and the batched tail out of line).
-template <typename R, int PB>
-__device__ __noinline__ void persist_build(const Dev<R> &D, const BPDev &B, Ctrl *c, PShared<R, PB> &sh,
-                                           unsigned char *sbuf, Bar &br, Stamper &st, RedBufs &rb)
-{
-    typedef typename PartT<R>::T PT;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthr = gridDim.x * blockDim.x;
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-    const Share vs = share_of(D.nv);
-    const int ov = vs.b0 + (int)threadIdx.x;
-    br.phase = 1;   // K_BP_BOXES
-    // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
-    if (lead) { c->n_cand = 0; c->n_units = 0; c->n_units_h = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
-    const int nprim = B.nf + B.ne;
-    float ext_max = 0.0f;
-    for (int j = tid; j < 3 * B.H; j += nthr) B.cnt[j] = 0u;
-    for (int j = ov; j < vs.b1; j += PB) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
-    const Share ps = share_of(nprim);
-    for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) {
-        int v[3];
-        int nvp;
-        if (j < B.nf) { const int4 t = B.tri[j]; v[0] = t.x; v[1] = t.y; v[2] = t.z; nvp = 3; }
-        else { const int4 e = B.edge[j - B.nf]; v[0] = e.x; v[1] = e.y; nvp = 2; }
-        float4 lo, hi;
-        box_of(B.x, v, nvp, B.infl, lo, hi);
-        B.blo[j] = lo;
-        B.bhi[j] = hi;
-        ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
-    }
-    const float ext = (float)grid_max<R, PB>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
-    if (lead) c->cell_bits = __float_as_uint(ext);
-    st.mark(1);   // K_BP_BOXES
-    const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
-    br.phase = 2;   // K_BP_COUNT
-    for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
-        for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
-    const Share ss = share_of(B.ns);
-    for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) {
-        int v, cc[3];
-        double4_32a X;
-        if (point_cell(B, j, cg, v, X, cc)) atomicAdd(&B.cnt[point_bucket(B, cc[0], cc[1], cc[2])], 1u);
-        else atomicOr(&c->err, ERR_RANGE);
-    }
-    grid_barrier(br, c);
-    st.mark(2);   // K_BP_COUNT
-    // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane; the work
-    // units of the triangle and edge buckets are listed on the way
-    br.phase = 3;   // K_BP_SCAN
-    const int cs = B.cshift_p;
-    const int nchunk = (3 * B.H) >> cs;
-    {
-        const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
-        for (int ch = gw; ch < nchunk; ch += nwarps) {
-            unsigned int run = 0;
-            for (int base = ch << cs; base < (ch + 1) << cs; base += 128) {
-                const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(B.cnt + base) + lane);
-                {
-                    const unsigned int b4 = (unsigned int)base + 4u * (unsigned int)lane;
-                    const unsigned int bb[4] = {b4, b4 + 1u, b4 + 2u, b4 + 3u}, nn[4] = {v.x, v.y, v.z, v.w};
-                    list_units(B, bb, nn);
-                }
-                const unsigned int tot = v.x + v.y + v.z + v.w;
-                unsigned int inc = tot;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += n;
-                }
-                const unsigned int ex = run + inc - tot;
-                reinterpret_cast<uint4 *>(B.off + base)[lane] = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
-                reinterpret_cast<uint4 *>(B.cnt + base)[lane] = make_uint4(0u, 0u, 0u, 0u);   // the fill cursor
-                run += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            if (lane == 0) B.ctot[ch] = run;
-        }
-    }
-    grid_barrier(br, c);
-    st.mark(3);   // K_BP_SCAN
-    // every block scans the chunk totals into shared memory; the buckets' global offsets go to goff for
-    // the queries, and the entries to their slots
-    br.phase = 4;   // K_BP_FILL
-    unsigned int *choff = reinterpret_cast<unsigned int *>(sbuf);   // [BP_MAX_CHUNKS]
-    {
-        const int per = (nchunk + PB - 1) / PB;   // chunks per thread (nchunk <= BP_MAX_CHUNKS)
-        const int c0 = threadIdx.x * per;
-        unsigned int loc[(BP_MAX_CHUNKS + PB - 1) / PB];
-        unsigned int tsum = 0;
-#pragma unroll
-        for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
-            loc[q] = (q < per && c0 + q < nchunk) ? __ldcg(B.ctot + c0 + q) : 0u;
-            tsum += loc[q];
-        }
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        unsigned int inc = tsum;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
-        }
-        __shared__ unsigned int wtot[PB / 32];
-        if (lane == 31) wtot[warp] = inc;
-        __syncthreads();
-        unsigned int run = inc - tsum;
-        for (int w = 0; w < warp; ++w) run += wtot[w];
-#pragma unroll
-        for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
-            if (q < per && c0 + q < nchunk) choff[c0 + q] = run;
-            run += loc[q];
-        }
-        __syncthreads();
-    }
-    for (int b = tid; b < 3 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
-    {
-        auto slot_of = [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); };
-        for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) fill_prim(B, j, cg, slot_of);
-        for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) fill_point(B, j, cg, slot_of);
-    }
-    grid_barrier(br, c);
-    st.mark(4);   // K_BP_FILL
-    // queries: the listed work units, the warp's staging area in sbuf; a warp takes its own unit, then
-    // whichever units are left
-    br.phase = 5;   // K_BP_QUERY
-    {
-        BPQWarp &W = reinterpret_cast<BPQWarp *>(sbuf)[threadIdx.x >> 5];
-        const int nw = nthr >> 5;
-        bpq_units(B, cg, W, tid >> 5, [&]() {
-            int nx = 0;
-            if ((threadIdx.x & 31) == 0) nx = nw + (int)atomicAdd(&c->ticket[TK_QUERY], 1u);
-            return __shfl_sync(0xffffffffu, nx, 0);
-        });
-    }
-    grid_barrier(br, c);
-    st.mark(5);   // K_BP_QUERY
-}
-
 template <typename R, int PB, int MINB, bool CO = false>
-__global__ void __launch_bounds__(PB, MINB)
-k_persistent(const __grid_constant__ Dev<R> D, const __grid_constant__ BPDev B, PersistArgs A)
+__global__ void __launch_bounds__(PB, MINB) k_persistent(Dev<R> D, BPDev B, PersistArgs A)
 {
     typedef typename V4<R>::T R4;
     typedef typename PartT<R>::T PT;
@@ -623,7 +486,127 @@ k_persistent(const __grid_constant__ Dev<R> D, const __grid_constant__ BPDev B, 
         const int par = k & 1;
         // ------------------------------------------------------------ a1: candidate build when needed
         if (rebuild) {
-            persist_build<R, PB>(D, B, c, sh, sbuf, br, st, rb);
+            br.phase = 1;   // K_BP_BOXES
+            // boxes, bucket counts to zero, build positions; the cell size is the grid max of the box extents
+            if (lead) { c->n_cand = 0; c->n_units = 0; c->n_units_h = 0; c->n_rebuilds += 1; c->ticket[TK_QUERY] = 0u; }
+            const int nprim = B.nf + B.ne;
+            float ext_max = 0.0f;
+            for (int j = tid; j < 3 * B.H; j += nthr) B.cnt[j] = 0u;
+            for (int j = ov; j < vs.b1; j += PB) { B.xb[j] = ldcg4(B.x + j); if (B.xbh) B.xbh[j] = ldcg4(B.xh + j); }
+            const Share ps = share_of(nprim);
+            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) {
+                int v[3];
+                int nvp;
+                if (j < B.nf) { const int4 t = B.tri[j]; v[0] = t.x; v[1] = t.y; v[2] = t.z; nvp = 3; }
+                else { const int4 e = B.edge[j - B.nf]; v[0] = e.x; v[1] = e.y; nvp = 2; }
+                float4 lo, hi;
+                box_of(B.x, v, nvp, B.infl, lo, hi);
+                B.blo[j] = lo;
+                B.bhi[j] = hi;
+                ext_max = fmaxf(ext_max, fmaxf(__fsub_ru(hi.x, lo.x), fmaxf(__fsub_ru(hi.y, lo.y), __fsub_ru(hi.z, lo.z))));
+            }
+            const float ext = (float)grid_max<R, PB>(R(ext_max), rb.max_region<PT, R>(), sh, br, c);
+            if (lead) c->cell_bits = __float_as_uint(ext);
+            st.mark(1);   // K_BP_BOXES
+            const CellGrid cg = grid_of(ext * 1.0001f);   // as cell_size() forms it from cell_bits
+            br.phase = 2;   // K_BP_COUNT
+            for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB)
+                for_cells(B, __ldcg(B.blo + j), __ldcg(B.bhi + j), cg, [&](int i, int jj, int kk) { atomicAdd(&B.cnt[prim_bucket(B, j, i, jj, kk)], 1u); });
+            const Share ss = share_of(B.ns);
+            for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) {
+                int v, cc[3];
+                double4_32a X;
+                if (point_cell(B, j, cg, v, X, cc)) atomicAdd(&B.cnt[point_bucket(B, cc[0], cc[1], cc[2])], 1u);
+                else atomicOr(&c->err, ERR_RANGE);
+            }
+            grid_barrier(br, c);
+            st.mark(2);   // K_BP_COUNT
+            // exclusive scans of the chunks of 2^cshift buckets, one warp per chunk, four buckets per lane; the work
+            // units of the triangle and edge buckets are listed on the way
+            br.phase = 3;   // K_BP_SCAN
+            const int cs = B.cshift_p;
+            const int nchunk = (3 * B.H) >> cs;
+            {
+                const int gw = tid >> 5, lane = threadIdx.x & 31, nwarps = nthr >> 5;
+                for (int ch = gw; ch < nchunk; ch += nwarps) {
+                    unsigned int run = 0;
+                    for (int base = ch << cs; base < (ch + 1) << cs; base += 128) {
+                        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(B.cnt + base) + lane);
+                        {
+                            const unsigned int b4 = (unsigned int)base + 4u * (unsigned int)lane;
+                            const unsigned int bb[4] = {b4, b4 + 1u, b4 + 2u, b4 + 3u}, nn[4] = {v.x, v.y, v.z, v.w};
+                            list_units(B, bb, nn);
+                        }
+                        const unsigned int tot = v.x + v.y + v.z + v.w;
+                        unsigned int inc = tot;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
+                            if (lane >= o) inc += n;
+                        }
+                        const unsigned int ex = run + inc - tot;
+                        reinterpret_cast<uint4 *>(B.off + base)[lane] = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+                        reinterpret_cast<uint4 *>(B.cnt + base)[lane] = make_uint4(0u, 0u, 0u, 0u);   // the fill cursor
+                        run += __shfl_sync(0xffffffffu, inc, 31);
+                    }
+                    if (lane == 0) B.ctot[ch] = run;
+                }
+            }
+            grid_barrier(br, c);
+            st.mark(3);   // K_BP_SCAN
+            // every block scans the chunk totals into shared memory; the buckets' global offsets go to goff for
+            // the queries, and the entries to their slots
+            br.phase = 4;   // K_BP_FILL
+            unsigned int *choff = reinterpret_cast<unsigned int *>(sbuf);   // [BP_MAX_CHUNKS]
+            {
+                const int per = (nchunk + PB - 1) / PB;   // chunks per thread (nchunk <= BP_MAX_CHUNKS)
+                const int c0 = threadIdx.x * per;
+                unsigned int loc[(BP_MAX_CHUNKS + PB - 1) / PB];
+                unsigned int tsum = 0;
+#pragma unroll
+                for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
+                    loc[q] = (q < per && c0 + q < nchunk) ? __ldcg(B.ctot + c0 + q) : 0u;
+                    tsum += loc[q];
+                }
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                unsigned int inc = tsum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int n = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += n;
+                }
+                __shared__ unsigned int wtot[PB / 32];
+                if (lane == 31) wtot[warp] = inc;
+                __syncthreads();
+                unsigned int run = inc - tsum;
+                for (int w = 0; w < warp; ++w) run += wtot[w];
+#pragma unroll
+                for (int q = 0; q < (BP_MAX_CHUNKS + PB - 1) / PB; ++q) {
+                    if (q < per && c0 + q < nchunk) choff[c0 + q] = run;
+                    run += loc[q];
+                }
+                __syncthreads();
+            }
+            for (int b = tid; b < 3 * B.H; b += nthr) B.goff[b] = choff[b >> cs] + __ldcg(B.off + b);
+            {
+                auto slot_of = [&](unsigned int b) { return choff[b >> cs] + __ldcg(B.off + b) + atomicAdd(&B.cnt[b], 1u); };
+                for (int j = ps.b0 + (int)threadIdx.x; j < ps.b1; j += PB) fill_prim(B, j, cg, slot_of);
+                for (int j = ss.b0 + (int)threadIdx.x; j < ss.b1; j += PB) fill_point(B, j, cg, slot_of);
+            }
+            grid_barrier(br, c);
+            st.mark(4);   // K_BP_FILL
+            // queries: the listed work units, the warp's staging area in sbuf; a warp takes its own unit, then
+            // whichever units are left
+            br.phase = 5;   // K_BP_QUERY
+            {
+                BPQWarp &W = reinterpret_cast<BPQWarp *>(sbuf)[threadIdx.x >> 5];
+                const int nw = nthr >> 5;
+                bpq_units(B, cg, W, tid >> 5, [&]() {
+                    int nx = 0;
+                    if ((threadIdx.x & 31) == 0) nx = nw + (int)atomicAdd(&c->ticket[TK_QUERY], 1u);
+                    return __shfl_sync(0xffffffffu, nx, 0);
+                });
+            }
+            grid_barrier(br, c);
+            st.mark(5);   // K_BP_QUERY
             ncand = block_read(&c->n_cand, &sh_i);
             rebuild = 0;
         }
