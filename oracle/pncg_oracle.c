@@ -21,6 +21,8 @@
  *   - the single-pass step alpha = min(dhat / (2 ||p||_inf), -g^T p / p^T H p)                   (Sec. 4.3, Eqs. upper, alpha)
  *   - the rest-pose exclusion of self-collision pairs closer than 1.5 dhat                        (Sec. 5.1)
  *   - per-object splitting: each object its own beta, direction and step                         (Sec. 5.2)
+ *   - differentiation, which the paper does not have: H v as the vector form of p^T H p, and the reverse of one
+ *     time step read as the exact minimiser of its potential (implicit function theorem; linear CG on H v)
  *
  * Readings where the paper is silent (each one is also taken by the CUDA library):
  *   - Psi(x) = sum_e V_e Psi_NH(F_e), F = Ds Dm^-1 with D = [x1-x0, x2-x0, x3-x0]; mu = E/(2(1+nu)),
