@@ -233,8 +233,9 @@ def sim_get_state(h, x_out=None, v_out=None, want_x=True, want_v=True):
 
 
 def sim_set_state(h, x=None, v=None):
-    px, kx = _ptr(x)
-    pv, kv = _ptr(v)
+    nv = sim_get_sizes(h)["n_verts"]
+    px, kx = _ptr(x, n=3 * nv)
+    pv, kv = _ptr(v, n=3 * nv)
     _check(load().sim_set_state(h, px, pv), h)
 
 
@@ -261,7 +262,8 @@ def sim_get_iterate(h):
 
 
 def sim_set_iterate(h, x=None, g=None, P=None, p=None, k: int = 0, gPg: float = 0.0):
-    ptrs = [_ptr(a) for a in (x, g, P, p)]
+    nv = sim_get_sizes(h)["n_verts"]
+    ptrs = [_ptr(a, n=3 * nv) for a in (x, g, P, p)]
     _check(load().sim_set_iterate(h, *[q[0] for q in ptrs], int(k), float(gPg)), h)
 
 
@@ -369,13 +371,14 @@ def sim_eval_hvp(h, x, v, out=None):
 def sim_adjoint_step(h, x1, ax1, av1, dE=None, tol=1e-10, max_iters=2000, ax0=None, av0=None):
     """Reverse of one time step ending at x1: returns (dL/dx_t, dL/dv_t, CG iterations, relative residual) and adds
     dL/dE_e to dE (a float64 [n_tets] array or tensor, updated in place) when given."""
-    nv = sim_get_sizes(h)["n_verts"]
+    sz = sim_get_sizes(h)
+    nv = sz["n_verts"]
     px, kx = _ptr(x1, n=3 * nv)
     pa, ka = _ptr(ax1, n=3 * nv)
     pb, kb = _ptr(av1, n=3 * nv)
     p0, a0 = _out(ax0, nv)
     p1, a1 = _out(av0, nv)
-    pe, ke = (None, None) if dE is None else _ptr(dE)
+    pe, ke = (None, None) if dE is None else _ptr(dE, n=sz["n_tets"])
     if dE is not None and not hasattr(dE, "data_ptr") and ke is not dE:
         raise TypeError("dE must be a C-contiguous float64 array (it is updated in place)")
     it = C.c_int32(0)

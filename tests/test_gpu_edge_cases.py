@@ -68,6 +68,26 @@ def test_invalid_inputs_are_rejected(B):
         assert ei.value.status == B.SIM_ERR_INVALID_ARG, field
 
 
+def test_short_host_arrays_are_rejected_before_the_library_reads_them(B):
+    """The binding checks every state-sized array against the handle's sizes before passing its address: a short
+    array raises ValueError and the handle's state is unchanged."""
+    sc = S.two_blocks(0, n=2)
+    sim = B.Sim(sc, precision=0)
+    x0, v0, _ = sim.state()
+    short = np.zeros((sc.n_verts - 1, 3))
+    with pytest.raises(ValueError):
+        B.sim_set_state(sim.h, short, None)
+    with pytest.raises(ValueError):
+        B.sim_set_iterate(sim.h, x0, short, None, None)
+    with pytest.raises(ValueError):
+        B.sim_eval_hvp(sim.h, x0, short)
+    with pytest.raises(ValueError):
+        B.sim_adjoint_step(sim.h, x0, np.zeros_like(x0), np.zeros_like(x0), dE=np.zeros(sc.n_tets - 1))
+    x1, v1, _ = sim.state()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
+    sim.close()
+
+
 @pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_single_tet_lockstep(B, O, prec, persistent):
