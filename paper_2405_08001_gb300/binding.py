@@ -502,6 +502,7 @@ class Sim:
                             v0=scene.v0, fixed=scene.fixed, youngs_per_tet=scene.youngs_per_tet,
                             scene_of_vert=scene.scene_of_vert, options=self.options, model=model)
         self.nv = scene.n_verts
+        self.n_fixed = 0 if scene.fixed is None else int(np.count_nonzero(scene.fixed))
 
     def close(self):
         if getattr(self, "h", None):
@@ -515,6 +516,9 @@ class Sim:
             pass
 
     def step(self, n=1, targets=None):
+        """n time steps; targets: [n][n_fixed][3] positions of the kinematic vertices (or None to keep them)."""
+        if targets is not None and np.size(targets) < 3 * self.n_fixed * n:
+            raise ValueError(f"targets has {np.size(targets)} values, {3 * self.n_fixed * n} needed")
         sim_step(self.h, n, targets)
 
     def state(self):
