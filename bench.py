@@ -293,13 +293,14 @@ def side_workload(B, torch, S, stream, flush, sc, name, desc, unit_scale, unit, 
             "stats_last_step": {k: st[k] for k in ("n_candidates", "n_active", "n_rebuilds", "n_capped")}}
 
 
-def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shapes, repeat=3):
+def equal_accuracy(B, torch, sc, stream, state, targets, ks, kref, name, shapes, repeat=3):
     """FP32-mixed against plain FP64 at equal final-energy accuracy on one time step (the fair comparison of the two
     precision forms: equal iteration counts would credit the FP32 form with steps that reach less).
 
     From a saved state the step is taken once per form with max(ks) iterations through the persistent kernel, one
     iteration batch at a time (sim_iterate), and the energy after K iterations is read for every K in `ks`; the
-    converged reference x* is the FP64 form after `kref` iterations.  Energies are evaluated by the FP64 oracle:
+    converged reference x* is the FP64 form after `kref` iterations.  Energies are evaluated by the library's FP64
+    energy pass (sim_eval_energy on an FP64 handle per scene; the parity tests match it to the oracle's energy):
     err(K) = (E(x_K) - E(x*)) / (E(x_0) - E(x*)), x_0 the step's start (kinematic targets applied); with several
     scenes (a batch) err is taken per scene and the median over scenes is used.  The target is the plain FP64 form's
     error at the headline iteration count ks[1]; each form's iteration count to reach it is interpolated linearly
@@ -309,10 +310,14 @@ def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shap
     x0, v0 = state
     fixed = sc.fixed.astype(bool) if sc.fixed is not None else None
     ranges = sc.scene_ranges()
-    oracles = [O.Oracle.from_scene(sc.subscene(i) if len(ranges) > 1 else sc) for i in range(len(ranges))]
+    evals = []
 
     def energies(x, xt):
-        return np.array([o.energy(x[v0_:v1_], xt[v0_:v1_])[0] for o, (v0_, v1_, _, _) in zip(oracles, ranges)])
+        if not evals:
+            evals.extend(B.Sim(sc.subscene(i) if len(ranges) > 1 else sc, precision=B.SIM_FP64,
+                               cuda_stream=stream.cuda_stream) for i in range(len(ranges)))
+        return np.array([B.sim_eval_energy(e.h, x[v0_:v1_], xt[v0_:v1_])[0]
+                         for e, (v0_, v1_, _, _) in zip(evals, ranges)])
 
     def sim_of(prec, K):   # in the block shape each form's autotuner chose on the benchmark's run
         return B.Sim(sc, precision=prec, cuda_stream=stream.cuda_stream, iters=K, persistent=1,
@@ -352,6 +357,16 @@ def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shap
             sim.close()
         return out
 
+    try:
+        return _equal_accuracy_rows(B, x0, fixed, targets, ks, kref, name, ranges, energies, curve, timed)
+    finally:
+        for e in evals:
+            e.close()
+
+
+def _equal_accuracy_rows(B, x0, fixed, targets, ks, kref, name, ranges, energies, curve, timed):
+    """The error curves, the target and the interpolated costs of equal_accuracy (its handles closed by the caller)."""
+    import numpy as np
     (xr, xt), = curve(B.SIM_FP64, (kref,))
     Eref = energies(xr, xt)
     xs = x0.copy()
@@ -379,7 +394,7 @@ def equal_accuracy(B, torch, O, sc, stream, state, targets, ks, kref, name, shap
             prev = r
         return None
     c64, c32 = cost(res["fp64"]), cost(res["fp32_mixed"])
-    return {"workload": name, "reference": f"FP64, {kref} iterations (x*); energies by the FP64 oracle",
+    return {"workload": name, "reference": f"FP64, {kref} iterations (x*); energies by the library's FP64 energy pass",
             "error": "(E(x_K) - E(x*)) / (E(x_0) - E(x*)) after K iterations of one trajectory per form"
                      + ("; median over the scenes" if len(ranges) > 1 else ""),
             "target_err": target, "fp64": res["fp64"], "fp32_mixed": res["fp32_mixed"],
@@ -549,14 +564,13 @@ def run_ours(args):
     # FP32-mixed against plain FP64 at equal final-energy accuracy (twisted bar step 100 and the batch's step 30)
     eq = None
     if not args.no_extras and not args.phases and rank == 0:
-        import oracle as O
         simr = B.Sim(sc, precision=B.SIM_FP64, cuda_stream=stream.cuda_stream, persistent=1)
         for s in range(100):
             B.sim_step_async(simr.h, 1, targets[s])
         xb, vb, _ = B.sim_get_state(simr.h)
         simr.close()
         shapes = {B.SIM_FP32_MIXED: shape32, B.SIM_FP64: shape64}
-        eq = {"twisted_bar": equal_accuracy(B, torch, O, sc, stream, (xb, vb), sc.targets(100), (25, 50, 75, 100),
+        eq = {"twisted_bar": equal_accuracy(B, torch, sc, stream, (xb, vb), sc.targets(100), (25, 50, 75, 100),
                                             1000, "twisted bar, time step 100 (from the FP64 form's state)", shapes)}
         if not args.no_pile:
             bsc = S.batched()
@@ -565,7 +579,7 @@ def run_ours(args):
                 B.sim_step_async(simr.h, 1, None)
             xb, vb, _ = B.sim_get_state(simr.h)
             simr.close()
-            eq["batched"] = equal_accuracy(B, torch, O, bsc, stream, (xb, vb), None, (25, 50, 75, 100), 400,
+            eq["batched"] = equal_accuracy(B, torch, bsc, stream, (xb, vb), None, (25, 50, 75, 100), 400,
                                            "batched, 256 scenes, time step 30 (from the FP64 form's state)",
                                            {B.SIM_FP32_MIXED: 0, B.SIM_FP64: 0}, repeat=2)
 
