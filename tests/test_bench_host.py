@@ -53,3 +53,25 @@ def test_recorded_traffic_is_gated_on_the_kernel_sources(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.recorded_traffic("k_persistent", "fp32") is None
     assert bench.recorded_traffic("k_persistent", "fp32", scene="no_such_scene") is None
+
+
+def test_oracle_runs_only_in_the_cpu_legs():
+    """The library package never imports the oracle; bench.py imports it only in the CPU baseline and the
+    reference arm."""
+    import ast
+    import glob
+    root = bench.ROOT
+
+    def oracle_imports(tree):
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in node.names):
+                yield node
+            if isinstance(node, ast.ImportFrom) and (node.module or "").split(".")[0] == "oracle":
+                yield node
+
+    for path in glob.glob(os.path.join(root, "paper_2405_08001_gb300", "*.py")):
+        assert not list(oracle_imports(ast.parse(open(path).read()))), path
+    tree = ast.parse(open(os.path.join(root, "bench.py")).read())
+    assert not [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom)) and list(oracle_imports(n))]
+    users = {f.name for f in ast.walk(tree) if isinstance(f, ast.FunctionDef) and list(oracle_imports(f))}
+    assert users <= {"_oracle_iterations", "_oracle_side", "run_reference"}, users
